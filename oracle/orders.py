@@ -1,0 +1,78 @@
+"""Fill orders for the oracle, written from their definitions.
+
+Test infrastructure only.  Each function returns a list of (i, j) cells.  The
+orders always start with row 0 (its cells are then fixed by a prefix, e.g.
+the identity row of Section 2.2).
+
+For vertically symmetric squares only left-half cells (j < N/2) are listed:
+the right half follows from A[i][N-1-j] = N-1-A[i][j] (Section 5.4).
+"""
+
+
+def _cols(n, vsym):
+    return range(n // 2) if vsym else range(n)
+
+
+def row0(n, vsym=False):
+    return [(0, j) for j in _cols(n, vsym)]
+
+
+def md_ad_rows(n, vsym=False, first_rows=1):
+    """Rows 0..first_rows-1, then the main diagonal top to bottom, then the
+    anti-diagonal top to bottom, then the remaining cells row by row, left to
+    right (cells already listed are skipped).  With ``vsym`` only left-half
+    cells are used, so the main diagonal contributes rows i < N/2 and the
+    anti-diagonal rows i >= N/2."""
+    seen = set()
+    out = []
+
+    def add(c):
+        if c not in seen and c[1] in _cols(n, vsym):
+            seen.add(c)
+            out.append(c)
+
+    for i in range(first_rows):
+        for j in _cols(n, vsym):
+            add((i, j))
+    for i in range(n):
+        add((i, i))
+    for i in range(n):
+        add((i, n - 1 - i))
+    for i in range(n):
+        for j in _cols(n, vsym):
+            add((i, j))
+    return out
+
+
+def row_major(n, vsym=False):
+    return [(i, j) for i in range(n) for j in _cols(n, vsym)]
+
+
+def hourglass(n):
+    """Row 0, main diagonal, anti-diagonal, last row (the cells of an
+    hourglass design, Section 4.2), then rows 1..N-2."""
+    seen = set()
+    out = []
+
+    def add(c):
+        if c not in seen:
+            seen.add(c)
+            out.append(c)
+
+    for j in range(n):
+        add((0, j))
+    for i in range(n):
+        add((i, i))
+    for i in range(n):
+        add((i, n - 1 - i))
+    for j in range(n):
+        add((n - 1, j))
+    for i in range(n):
+        for j in range(n):
+            add((i, j))
+    return out
+
+
+def identity(n, vsym=False):
+    """Values of row 0 fixed to 0..N-1 (left half only when vsym)."""
+    return [j for j in _cols(n, vsym)]

@@ -1,0 +1,199 @@
+"""Pins for the oracle: values it must reproduce that do not come from itself.
+
+* brute force (row-permutation lister, oracle/brute.py) on orders 4..6,
+  whole-square counts and per-prefix counts;
+* known totals 48 / 960 / 92160 and the paper's printed hourglass count;
+* invariants the mathematics fixes: independence of the fill order, of the
+  symbols of row 0, transposition, the multipliers, sums over prefix splits.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import brute, orders
+
+D = oracle.DIAGONAL
+V = oracle.VSYM
+
+
+def _full_count(n, flags, order=None, row0=None):
+    vs = bool(flags & V)
+    if order is None:
+        order = orders.md_ad_rows(n, vsym=vs)
+    if row0 is None:
+        row0 = orders.identity(n, vsym=vs)
+    return oracle.count(n, flags, order, row0)[0]
+
+
+@pytest.mark.parametrize("n", [4, 5, 6])
+def test_brute_force_dls_row0_fixed(n):
+    sq = brute.squares(n, diagonal=True, row0=list(range(n)))
+    assert _full_count(n, D) == len(sq)
+
+
+@pytest.mark.parametrize("n", [4, 5])
+def test_brute_force_free_row0(n):
+    # no prefix at all: every square of the order
+    for flags, diag in ((D, True), (0, False)):
+        sq = brute.squares(n, diagonal=diag, row0=None)
+        got = oracle.count(n, flags, orders.row_major(n), [])[0]
+        assert got == len(sq)
+
+
+@pytest.mark.parametrize("n", [4, 5])
+def test_brute_force_latin_row0_fixed(n):
+    sq = brute.squares(n, diagonal=False, row0=list(range(n)))
+    assert _full_count(n, 0) == len(sq)
+
+
+@pytest.mark.parametrize("n", [4, 6])
+def test_brute_force_vsym(n):
+    sq = brute.squares(n, diagonal=True, vsym=True, row0=list(range(n)))
+    assert _full_count(n, D | V) == len(sq)
+    # vertically symmetric squares are diagonal squares too
+    assert len(sq) <= _full_count(n, D)
+
+
+@pytest.mark.parametrize("n", [4, 6])
+def test_vsym_multiplier_by_brute_force(n):
+    free = brute.squares(n, diagonal=True, vsym=True, row0=None)
+    assert len(free) == _full_count(n, D | V) * oracle.multiplier(n, D | V)
+
+
+@pytest.mark.parametrize("n", [4, 5])
+def test_dls_multiplier_by_brute_force(n):
+    free = brute.squares(n, diagonal=True, row0=None)
+    assert len(free) == _full_count(n, D) * oracle.multiplier(n, D)
+
+
+@pytest.mark.parametrize("n", [3, 5, 7])
+def test_vsym_odd_order_is_empty(n):
+    assert _full_count(n, D | V) == 0
+    assert len(brute.squares(min(n, 5), True, True, row0=None)) == 0
+
+
+def test_known_totals(golden):
+    for n in (4, 5, 6):
+        assert _full_count(n, D) * oracle.multiplier(n, D) == golden["dls_total_%d" % n]
+
+
+def test_hourglass_count_order8(golden):
+    # Section 4.2: hourglass designs of order 8 (row 0 identity, both
+    # diagonals, last row); the hourglass order lists exactly those cells first
+    n = 8
+    ho = orders.hourglass(n)
+    cells = set()
+    for i in range(n):
+        cells |= {(0, i), (i, i), (i, n - 1 - i), (n - 1, i)}
+    part = ho[:len(cells)]
+    assert set(part) == cells
+    assert oracle.count(n, D, part, orders.identity(n))[0] == golden["hourglass8"]
+
+
+@pytest.mark.parametrize("n", [5, 6])
+def test_fill_order_invariance(n):
+    ref = _full_count(n, D)
+    rng = np.random.default_rng(n)
+    for order in (orders.row_major(n), orders.hourglass(n)):
+        assert _full_count(n, D, order) == ref
+    rest = [c for c in orders.row_major(n) if c[0] != 0]
+    for _ in range(3):
+        perm = rng.permutation(len(rest))
+        order = orders.row0(n) + [rest[k] for k in perm]
+        assert _full_count(n, D, order) == ref
+
+
+def test_relabel_invariance_of_row0():
+    # any permutation as row 0 gives the same count (the symbols can be renamed)
+    n = 5
+    ref = _full_count(n, D)
+    for p in itertools.permutations(range(n)):
+        assert _full_count(n, D, row0=list(p)) == ref
+
+
+def test_transpose_invariance():
+    # transposing keeps both diagonals, so fixing column 0 counts the same
+    n = 6
+    order = [(i, 0) for i in range(n)] + [c for c in orders.row_major(n) if c[1] != 0]
+    assert oracle.count(n, D, order, list(range(n)))[0] == _full_count(n, D)
+
+
+@pytest.mark.parametrize("n,flags", [(5, D), (6, D), (6, D | V), (5, 0)])
+def test_per_prefix_counts_against_brute_force(n, flags):
+    vs = bool(flags & V)
+    sq = brute.squares(n, diagonal=bool(flags & D), vsym=vs, row0=list(range(n)))
+    order = orders.md_ad_rows(n, vsym=vs)
+    base = np.array([orders.identity(n, vs)], np.uint8)
+    r0 = len(base[0])
+    for depth in range(r0, len(order) + 1, 3):
+        pre, _ = oracle.extend(n, flags, order, base, depth)
+        # every full square is counted exactly once across the prefixes
+        cnt, _ = oracle.count_many(n, flags, order, pre)
+        assert int(cnt.sum()) == len(sq)
+        for k in range(0, len(pre), max(1, len(pre) // 25)):
+            cells = order[:depth]
+            vals = [int(x) for x in pre[k]]
+            if vs:
+                cells = cells + [(i, n - 1 - j) for (i, j) in cells]
+                vals = vals + [n - 1 - x for x in vals]
+            assert cnt[k] == brute.count_matching(sq, cells, vals)
+
+
+def test_invalid_prefix_counts_zero():
+    n = 6
+    order = orders.md_ad_rows(n)
+    bad = orders.identity(n) + [0]            # (1,1) == (0,0) on the diagonal
+    assert oracle.count(n, D, order, bad)[0] == 0
+    bad = orders.identity(n) + [7]            # value out of range
+    assert oracle.count(n, D, order, bad)[0] == 0
+
+
+def test_split_sums_equal_unsplit():
+    n = 7
+    order = orders.md_ad_rows(n)
+    base = np.array([orders.identity(n)], np.uint8)
+    total = _full_count(n, D)
+    for depth in (n + 3, n + 10):
+        pre, par = oracle.extend(n, D, order, base, depth)
+        assert (par == 0).all()
+        cnt, _ = oracle.count_many(n, D, order, pre, threads=4)
+        assert int(cnt.sum()) == total
+
+
+def test_extend_is_lexicographic_and_matches_partial_count():
+    n = 6
+    order = orders.md_ad_rows(n)
+    base = np.array([orders.identity(n)], np.uint8)
+    for depth in (n + 2, n + 5, n + 9):
+        pre, _ = oracle.extend(n, D, order, base, depth)
+        assert len(pre) == oracle.count(n, D, order[:depth], orders.identity(n))[0]
+        keys = [tuple(r) for r in pre]
+        assert keys == sorted(keys) and len(set(keys)) == len(keys)
+
+
+def test_sample_prefix_is_valid_and_deterministic():
+    rng = np.random.Generator(np.random.PCG64(5))
+    for n, flags in ((6, D), (8, D), (8, D | V), (9, D)):
+        vs = bool(flags & V)
+        order = orders.md_ad_rows(n, vsym=vs, first_rows=n - 3)
+        depth = (n - 3) * len(orders.identity(n, vs))
+        draws = rng.integers(0, 2**32, size=4096, dtype=np.uint32)
+        p1, u1 = oracle.sample_prefix(n, flags, order, depth, draws)
+        p2, u2 = oracle.sample_prefix(n, flags, order, depth, draws)
+        assert p1 is not None and u1 == u2 and (p1 == p2).all()
+        # valid: the partial count of exactly these cells is 1
+        assert oracle.count(n, flags, order[:depth], p1)[0] == 1
+
+
+def test_nodes_count_accepted_placements():
+    # the last position of the order accepts exactly one value per square,
+    # so nodes >= squares, and a full prefix has no nodes and one square
+    n = 5
+    order = orders.md_ad_rows(n)
+    c, nd = oracle.count(n, D, order, orders.identity(n))
+    assert nd >= c
+    sq = brute.squares(n, True, row0=list(range(n)))
+    full = [int(sq[0][i][j]) for (i, j) in order]
+    assert oracle.count(n, D, order, full) == (1, 0)
