@@ -1,0 +1,371 @@
+#!/usr/bin/env python
+"""Throughput of the GPU enumerator of diagonal Latin squares.
+
+One step = one pass of the whole search over one batch: order 8, row 0 fixed
+to the identity, 64 seed-drawn main-diagonal fillings, each split 20 cells
+past row 0 (~1.17 M independent prefixes, ~2.5e8 squares), counted by the
+persistent kernel launched from a CUDA graph.  Reported:
+
+* value     -- squares enumerated per second (exact counts), device-timed
+               with CUDA events on the launching stream, L2 flushed between
+               steps;
+* plain     -- the same for the one-thread-per-prefix launch;
+* e2e       -- through dls_count_host (host buffers, copies inside the timed
+               region);
+* roofline  -- integer-issue roofline of the search kernel;
+* cpu_baseline -- the oracle on the host cores, on a bounded sample.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With torchrun (N > 1) each rank counts its own 64 diagonals (seed = rank) and
+rank 0 prints the line (weak scaling, no collective on the data path).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import dls_inputs  # noqa: E402
+
+METRIC = "diagonal Latin squares enumerated/sec on 1 GB300 (exact count) vs plain launch; p99 latency"
+UNIT = "squares/s"
+WORKLOAD = "dls8_diag64"
+N, FLAGS, DIAGS, AFTER_ROW0 = 8, 1, 64, 20
+# integer operations per search node in the bitmask form (see the design
+# notes): isolate + clear the lowest candidate bit (4), mark and unmark the
+# row and column words (4), next cell's forbidden mask and complement (2),
+# loop test (1)
+OPS_PER_NODE = 11
+ISSUE_LANES_PER_SM = 4 * 32      # 4 schedulers x 32 lanes, one instruction/clk
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--launch", default="", help="json dict of Launch fields")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------ workloads --
+
+def product_workload(dls, seed):
+    order = dls.fill_order(N, FLAGS)
+    ident = np.arange(N, dtype=np.uint8)[None]
+    diags, _ = dls.extend_prefixes(N, FLAGS, order, ident, N + (N - 1))
+    picks = dls_inputs.choose(len(diags), DIAGS, seed)
+    pre, par = dls.extend_prefixes(N, FLAGS, order, diags[picks], N + AFTER_ROW0)
+    return order, pre, par, picks
+
+
+def oracle_sample(seed, n_diags):
+    """The oracle's own prefixes for `n_diags` of the run's diagonals."""
+    import oracle
+    from oracle import orders
+    o_order = orders.md_ad_rows(N)
+    ident = np.array([orders.identity(N)], np.uint8)
+    diags, _ = oracle.extend(N, FLAGS, o_order, ident, N + (N - 1))
+    picks = dls_inputs.choose(len(diags), DIAGS, seed)
+    sub = picks[dls_inputs.choose(len(picks), n_diags, seed + 1000)]
+    pre, _ = oracle.extend(N, FLAGS, o_order, diags[sub], N + AFTER_ROW0)
+    return o_order, pre
+
+
+def run_oracle(o_order, pre, threads):
+    import oracle
+    t0 = time.perf_counter()
+    counts, nodes = oracle.count_many(N, FLAGS, o_order, pre, threads=threads)
+    dt = time.perf_counter() - t0
+    return int(counts.sum()), int(nodes.sum()), dt
+
+
+# --------------------------------------------------------------- clocks --
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id=None):
+        self.rows = []
+        self.proc = None
+        self.bus_id = bus_id
+
+    def start(self):
+        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if self.bus_id:
+            cmd[1:1] = ["-i", self.bus_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm = []
+        mx = []
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if r[4 + k].lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_bus_id(dev):
+    try:
+        import torch
+        p = torch.cuda.get_device_properties(dev)
+        dom = getattr(p, "pci_domain_id", 0)
+        bus = getattr(p, "pci_bus_id", None)
+        devid = getattr(p, "pci_device_id", 0)
+        if bus is None:
+            return None
+        return "%08X:%02X:%02X.0" % (dom, bus, devid)
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------- measurement --
+
+def timed_steps(launch_fn, stream, steps, flush):
+    """Per-step CUDA events around launch_fn on `stream`, L2 flushed between
+    steps (outside the events).  Returns the list of step times (s)."""
+    import torch
+    evs = []
+    with torch.cuda.stream(stream):
+        for _ in range(steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            launch_fn()
+            b.record(stream)
+            evs.append((a, b))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) / 1e3 for a, b in evs]
+
+
+def reference_arm(args):
+    """The oracle, as it stands, on the host cores: each step a bounded sample
+    (one diagonal's prefixes) of the same workload."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    threads = os.cpu_count() or 1
+    o_order, pre = oracle_sample(0, 1)
+    for _ in range(args.warmup):
+        run_oracle(o_order, pre, threads)
+    sq = 0
+    t = 0.0
+    for _ in range(args.steps):
+        c, _, dt = run_oracle(o_order, pre, threads)
+        sq += c
+        t += dt
+    value = sq / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N, "sample": "1 of the 64 diagonals per step",
+                   "prefixes_per_step": int(len(pre))},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": "all %d prefixes of 1 seed-chosen diagonal of the 64"
+                                   % len(pre)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    import torch
+    import paper_1709_02599_gb300 as dls
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.Stream()
+
+    seed = rank
+    order, pre, par, picks = product_workload(dls, seed)
+    P, depth = pre.shape
+    d_pre = torch.from_numpy(pre).to("cuda")
+    counts = torch.empty(P, dtype=torch.uint64, device="cuda")
+    total = torch.empty(1, dtype=torch.uint64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    cfg = json.loads(args.launch) if args.launch else {}
+    launch = dls.Launch(**cfg)
+    plan = dls.Plan(N, FLAGS, order, d_pre, counts, total, launch)
+
+    # node count of the workload (separately compiled counting variant,
+    # untimed) and the exact square count
+    nodes_t = torch.zeros(1, dtype=torch.uint64, device="cuda")
+    with torch.cuda.stream(stream):
+        dls.count(N, FLAGS, order, d_pre, counts=counts, total=total, nodes=nodes_t,
+                  launch=launch, stream=stream)
+    torch.cuda.synchronize()
+    squares = int(total.cpu().numpy()[0])
+    nodes = int(nodes_t.cpu().numpy()[0])
+
+    for _ in range(max(args.warmup, 0)):
+        plan.launch(stream)
+    torch.cuda.synchronize()
+
+    if ws > 1:
+        torch.distributed.barrier()
+    sampler = ClockSampler(gpu_bus_id(dev)) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    times = timed_steps(lambda: plan.launch(stream), stream, args.steps, flush)
+    t_wall = time.perf_counter() - t_wall0
+    clocks = sampler.stop() if sampler else None
+    if int(total.cpu().numpy()[0]) != squares:
+        raise RuntimeError("count changed between runs")
+    step_s = sum(times) / len(times)
+    if ws > 1:
+        t = torch.tensor([step_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        step_s = float(t.item())
+        s = torch.tensor([float(squares)], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(s)
+        squares_all = int(s.item())
+    else:
+        squares_all = squares
+    value = squares_all / step_s
+
+    # plain launch on the same workload
+    plain = None
+    if not args.no_plain:
+        pplan = dls.Plan(N, FLAGS, order, d_pre, counts, total,
+                         dls.Launch(kernel=dls.KERNEL_PLAIN))
+        for _ in range(max(args.warmup, 1)):
+            pplan.launch(stream)
+        torch.cuda.synchronize()
+        pt = timed_steps(lambda: pplan.launch(stream), stream, args.steps, flush)
+        if int(total.cpu().numpy()[0]) != squares:
+            raise RuntimeError("plain launch count differs")
+        p_step = sum(pt) / len(pt)
+        plain = {"value": squares / p_step, "unit": UNIT, "ms_per_step": 1e3 * p_step,
+                 "kernel": "k_plain", "speedup_of_persistent": p_step / step_s}
+        pplan.close()
+
+    # end to end through the host-buffer entry point
+    pinned_in = torch.from_numpy(pre).pin_memory()
+    pinned_out = torch.empty(P, dtype=torch.int64).pin_memory()
+    for _ in range(2):
+        dls.count_host(N, FLAGS, order, pinned_in, pinned_out, launch, stream)
+    e2e_t = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        _, tot = dls.count_host(N, FLAGS, order, pinned_in, pinned_out, launch, stream)
+        e2e_t.append(time.perf_counter() - t0)
+        if tot != squares:
+            raise RuntimeError("host-buffer count differs")
+    e2e_step = sum(e2e_t) / len(e2e_t)
+
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    sm_max_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+    peak_tops = sms * ISSUE_LANES_PER_SM * sm_max_mhz * 1e6 / 1e12
+    achieved_tops = nodes * OPS_PER_NODE / step_s / 1e12
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * step_s, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N, "flags": "diagonal", "row0": "identity",
+                   "diagonal_fillings": DIAGS, "seed": "rank", "split_after_row0": AFTER_ROW0,
+                   "prefixes": int(P), "squares_per_step": squares, "nodes_per_step": nodes,
+                   "kernel": "k_persistent (CUDA graph)", "launch": cfg,
+                   "l2": "flushed: 256 MiB write between timed steps"},
+        "plain": plain,
+        "e2e": {"value": squares_all / e2e_step if ws == 1 else squares / e2e_step,
+                "unit": UNIT, "h2d_bytes_per_step": int(P * depth),
+                "d2h_bytes_per_step": int(P * 8), "entry": "dls_count_host"},
+        "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops,
+                     "unit": "Tops/s", "frac": achieved_tops / peak_tops, "traffic": None,
+                     "ops_per_node": OPS_PER_NODE,
+                     "peak_from": "%d SMs x 4 schedulers x 32 lanes x %.0f MHz" % (sms, sm_max_mhz)},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+        "wall_s_timed_region": t_wall,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        o_order, opre = oracle_sample(seed, 2)
+        c, _, dt = run_oracle(o_order, opre, threads)
+        line["cpu_baseline"] = {"value": c / dt, "unit": UNIT, "cores": threads,
+                                "kind": "oracle",
+                                "sample": "all %d prefixes of 2 seed-chosen diagonals of the 64 "
+                                          "(%d squares, %.1f s)" % (len(opre), c, dt)}
+    plan.close()
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,249 @@
+/*
+ * dls.h -- C ABI of the GB300 enumerator of diagonal Latin squares
+ * (Kochemazov, Vatutin, Zaikin, "Fast Algorithm for Enumerating Diagonal
+ * Latin Squares of Small Order").
+ *
+ * Definitions (Section 1): a Latin square of order N is an N x N array over
+ * {0..N-1} whose rows and columns are permutations.  It is diagonal when the
+ * main diagonal and the anti-diagonal are permutations too, and vertically
+ * symmetric when A[i][N-1-j] == N-1-A[i][j] for all i, j (Section 5.4).
+ *
+ * The method (Sections 2-3): cells are filled one at a time in a fixed fill
+ * order; one bitmask per row, column and diagonal records the values in use;
+ * a cell's admissible values are ALL & ~(row | column | diagonals) and are
+ * visited lowest bit first (Algorithm 4).  The search tree is split at a
+ * fixed depth into independent subproblems ("prefixes", Section 5.2) whose
+ * counts are summed.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - n: the order, 1 <= n <= DLS_MAX_N.
+ * - flags: OR of DLS_DIAGONAL and DLS_VSYM (0 = ordinary Latin squares).
+ * - order: host array of order_len (i, j) byte pairs, the fill order.  Cells
+ *   must be distinct and inside the square.  With DLS_VSYM every cell must be
+ *   in the left half (j < n/2); its mirror (i, n-1-j) is filled with the
+ *   mirrored value at the same time.  The order need not cover the square:
+ *   a shorter order counts partial squares (Section 5.3 counts the first k
+ *   cells in row-major order that way).
+ * - prefix: the values of the first `depth` cells of the order, one byte per
+ *   cell (0..n-1), prefixes packed back to back (`depth` bytes each).  Row 0
+ *   is not special: to fix it to 0..n-1 (Section 2.2), start the order with
+ *   row 0 and put 0..n-1 (left half with DLS_VSYM) in every prefix.
+ * - Count(prefix) = number of ways to give every remaining cell of the order
+ *   (and its mirror with DLS_VSYM) a value so that no value repeats in a row,
+ *   a column and, with DLS_DIAGONAL, on either diagonal, among the cells
+ *   assigned.  A prefix that breaks a constraint or holds a value >= n has
+ *   count 0.  With DLS_VSYM and odd n >= 3 every count is 0: the middle
+ *   column would have to hold (n-1)/2 in every row.
+ * - All counts are exact unsigned 64-bit integers.
+ * - Return value: DLS_OK (0) or a dls_status code; dls_strerror() names it.
+ *   Device work is asynchronous on the given CUDA stream (NULL = legacy
+ *   default stream); errors raised by the GPU while it runs are reported by
+ *   the next call that synchronises.
+ */
+#ifndef DLS_H
+#define DLS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DLS_MAX_N 16
+#define DLS_MAX_CELLS (DLS_MAX_N * DLS_MAX_N)
+
+/* flags */
+#define DLS_DIAGONAL 1u
+#define DLS_VSYM 2u
+
+typedef enum {
+    DLS_OK = 0,
+    DLS_ERR_INVALID_N = 1,    /* n outside 1..DLS_MAX_N                      */
+    DLS_ERR_BAD_ORDER = 2,    /* repeated / out-of-range / right-half cell   */
+    DLS_ERR_BAD_ARG = 3,      /* NULL pointer, negative size, bad depth ...  */
+    DLS_ERR_CAPACITY = 4,     /* output buffer too small; *n_out = needed    */
+    DLS_ERR_CUDA = 5,         /* a CUDA call failed (dls_last_cuda_error())  */
+    DLS_ERR_TIMEOUT = 6,      /* a bounded wait or budget ran out            */
+    DLS_ERR_ABORTED = 7,      /* stopped through dls_server_abort()          */
+    DLS_ERR_NO_MEMORY = 8,    /* host or device allocation failed            */
+    DLS_ERR_BAD_STATE = 9     /* object used after release / wrong sequence  */
+} dls_status;
+
+/* kinds of fill order for dls_fill_order() */
+typedef enum {
+    /* rows 0..first_rows-1, then the main diagonal, then the anti-diagonal,
+     * then the remaining cells row by row (Section 2.3 fills the diagonals
+     * first; Section 4.3 keeps them first) */
+    DLS_ORDER_MD_AD_ROWS = 0,
+    /* row by row, left to right (the trivial order of Sections 2.1, 5.3) */
+    DLS_ORDER_ROW_MAJOR = 1,
+    /* row 0, both diagonals, last row, then the rest: the cells of an
+     * hourglass design first (Section 4.2) */
+    DLS_ORDER_HOURGLASS = 2,
+    /* the greedy most-constrained-cell order of Section 2.3 with its
+     * forced-last-cell rule (Fig. 1 for order 9) */
+    DLS_ORDER_HEURISTIC = 3
+} dls_order_kind;
+
+typedef struct {
+    uint64_t lo, hi;
+} dls_u128;
+
+/* ------------------------------------------------------------------ info */
+
+/* Name of a status code (static string, never NULL). */
+const char *dls_strerror(int code);
+
+/* Last CUDA error string seen by the library on this thread ("" if none). */
+const char *dls_last_cuda_error(void);
+
+/* Library version, (major << 16) | minor. */
+int dls_version(void);
+
+/* ------------------------------------------------------ host-side setup */
+
+/* Fill order of the given kind (Sections 2.3, 4.2).  Writes up to `cap` (i,j)
+ * pairs to ij_out (2*cap bytes) and their number to *len_out.  first_rows
+ * (>= 1) only affects DLS_ORDER_MD_AD_ROWS.  With DLS_VSYM only left-half
+ * cells are listed.  Host memory; caller owns both buffers.  Errors:
+ * INVALID_N, BAD_ARG, CAPACITY (*len_out = needed). */
+int dls_fill_order(int n, uint32_t flags, int kind, int first_rows,
+                   uint8_t *ij_out, int cap, int *len_out);
+
+/* The prefix split of Section 5.2: every valid assignment of the first
+ * `depth` order cells that extends one of the n_base base prefixes (each
+ * base_depth bytes), base prefixes in turn, each one's extensions in
+ * ascending lexicographic order of the values along the fill order.  Writes
+ * at most `cap` records of `depth` bytes to out and, if parents_out is not
+ * NULL, the index of the base prefix of each record; *n_out = number of
+ * records (also when it exceeds cap, with DLS_ERR_CAPACITY).  Invalid base
+ * prefixes have no extensions.  Host memory, caller-owned. */
+int dls_extend_prefixes(int n, uint32_t flags, const uint8_t *order,
+                        int order_len, const uint8_t *base, int base_depth,
+                        int64_t n_base, int depth, uint8_t *out, int64_t cap,
+                        int64_t *parents_out, int64_t *n_out);
+
+/* A random valid prefix built from caller-supplied uniform draws (used for
+ * the partial squares of the serving workload).  Cells are filled in order;
+ * each row's cells must be contiguous in the order.  For each cell the
+ * admissible values are listed in ascending order and draws[k] % count picks
+ * one (one draw per cell filled); when a cell has no admissible value, the
+ * cells of its row filled in the current pass are cleared and the row starts
+ * again, taking no draw.  Writes `depth` bytes to out and the number of
+ * draws used to *draws_used.  DLS_ERR_CAPACITY if the draws run out first.
+ * Host memory, caller-owned. */
+int dls_sample_prefix(int n, uint32_t flags, const uint8_t *order,
+                      int order_len, int depth, const uint32_t *draws,
+                      int64_t n_draws, uint8_t *out, int64_t *draws_used);
+
+/* Number of squares represented by one square whose row 0 is 0..n-1:
+ * n! for diagonal and ordinary Latin squares (Section 2.2; the order-9 total
+ * of Section 5.2.1 is the fixed-row count times 9!), 2^(n/2) (n/2)! for
+ * vertically symmetric ones of even order (the relabellings that commute
+ * with v -> n-1-v), 1 for odd vertically symmetric orders. */
+dls_u128 dls_multiplier(int n, uint32_t flags);
+
+/* 128-bit a * b and a + b (totals of order 9 and above exceed 64 bits). */
+dls_u128 dls_mul_u64(uint64_t a, dls_u128 b);
+dls_u128 dls_add_u128(dls_u128 a, dls_u128 b);
+
+/* -------------------------------------------------------- GPU counting */
+
+typedef enum {
+    DLS_KERNEL_PERSISTENT = 0, /* one resident grid, atomic work queue,
+                                  in-warp work donation                     */
+    DLS_KERNEL_PLAIN = 1       /* one thread per (prefix, lane) work item     */
+} dls_kernel_kind;
+
+/* Launch shape.  Zero fields take the defaults. */
+typedef struct {
+    int kernel;           /* dls_kernel_kind                                 */
+    int block_threads;    /* 32..512, multiple of 32 (default 128)           */
+    int blocks_per_sm;    /* persistent grid: blocks per SM (default: all that
+                             fit)                                            */
+    int lanes_per_prefix; /* 1,2,4,...,32 work items per prefix (default 1); a
+                             prefix's item s takes the nodes at order
+                             position split_pos whose DFS index is s mod
+                             lanes_per_prefix                                */
+    int split_pos;        /* order position of that split (default depth+2)  */
+    int donate;           /* persistent only: 1 = idle lanes take work from
+                             busy lanes of their warp once the queue is empty
+                             (default), -1 = off                            */
+    int check_every;      /* persistent only: iterations between donation
+                             checks (power of two, default 64)               */
+} dls_launch_t;
+
+/* Count completions of every prefix on the GPU (Algorithm 4 on the device).
+ * d_prefixes: DEVICE, n_prefixes * depth bytes (caller-owned).
+ * d_counts:   DEVICE, n_prefixes uint64 (caller-owned) or NULL; overwritten
+ *             with Count(prefix) for each prefix.
+ * d_total:    DEVICE, one uint64 (caller-owned) or NULL; overwritten with the
+ *             sum of all counts (exact; the caller must know it fits 64 bits).
+ * stream:     cudaStream_t (NULL = default stream).
+ * Uses a small per-(device, stream) work area that the library allocates on
+ * first use and keeps until dls_release(); call once before capturing the
+ * stream into a CUDA graph.  Asynchronous.  Errors: INVALID_N, BAD_ORDER,
+ * BAD_ARG (depth outside 0..order_len, n_prefixes < 0, both outputs NULL),
+ * CUDA, NO_MEMORY.  The persistent kernel is used (dls_count_ex selects). */
+int dls_count(int n, uint32_t flags, const uint8_t *order, int order_len,
+              const uint8_t *d_prefixes, int depth, int64_t n_prefixes,
+              uint64_t *d_counts, uint64_t *d_total, void *stream);
+
+/* Same counts from the plain one-thread-per-prefix launch (the comparison
+ * baseline): no queue, no donation, one grid thread per prefix. */
+int dls_count_plain(int n, uint32_t flags, const uint8_t *order,
+                    int order_len, const uint8_t *d_prefixes, int depth,
+                    int64_t n_prefixes, uint64_t *d_counts, uint64_t *d_total,
+                    void *stream);
+
+/* dls_count with an explicit launch shape (cfg may be NULL = defaults).
+ * d_nodes: DEVICE, one uint64, or NULL.  If given, it is overwritten with
+ * the number of nodes of the search -- accepted placements of a value into
+ * a cell at order positions >= depth, the last position included (one pass
+ * of the body of a loop of Algorithm 1 past its occupancy test) -- counted
+ * by a separately compiled variant of the kernel. */
+int dls_count_ex(int n, uint32_t flags, const uint8_t *order, int order_len,
+                 const uint8_t *d_prefixes, int depth, int64_t n_prefixes,
+                 uint64_t *d_counts, uint64_t *d_total, uint64_t *d_nodes,
+                 const dls_launch_t *cfg, void *stream);
+
+/* Host-buffer entry point: copies h_prefixes (HOST, n_prefixes*depth bytes;
+ * page-locked memory makes the copy asynchronous) to the device, counts, and
+ * copies the counts back to h_counts (HOST, n_prefixes uint64, may be NULL)
+ * and the sum to *total_out (may be NULL; the plain 128-bit sum of the
+ * counts -- multiply by dls_multiplier() for whole-square totals).
+ * Synchronous: returns after the copies back have landed.  The device
+ * buffers come from a per-(device, stream) area that grows on demand and
+ * lives until dls_release(). */
+int dls_count_host(int n, uint32_t flags, const uint8_t *order,
+                   int order_len, const uint8_t *h_prefixes, int depth,
+                   int64_t n_prefixes, uint64_t *h_counts,
+                   dls_u128 *total_out, const dls_launch_t *cfg,
+                   void *stream);
+
+/* Free the library's per-(device, stream) work areas and cached plans. */
+void dls_release(void);
+
+/* ------------------------------------------------------------ plans */
+
+/* A plan freezes one dls_count_ex call (all pointers and sizes) into a CUDA
+ * graph so that repeated launches cost one graph launch.  The buffers must
+ * stay valid while the plan lives.  dls_plan_create captures on its own
+ * private stream. */
+typedef struct dls_plan dls_plan;
+
+int dls_plan_create(dls_plan **plan_out, int n, uint32_t flags,
+                    const uint8_t *order, int order_len,
+                    const uint8_t *d_prefixes, int depth, int64_t n_prefixes,
+                    uint64_t *d_counts, uint64_t *d_total,
+                    const dls_launch_t *cfg);
+int dls_plan_launch(dls_plan *plan, void *stream);
+void dls_plan_destroy(dls_plan *plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DLS_H */

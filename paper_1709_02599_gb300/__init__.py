@@ -1,0 +1,218 @@
+"""GB300 enumerator of diagonal Latin squares (Kochemazov, Vatutin, Zaikin).
+
+Python binding of the C ABI in include/dls.h: every function here only
+marshals arguments and calls libdls.so; every step of the count runs in the
+library's CUDA kernels (or, for prefix generation, in its host C++ code).
+PyTorch provides device memory and streams.
+
+    import paper_1709_02599_gb300 as dls
+    order = dls.fill_order(8, dls.DIAGONAL)             # md, ad, rows
+    base = np.arange(8, dtype=np.uint8)[None]          # row 0 = identity
+    pre, _ = dls.extend_prefixes(8, dls.DIAGONAL, order, base, 8 + 20)
+    counts = dls.count(8, dls.DIAGONAL, order, torch.from_numpy(pre).cuda())
+"""
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _lib
+from ._lib import (DIAGONAL, VSYM, DLS_MAX_N, ORDER_MD_AD_ROWS, ORDER_ROW_MAJOR,  # noqa: F401
+                   ORDER_HOURGLASS, ORDER_HEURISTIC, KERNEL_PERSISTENT, KERNEL_PLAIN,
+                   DlsError)
+
+
+@dataclass
+class Launch:
+    """Launch shape (dls_launch_t); zero fields take the library defaults."""
+    kernel: int = KERNEL_PERSISTENT
+    block_threads: int = 0
+    blocks_per_sm: int = 0
+    lanes_per_prefix: int = 0
+    split_pos: int = 0
+    donate: int = 0
+    check_every: int = 0
+
+    def c(self):
+        return _lib.LaunchT(self.kernel, self.block_threads, self.blocks_per_sm,
+                            self.lanes_per_prefix, self.split_pos, self.donate,
+                            self.check_every)
+
+
+def lib():
+    return _lib.load()
+
+
+def _u8(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.uint8))
+
+
+def _order(order):
+    o = _u8(order).reshape(-1, 2)
+    return o, o.ctypes.data_as(_lib.u8p), len(o)
+
+
+def fill_order(n, flags=DIAGONAL, kind=ORDER_MD_AD_ROWS, first_rows=1):
+    """Fill order as uint8 [L, 2] (i, j) pairs."""
+    L = lib()
+    buf = np.zeros((DLS_MAX_N * DLS_MAX_N, 2), np.uint8)
+    ln = ctypes.c_int(0)
+    _lib.check(L.dls_fill_order(n, flags, kind, first_rows, buf.ctypes.data_as(_lib.u8p),
+                                DLS_MAX_N * DLS_MAX_N, ctypes.byref(ln)), "dls_fill_order")
+    return buf[:ln.value].copy()
+
+
+def extend_prefixes(n, flags, order, base, depth):
+    """All valid assignments of the first ``depth`` order cells extending
+    the rows of ``base`` (uint8 [B, base_depth]).  Returns (uint8 [M, depth],
+    int64 parents [M])."""
+    L = lib()
+    o, op, ol = _order(order)
+    b = _u8(base)
+    if b.ndim == 1:
+        b = b.reshape(1, -1)
+    nb, bd = b.shape
+    bptr = b.ctypes.data_as(_lib.u8p) if b.size else None
+    need = ctypes.c_int64(0)
+    cap = 1 << 16
+    while True:
+        out = np.zeros((cap, max(depth, 1)), np.uint8)
+        par = np.zeros(cap, np.int64)
+        rc = L.dls_extend_prefixes(n, flags, op, ol, bptr, bd, nb, depth,
+                                   out.ctypes.data_as(_lib.u8p), cap,
+                                   par.ctypes.data_as(_lib.i64p), ctypes.byref(need))
+        if rc == _lib.ERR_CAPACITY:
+            cap = int(need.value)
+            continue
+        _lib.check(rc, "dls_extend_prefixes")
+        m = int(need.value)
+        return out[:m, :depth].copy(), par[:m].copy()
+
+
+def sample_prefix(n, flags, order, depth, draws):
+    """Draw-driven random prefix -> (uint8 [depth], draws used); (None, -1)
+    when the draws run out."""
+    L = lib()
+    o, op, ol = _order(order)
+    d = np.ascontiguousarray(np.asarray(draws, dtype=np.uint32))
+    out = np.zeros(max(depth, 1), np.uint8)
+    used = ctypes.c_int64(0)
+    rc = L.dls_sample_prefix(n, flags, op, ol, depth, d.ctypes.data_as(_lib.u32p), d.size,
+                             out.ctypes.data_as(_lib.u8p), ctypes.byref(used))
+    if rc == _lib.ERR_CAPACITY:
+        return None, -1
+    _lib.check(rc, "dls_sample_prefix")
+    return out[:depth].copy(), int(used.value)
+
+
+def multiplier(n, flags):
+    return lib().dls_multiplier(n, flags).value()
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev_ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def count(n, flags, order, prefixes, counts=None, total=None, nodes=None, launch=None,
+          stream=None):
+    """Count completions of every prefix on the GPU.
+
+    prefixes: torch uint8 CUDA tensor [P, depth] (contiguous).
+    counts / total / nodes: optional torch uint64 CUDA tensors ([P], [1], [1])
+    to write into; counts is allocated when None.  Asynchronous on
+    ``stream`` (default: torch's current stream).  Returns counts."""
+    import torch
+    if prefixes.dtype != torch.uint8 or not prefixes.is_cuda or prefixes.dim() != 2:
+        raise ValueError("prefixes must be a 2-D uint8 CUDA tensor")
+    prefixes = prefixes.contiguous()
+    P, depth = prefixes.shape
+    if counts is None:
+        counts = torch.empty(P, dtype=torch.uint64, device=prefixes.device)
+    o, op, ol = _order(order)
+    cfg = (launch or Launch()).c()
+    _lib.check(lib().dls_count_ex(n, flags, op, ol, _dev_ptr(prefixes) if P else None, depth,
+                                  P, _dev_ptr(counts), _dev_ptr(total), _dev_ptr(nodes),
+                                  ctypes.byref(cfg), _stream_handle(stream)), "dls_count_ex")
+    return counts
+
+
+def count_plain(n, flags, order, prefixes, counts=None, total=None, stream=None):
+    """The plain one-thread-per-prefix launch (dls_count_plain)."""
+    import torch
+    prefixes = prefixes.contiguous()
+    P, depth = prefixes.shape
+    if counts is None:
+        counts = torch.empty(P, dtype=torch.uint64, device=prefixes.device)
+    o, op, ol = _order(order)
+    _lib.check(lib().dls_count_plain(n, flags, op, ol, _dev_ptr(prefixes) if P else None,
+                                     depth, P, _dev_ptr(counts), _dev_ptr(total),
+                                     _stream_handle(stream)), "dls_count_plain")
+    return counts
+
+
+def count_host(n, flags, order, prefixes, counts_out=None, launch=None, stream=None):
+    """Host-buffer entry point (dls_count_host): prefixes and counts in host
+    memory (numpy or CPU torch tensors; pinned memory makes the copies
+    asynchronous).  Synchronous.  Returns (counts uint64 [P], total int)."""
+    pre = prefixes
+    if hasattr(pre, "numpy"):
+        pre_np = pre.numpy()
+    else:
+        pre_np = np.ascontiguousarray(np.asarray(pre, dtype=np.uint8))
+    if pre_np.ndim != 2:
+        raise ValueError("prefixes must be 2-D")
+    P, depth = pre_np.shape
+    if counts_out is None:
+        counts_out = np.zeros(P, np.uint64)
+    cnt_np = counts_out.numpy() if hasattr(counts_out, "numpy") else counts_out
+    o, op, ol = _order(order)
+    tot = _lib.U128()
+    cfg = (launch or Launch()).c()
+    sh = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+    _lib.check(lib().dls_count_host(n, flags, op, ol,
+                                    ctypes.c_void_p(pre_np.ctypes.data) if P else None,
+                                    depth, P, ctypes.c_void_p(cnt_np.ctypes.data),
+                                    ctypes.byref(tot), ctypes.byref(cfg), sh),
+               "dls_count_host")
+    return counts_out, tot.value()
+
+
+def release():
+    lib().dls_release()
+
+
+class Plan:
+    """One dls_count_ex call frozen into a CUDA graph (dls_plan_*)."""
+
+    def __init__(self, n, flags, order, prefixes, counts, total=None, launch=None):
+        self._keep = (prefixes, counts, total)
+        o, op, ol = _order(order)
+        P, depth = prefixes.shape
+        cfg = (launch or Launch()).c()
+        h = ctypes.c_void_p(0)
+        _lib.check(lib().dls_plan_create(ctypes.byref(h), n, flags, op, ol,
+                                         _dev_ptr(prefixes) if P else None, depth, P,
+                                         _dev_ptr(counts), _dev_ptr(total),
+                                         ctypes.byref(cfg)), "dls_plan_create")
+        self._h = h
+
+    def launch(self, stream=None):
+        _lib.check(lib().dls_plan_launch(self._h, _stream_handle(stream)), "dls_plan_launch")
+
+    def close(self):
+        if self._h:
+            lib().dls_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

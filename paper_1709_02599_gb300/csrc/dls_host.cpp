@@ -1,0 +1,433 @@
+// dls_host.cpp -- host-side part of the C ABI: fill orders, the prefix split,
+// the draw-driven prefix sampler, multipliers, 128-bit helpers, status names.
+//
+// Everything here runs on the CPU and prepares the input of the GPU search
+// (dls_kernels.cu).  The search state is the bitmask form of Section 3: one
+// word per row, column and diagonal holding the values in use, candidates
+// ALL & ~(row | col | md | ad), lowest set bit first (Algorithm 4).
+
+#include "dls_internal.h"
+
+#include <algorithm>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <string>
+#include <vector>
+
+namespace dls {
+
+thread_local std::string g_last_cuda_error;
+
+void set_cuda_error(const char *what) { g_last_cuda_error = what ? what : ""; }
+
+// ------------------------------------------------------------ validation --
+
+int validate_order(int n, uint32_t flags, const uint8_t *order, int order_len,
+                   OrderInfo *info) {
+  if (n < 1 || n > DLS_MAX_N) return DLS_ERR_INVALID_N;
+  if (order_len < 0 || order_len > n * n) return DLS_ERR_BAD_ORDER;
+  if (order_len > 0 && order == nullptr) return DLS_ERR_BAD_ARG;
+  if (flags & ~(DLS_DIAGONAL | DLS_VSYM)) return DLS_ERR_BAD_ARG;
+  bool seen[DLS_MAX_N][DLS_MAX_N] = {};
+  const bool vsym = (flags & DLS_VSYM) != 0;
+  for (int t = 0; t < order_len; ++t) {
+    int i = order[2 * t], j = order[2 * t + 1];
+    if (i >= n || j >= n) return DLS_ERR_BAD_ORDER;
+    if (vsym && j >= n / 2 && n > 1) return DLS_ERR_BAD_ORDER;
+    if (seen[i][j]) return DLS_ERR_BAD_ORDER;
+    seen[i][j] = true;
+    if (info) {
+      info->i[t] = (uint8_t)i;
+      info->j[t] = (uint8_t)j;
+    }
+  }
+  if (vsym && n == 1 && order_len > 0) return DLS_ERR_BAD_ORDER;
+  if (info) {
+    info->n = n;
+    info->flags = flags;
+    info->len = order_len;
+  }
+  return DLS_OK;
+}
+
+bool vsym_all_zero(int n, uint32_t flags) {
+  return (flags & DLS_VSYM) && (n % 2 == 1) && n >= 3;
+}
+
+// Host bitmask search state (Section 3).
+struct HostState {
+  int n;
+  bool diag, vsym;
+  uint32_t all;
+  uint32_t row[DLS_MAX_N], col[DLS_MAX_N], md, ad;
+  const OrderInfo *o;
+
+  void init(const OrderInfo &info) {
+    o = &info;
+    n = info.n;
+    diag = (info.flags & DLS_DIAGONAL) != 0;
+    vsym = (info.flags & DLS_VSYM) != 0;
+    all = (n >= 32) ? 0xffffffffu : ((1u << n) - 1u);
+    // odd order with vertical symmetry: a left cell holding (n-1)/2 would put
+    // the same value in its mirror cell, in the same row
+    if (vsym && (n & 1)) all &= ~(1u << (n / 2));
+    std::memset(row, 0, sizeof(row));
+    std::memset(col, 0, sizeof(col));
+    md = ad = 0;
+  }
+  uint32_t mirror(uint32_t m) const {
+    // bit v -> bit n-1-v
+    uint32_t r = 0;
+    for (int v = 0; v < n; ++v)
+      if (m >> v & 1u) r |= 1u << (n - 1 - v);
+    return r;
+  }
+  bool on_md(int t) const { return diag && o->i[t] == o->j[t]; }
+  bool on_ad(int t) const { return diag && o->i[t] + o->j[t] == n - 1; }
+  uint32_t candidates(int t) const {
+    uint32_t f = row[o->i[t]] | col[o->j[t]];
+    if (on_md(t)) f |= md;
+    if (on_ad(t)) f |= ad;
+    return all & ~f;
+  }
+  // toggle one-hot (or two-hot) value bits d at order position t
+  void toggle(int t, uint32_t d) {
+    uint32_t dm = vsym ? mirror(d) : 0u;
+    row[o->i[t]] ^= d ^ dm;
+    col[o->j[t]] ^= d;
+    if (on_md(t)) md ^= d;
+    if (on_ad(t)) ad ^= d;
+    if (vsym) {
+      if (on_md(t)) ad ^= dm;  // mirror cell (i, n-1-i) is on the anti-diagonal
+      if (on_ad(t)) md ^= dm;  // mirror cell (i, i) is on the main diagonal
+    }
+  }
+  bool place(int t, int value) {
+    if (value < 0 || value >= n) return false;
+    uint32_t b = 1u << value;
+    if (!(candidates(t) & b)) return false;
+    toggle(t, b);
+    return true;
+  }
+};
+
+// ------------------------------------------------------------ fill orders --
+
+static void order_md_ad_rows(int n, bool vsym, int first_rows,
+                             std::vector<std::pair<int, int>> &out) {
+  const int w = vsym ? n / 2 : n;
+  bool used[DLS_MAX_N][DLS_MAX_N] = {};
+  auto add = [&](int i, int j) {
+    if (j >= w || used[i][j]) return;
+    used[i][j] = true;
+    out.push_back({i, j});
+  };
+  for (int i = 0; i < first_rows && i < n; ++i)
+    for (int j = 0; j < w; ++j) add(i, j);
+  for (int i = 0; i < n; ++i) add(i, i);
+  for (int i = 0; i < n; ++i) add(i, n - 1 - i);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < w; ++j) add(i, j);
+}
+
+static void order_hourglass(int n, std::vector<std::pair<int, int>> &out) {
+  bool used[DLS_MAX_N][DLS_MAX_N] = {};
+  auto add = [&](int i, int j) {
+    if (used[i][j]) return;
+    used[i][j] = true;
+    out.push_back({i, j});
+  };
+  for (int j = 0; j < n; ++j) add(0, j);
+  for (int i = 0; i < n; ++i) add(i, i);
+  for (int i = 0; i < n; ++i) add(i, n - 1 - i);
+  for (int j = 0; j < n; ++j) add(n - 1, j);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) add(i, j);
+}
+
+// Section 2.3: after row 0, repeatedly take the unassigned cell with the
+// largest V = r_i + c_j + md(i,j) + ad(i,j) -- the numbers of assigned cells
+// in its row, its column and, when the cell lies on them, the two diagonals
+// -- ties broken by the first cell in row-major order.  Whenever placing a
+// cell leaves exactly one unassigned cell in one of its lines (row, column,
+// main diagonal, anti-diagonal, checked in that order), that cell is queued
+// and taken next, queued cells first-in first-out.  Only which cells are
+// assigned matters, never their values.  This reproduces Fig. 1 for order 9.
+// With vsym the cells are the left half: a row has n/2 of them, a column n,
+// and the two diagonals become one line (the left cells on the main diagonal
+// and those on the anti-diagonal, whose mirrors complete the main diagonal).
+static void order_heuristic(int n, bool diag, bool vsym,
+                            std::vector<std::pair<int, int>> &out) {
+  const int w = vsym ? n / 2 : n;
+  std::vector<std::vector<std::pair<int, int>>> lines;
+  std::vector<std::vector<int>> of_cell(n * w);
+  for (int i = 0; i < n; ++i) {
+    std::vector<std::pair<int, int>> l;
+    for (int j = 0; j < w; ++j) l.push_back({i, j});
+    lines.push_back(l);
+  }
+  for (int j = 0; j < w; ++j) {
+    std::vector<std::pair<int, int>> l;
+    for (int i = 0; i < n; ++i) l.push_back({i, j});
+    lines.push_back(l);
+  }
+  if (diag && !vsym) {
+    std::vector<std::pair<int, int>> m, a;
+    for (int i = 0; i < n; ++i) m.push_back({i, i});
+    for (int i = 0; i < n; ++i) a.push_back({i, n - 1 - i});
+    lines.push_back(m);
+    lines.push_back(a);
+  } else if (diag && vsym) {
+    std::vector<std::pair<int, int>> m;
+    for (int i = 0; i < n; ++i) m.push_back(i < w ? std::make_pair(i, i) : std::make_pair(i, n - 1 - i));
+    lines.push_back(m);
+  }
+  for (int l = 0; l < (int)lines.size(); ++l)
+    for (auto &c : lines[l]) of_cell[c.first * w + c.second].push_back(l);
+  std::vector<int> filled(lines.size(), 0);
+  std::vector<char> asg(n * w, 0);
+  std::deque<std::pair<int, int>> queue;
+  auto assign = [&](int i, int j, bool forced_rule) {
+    asg[i * w + j] = 1;
+    out.push_back({i, j});
+    for (int l : of_cell[i * w + j]) {
+      filled[l]++;
+      if (forced_rule && filled[l] == (int)lines[l].size() - 1)
+        for (auto &c : lines[l])
+          if (!asg[c.first * w + c.second]) queue.push_back(c);
+    }
+  };
+  for (int j = 0; j < w; ++j) assign(0, j, false);
+  const int total = n * w;
+  while ((int)out.size() < total) {
+    std::pair<int, int> cell{-1, -1};
+    while (!queue.empty()) {
+      auto q = queue.front();
+      queue.pop_front();
+      if (!asg[q.first * w + q.second]) {
+        cell = q;
+        break;
+      }
+    }
+    if (cell.first < 0) {
+      int best = -1;
+      for (int i = 0; i < n; ++i)
+        for (int j = 0; j < w; ++j) {
+          if (asg[i * w + j]) continue;
+          int v = 0;
+          for (int l : of_cell[i * w + j]) v += filled[l];
+          if (v > best) {
+            best = v;
+            cell = {i, j};
+          }
+        }
+    }
+    assign(cell.first, cell.second, true);
+  }
+}
+
+}  // namespace dls
+
+using namespace dls;
+
+extern "C" {
+
+const char *dls_strerror(int code) {
+  switch (code) {
+    case DLS_OK: return "ok";
+    case DLS_ERR_INVALID_N: return "order n outside 1..16";
+    case DLS_ERR_BAD_ORDER: return "bad fill order (repeated, out-of-range or right-half cell)";
+    case DLS_ERR_BAD_ARG: return "bad argument";
+    case DLS_ERR_CAPACITY: return "output buffer too small";
+    case DLS_ERR_CUDA: return "CUDA error";
+    case DLS_ERR_TIMEOUT: return "bounded wait or budget ran out";
+    case DLS_ERR_ABORTED: return "aborted";
+    case DLS_ERR_NO_MEMORY: return "out of memory";
+    case DLS_ERR_BAD_STATE: return "object in the wrong state";
+    default: return "unknown status";
+  }
+}
+
+const char *dls_last_cuda_error(void) { return g_last_cuda_error.c_str(); }
+
+int dls_version(void) { return (1 << 16) | 0; }
+
+int dls_fill_order(int n, uint32_t flags, int kind, int first_rows,
+                   uint8_t *ij_out, int cap, int *len_out) {
+  if (n < 1 || n > DLS_MAX_N) return DLS_ERR_INVALID_N;
+  if (len_out == nullptr || cap < 0 || (cap > 0 && ij_out == nullptr))
+    return DLS_ERR_BAD_ARG;
+  if (flags & ~(DLS_DIAGONAL | DLS_VSYM)) return DLS_ERR_BAD_ARG;
+  const bool vsym = (flags & DLS_VSYM) != 0;
+  const bool diag = (flags & DLS_DIAGONAL) != 0;
+  std::vector<std::pair<int, int>> cells;
+  switch (kind) {
+    case DLS_ORDER_MD_AD_ROWS:
+      if (first_rows < 1) first_rows = 1;
+      order_md_ad_rows(n, vsym, first_rows, cells);
+      break;
+    case DLS_ORDER_ROW_MAJOR:
+      for (int i = 0; i < n; ++i)
+        for (int j = 0; j < (vsym ? n / 2 : n); ++j) cells.push_back({i, j});
+      break;
+    case DLS_ORDER_HOURGLASS:
+      if (vsym) return DLS_ERR_BAD_ARG;
+      order_hourglass(n, cells);
+      break;
+    case DLS_ORDER_HEURISTIC:
+      order_heuristic(n, diag, vsym, cells);
+      break;
+    default:
+      return DLS_ERR_BAD_ARG;
+  }
+  *len_out = (int)cells.size();
+  if ((int)cells.size() > cap) return DLS_ERR_CAPACITY;
+  for (size_t t = 0; t < cells.size(); ++t) {
+    ij_out[2 * t] = (uint8_t)cells[t].first;
+    ij_out[2 * t + 1] = (uint8_t)cells[t].second;
+  }
+  return DLS_OK;
+}
+
+int dls_extend_prefixes(int n, uint32_t flags, const uint8_t *order,
+                        int order_len, const uint8_t *base, int base_depth,
+                        int64_t n_base, int depth, uint8_t *out, int64_t cap,
+                        int64_t *parents_out, int64_t *n_out) {
+  OrderInfo info;
+  int rc = validate_order(n, flags, order, order_len, &info);
+  if (rc) return rc;
+  if (n_out == nullptr || n_base < 0 || cap < 0 || base_depth < 0 ||
+      depth < base_depth || depth > order_len)
+    return DLS_ERR_BAD_ARG;
+  if ((n_base > 0 && base_depth > 0 && base == nullptr) ||
+      (cap > 0 && depth > 0 && out == nullptr))
+    return DLS_ERR_BAD_ARG;
+  *n_out = 0;
+  if (vsym_all_zero(n, flags)) return DLS_OK;
+  int64_t produced = 0;
+  HostState s;
+  uint32_t L[DLS_MAX_CELLS + 1];
+  uint32_t cur[DLS_MAX_CELLS + 1];
+  uint8_t vals[DLS_MAX_CELLS];
+  for (int64_t b = 0; b < n_base; ++b) {
+    s.init(info);
+    bool ok = true;
+    const uint8_t *bp = base + (size_t)b * (size_t)base_depth;
+    for (int t = 0; t < base_depth && ok; ++t) {
+      ok = s.place(t, bp[t]);
+      vals[t] = bp[t];
+    }
+    if (!ok) continue;
+    if (depth == base_depth) {
+      if (produced < cap) {
+        if (depth) std::memcpy(out + (size_t)produced * depth, vals, depth);
+        if (parents_out) parents_out[produced] = b;
+      }
+      produced++;
+      continue;
+    }
+    // iterative DFS over positions base_depth..depth-1 (Algorithm 4)
+    int t = base_depth;
+    L[t] = s.candidates(t);
+    cur[t] = 0;
+    while (t >= base_depth) {
+      if (cur[t]) {
+        s.toggle(t, cur[t]);
+        cur[t] = 0;
+      }
+      if (L[t] == 0) {
+        --t;
+        continue;
+      }
+      uint32_t v = L[t] & (0u - L[t]);
+      L[t] &= L[t] - 1u;
+      s.toggle(t, v);
+      cur[t] = v;
+      vals[t] = (uint8_t)__builtin_ctz(v);
+      if (t + 1 == depth) {
+        if (produced < cap) {
+          std::memcpy(out + (size_t)produced * depth, vals, depth);
+          if (parents_out) parents_out[produced] = b;
+        }
+        produced++;
+        continue;
+      }
+      ++t;
+      L[t] = s.candidates(t);
+      cur[t] = 0;
+    }
+  }
+  *n_out = produced;
+  return produced > cap ? DLS_ERR_CAPACITY : DLS_OK;
+}
+
+int dls_sample_prefix(int n, uint32_t flags, const uint8_t *order,
+                      int order_len, int depth, const uint32_t *draws,
+                      int64_t n_draws, uint8_t *out, int64_t *draws_used) {
+  OrderInfo info;
+  int rc = validate_order(n, flags, order, order_len, &info);
+  if (rc) return rc;
+  if (depth < 0 || depth > order_len || n_draws < 0 ||
+      (depth > 0 && out == nullptr) || (n_draws > 0 && draws == nullptr))
+    return DLS_ERR_BAD_ARG;
+  if (draws_used) *draws_used = 0;
+  HostState s;
+  s.init(info);
+  uint32_t placed[DLS_MAX_CELLS];
+  int64_t used = 0;
+  int t = 0;
+  while (t < depth) {
+    uint32_t cand = s.candidates(t);
+    if (cand == 0) {
+      int r = t;
+      while (r > 0 && info.i[r - 1] == info.i[t]) --r;
+      for (int u = t - 1; u >= r; --u) s.toggle(u, placed[u]);
+      t = r;
+      continue;
+    }
+    if (used >= n_draws) return DLS_ERR_CAPACITY;
+    int k = (int)(draws[used++] % (uint32_t)__builtin_popcount(cand));
+    uint32_t v = cand;
+    for (int q = 0; q < k; ++q) v &= v - 1u;
+    v &= 0u - v;
+    s.toggle(t, v);
+    placed[t] = v;
+    out[t] = (uint8_t)__builtin_ctz(v);
+    ++t;
+  }
+  if (draws_used) *draws_used = used;
+  return DLS_OK;
+}
+
+dls_u128 dls_mul_u64(uint64_t a, dls_u128 b) {
+  unsigned __int128 lo = (unsigned __int128)a * b.lo;
+  unsigned __int128 hi = (unsigned __int128)a * b.hi;
+  dls_u128 r;
+  r.lo = (uint64_t)lo;
+  r.hi = (uint64_t)(lo >> 64) + (uint64_t)hi;
+  return r;
+}
+
+dls_u128 dls_add_u128(dls_u128 a, dls_u128 b) {
+  dls_u128 r;
+  r.lo = a.lo + b.lo;
+  r.hi = a.hi + b.hi + (r.lo < a.lo ? 1u : 0u);
+  return r;
+}
+
+dls_u128 dls_multiplier(int n, uint32_t flags) {
+  dls_u128 m = {1, 0};
+  if (n < 1 || n > DLS_MAX_N) return dls_u128{0, 0};
+  if (flags & DLS_VSYM) {
+    if (n % 2 == 1) return m;
+    int h = n / 2;
+    for (int k = 2; k <= h; ++k) m = dls_mul_u64((uint64_t)k, m);
+    for (int k = 0; k < h; ++k) m = dls_mul_u64(2u, m);
+    return m;
+  }
+  for (int k = 2; k <= n; ++k) m = dls_mul_u64((uint64_t)k, m);
+  return m;
+}
+
+}  // extern "C"

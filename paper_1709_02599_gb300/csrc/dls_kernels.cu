@@ -1,0 +1,869 @@
+// dls_kernels.cu -- the GPU search (Algorithm 4 of the paper on sm_103a) and
+// the C-ABI entry points that launch it.
+//
+// One lane runs one depth-first search over the order positions after its
+// prefix.  Its state is the bitmask form of Section 3 -- a word per row and
+// per column holding the values in use, plus the two diagonal words md/ad --
+// and a stack of (remaining candidates, placed value) per position, i.e. the
+// L[i][j] / LS[i][j] pairs of Algorithm 4 kept as an explicit stack instead of
+// nested loops.  Row/column words and the stack live in shared memory in a
+// thread-minor layout (word w of thread t at w * blockDim + t), so a warp's
+// accesses hit 32 distinct banks whatever positions its lanes are at; the
+// diagonal words, the current position's candidates and value stay in
+// registers.
+//
+// One iteration of a lane:
+//   nv = lowest bit of L        (Algorithm 4: LS = L & -L)
+//   d  = v ^ nv                 (take the old value out, put the new one in,
+//                                the two XOR steps of Algorithm 4 fused)
+//   row ^= d (and its mirror for vertically symmetric squares), col ^= d,
+//   md/ad ^= d when the cell lies on them
+//   nv == 0: the loop of this cell is exhausted -> pop to the previous one
+//   else:    candidates of the next cell ALL & ~(row|col|md|ad); at the last
+//            cell add popcount (each admissible value completes a square,
+//            Algorithm 1's innermost loop), an empty set is a dead end, else
+//            push and descend.
+//
+// Kernels:
+//   k_plain      -- one thread per work item, the comparison baseline.
+//   k_persistent -- a resident grid; warps take work items from a global
+//                   atomic queue as lanes go idle, and once the queue is empty
+//                   idle lanes take the shallowest untried subtree of a busy
+//                   lane in the same warp (ballot + shuffle + shared memory).
+//   Both keep per-lane totals, reduce them per block in shared memory and add
+//   one 64-bit atomic per block to the global total.
+//
+// Work items: prefix p is split into `lanes` items (p, s); item s keeps the
+// nodes at order position split_pos whose index in depth-first order is
+// s mod lanes (all items walk the few positions above split_pos).
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <utility>
+#include <vector>
+
+#include "dls_internal.h"
+
+namespace dls {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+struct KParams {
+  int n;
+  uint32_t all;          // (1 << n) - 1
+  int order_len;
+  int depth;             // prefix length
+  int last;              // order_len - 1
+  int lanes_log2;        // work items per prefix = 1 << lanes_log2
+  int split_pos;         // order position of the item split (-1 = none)
+  int check_mask;        // donation check period - 1
+  int donate;
+  int count_store;       // 1: counts[p] = cnt (one item per prefix, no donation)
+  long long n_prefixes;
+  long long n_items;
+  const uint8_t *prefixes;
+  unsigned long long *counts;
+  unsigned long long *total;
+  unsigned long long *nodes;
+  unsigned long long *queue;
+  uint8_t ci[DLS_MAX_CELLS];
+  uint8_t cj[DLS_MAX_CELLS];
+};
+
+// Per-lane search state kept in registers.
+struct Lane {
+  int p;                 // current order position
+  uint32_t L;            // untried candidates at p
+  uint32_t v;            // value placed at p (one-hot), 0 = none yet
+  uint32_t info;         // cell descriptor of p (see cell_info)
+  uint32_t md, ad;       // diagonal words
+  uint32_t splitc;       // nodes met at split_pos so far
+  uint32_t sub;          // residue class of split nodes this item keeps
+  long long prefix;      // prefix index of the current item
+  unsigned long long cnt;    // completions found for the current item
+  unsigned long long nodes;  // placements made (node counting variant)
+};
+
+// Cell descriptor: byte offsets (from the lane's first state word) of the
+// row word and of the column word, with the main-diagonal flag in bit 0 and
+// the anti-diagonal flag in bit 16.
+__device__ __forceinline__ uint32_t cell_info(const KParams &p, int pos,
+                                              int diag, unsigned B) {
+  const int i = p.ci[pos], j = p.cj[pos];
+  const uint32_t roff = (uint32_t)i * B * 4u;
+  const uint32_t coff = (uint32_t)(p.n + j) * B * 4u;
+  const uint32_t md = (diag && i == j) ? 1u : 0u;
+  const uint32_t ad = (diag && i + j == p.n - 1) ? 1u : 0u;
+  return roff | md | ((coff | ad) << 16);
+}
+
+__device__ __forceinline__ uint32_t &word_at(char *tb, uint32_t off) {
+  return *reinterpret_cast<uint32_t *>(tb + off);
+}
+
+template <bool VSYM>
+__device__ __forceinline__ uint32_t mirror(uint32_t d, int n) {
+  return VSYM ? (__brev(d) >> (32 - n)) : 0u;
+}
+
+// Admissible values of the cell described by `info`.
+__device__ __forceinline__ uint32_t cands(char *tb, uint32_t info, uint32_t md,
+                                          uint32_t ad, uint32_t all) {
+  uint32_t f = word_at(tb, info & 0xfffcu) | word_at(tb, (info >> 16) & 0xfffcu);
+  f |= (info & 1u) ? md : 0u;
+  f |= (info & 0x10000u) ? ad : 0u;
+  return all & ~f;
+}
+
+// XOR value bits d into the words of the cell described by `info`.
+template <bool VSYM>
+__device__ __forceinline__ void toggle(char *tb, uint32_t info, uint32_t d,
+                                       uint32_t &md, uint32_t &ad, int n) {
+  const uint32_t dm = mirror<VSYM>(d, n);
+  word_at(tb, info & 0xfffcu) ^= d ^ dm;
+  word_at(tb, (info >> 16) & 0xfffcu) ^= d;
+  const bool onmd = (info & 1u) != 0, onad = (info & 0x10000u) != 0;
+  // with vertical symmetry the mirror of a main-diagonal cell is on the
+  // anti-diagonal and vice versa
+  md ^= (onmd ? d : 0u) ^ ((VSYM && onad) ? dm : 0u);
+  ad ^= (onad ? d : 0u) ^ ((VSYM && onmd) ? dm : 0u);
+}
+
+// One search iteration.  Returns true when the lane's item is finished.
+template <bool VSYM, bool NODES>
+__device__ __forceinline__ bool dfs_step(Lane &s, const KParams &p, char *tb,
+                                         uint32_t *stk, const uint32_t *tbl,
+                                         int lane, unsigned B) {
+  const uint32_t nv = s.L & (0u - s.L);
+  toggle<VSYM>(tb, s.info, s.v ^ nv, s.md, s.ad, p.n);
+  s.L ^= nv;
+  s.v = nv;
+  if (nv == 0u) {
+    if (--s.p < p.depth) return true;
+    const uint32_t w = stk[(s.p - p.depth) * B];
+    s.L = w & 0xffffu;
+    s.v = w >> 16;
+    s.info = tbl[s.p * 32 + lane];
+    return false;
+  }
+  if (s.p == p.split_pos) {
+    const uint32_t c = s.splitc++;
+    if ((c & ((1u << p.lanes_log2) - 1u)) != s.sub) return false;
+    if (NODES) s.nodes++;
+  } else if (NODES) {
+    if (s.p > p.split_pos || s.sub == 0u) s.nodes++;
+  }
+  const int q = s.p + 1;
+  const uint32_t info1 = tbl[q * 32 + lane];
+  const uint32_t L1 = cands(tb, info1, s.md, s.ad, p.all);
+  if (q == p.last) {
+    s.cnt += (unsigned)__popc(L1);
+    if (NODES) s.nodes += (unsigned)__popc(L1);
+    return false;
+  }
+  if (L1 == 0u) return false;
+  stk[(s.p - p.depth) * B] = s.L | (s.v << 16);
+  s.p = q;
+  s.L = L1;
+  s.v = 0u;
+  s.info = info1;
+  return false;
+}
+
+// Load work item `item` into the lane.  Returns true if it is already
+// finished (invalid prefix, or nothing left to search).
+template <bool VSYM, bool NODES>
+__device__ bool load_item(Lane &s, const KParams &p, long long item, char *tb,
+                          const uint32_t *tbl, int lane, unsigned B) {
+  s.prefix = item >> p.lanes_log2;
+  s.sub = (uint32_t)(item & ((1ll << p.lanes_log2) - 1));
+  s.cnt = 0ull;
+  s.splitc = 0u;
+  s.md = s.ad = 0u;
+  for (int w = 0; w < 2 * p.n; ++w) word_at(tb, (uint32_t)w * B * 4u) = 0u;
+  const uint8_t *rec = p.prefixes + (size_t)s.prefix * (size_t)p.depth;
+  for (int t = 0; t < p.depth; ++t) {
+    const uint32_t val = rec[t];
+    const uint32_t info = tbl[t * 32 + lane];
+    const uint32_t b = (val < (uint32_t)p.n) ? (1u << val) : 0u;
+    if ((cands(tb, info, s.md, s.ad, p.all) & b) == 0u) return true;
+    toggle<VSYM>(tb, info, b, s.md, s.ad, p.n);
+  }
+  if (p.depth == p.order_len) {
+    s.cnt = (s.sub == 0u) ? 1ull : 0ull;
+    return true;
+  }
+  const uint32_t info = tbl[p.depth * 32 + lane];
+  const uint32_t L = cands(tb, info, s.md, s.ad, p.all);
+  if (p.depth == p.last) {
+    if (s.sub == 0u) {
+      s.cnt = (unsigned)__popc(L);
+      if (NODES) s.nodes += (unsigned)__popc(L);
+    }
+    return true;
+  }
+  s.p = p.depth;
+  s.L = L;
+  s.v = 0u;
+  s.info = info;
+  return L == 0u;
+}
+
+__device__ __forceinline__ void flush_item(const Lane &s, const KParams &p,
+                                           unsigned long long &lane_total) {
+  lane_total += s.cnt;
+  if (p.counts != nullptr) {
+    if (p.count_store)
+      p.counts[s.prefix] = s.cnt;
+    else if (s.cnt)
+      atomicAdd(p.counts + s.prefix, s.cnt);
+  }
+}
+
+// Per-block reduction of the lane totals, one global atomic per block.
+__device__ void block_reduce_add(unsigned long long v, unsigned long long *dst,
+                                 unsigned long long *red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long s = 0ull;
+    for (unsigned w = 0; w < (blockDim.x >> 5); ++w) s += red[w];
+    if (dst != nullptr && s) atomicAdd(dst, s);
+  }
+}
+
+// Shared memory: [table: order_len * 32 words][state: (2n + stack) * B words]
+__device__ __forceinline__ void build_table(const KParams &p, uint32_t *tbl,
+                                            int diag) {
+  const unsigned B = blockDim.x;
+  for (int idx = threadIdx.x; idx < p.order_len * 32; idx += B)
+    tbl[idx] = cell_info(p, idx >> 5, diag, B);
+}
+
+template <bool VSYM, bool NODES>
+__global__ void __launch_bounds__(512) k_plain(const __grid_constant__ KParams p,
+                                               int diag) {
+  extern __shared__ uint32_t smem[];
+  __shared__ unsigned long long red[16];
+  const unsigned B = blockDim.x;
+  const int lane = threadIdx.x & 31;
+  uint32_t *tbl = smem;
+  uint32_t *st = smem + p.order_len * 32;
+  build_table(p, tbl, diag);
+  __syncthreads();
+  char *tb = reinterpret_cast<char *>(st + threadIdx.x);
+  uint32_t *stk = st + 2 * p.n * B + threadIdx.x;
+
+  Lane s;
+  s.nodes = 0ull;
+  unsigned long long lane_total = 0ull;
+  const long long item = (long long)blockIdx.x * B + threadIdx.x;
+  bool busy = false;
+  if (item < p.n_items) {
+    busy = !load_item<VSYM, NODES>(s, p, item, tb, tbl, lane, B);
+    if (!busy) flush_item(s, p, lane_total);
+  }
+  while (__any_sync(FULL, busy)) {
+    if (busy && dfs_step<VSYM, NODES>(s, p, tb, stk, tbl, lane, B)) {
+      busy = false;
+      flush_item(s, p, lane_total);
+    }
+  }
+  block_reduce_add(lane_total, p.total, red);
+  if (NODES) block_reduce_add(s.nodes, p.nodes, red);
+}
+
+// Position of the (r+1)-th set bit of m (r = 0 -> lowest set bit).
+__device__ __forceinline__ int nth_set_bit(unsigned m, int r) {
+  for (int k = 0; k < r; ++k) m &= m - 1u;
+  return __ffs(m) - 1;
+}
+
+// In-warp work donation: each idle lane is paired with a busy lane that has
+// an untried candidate at some position pd (the shallowest such position at
+// or below the item split); the idle lane copies the busy lane's words and
+// path, undoes its placements below pd and takes the untried candidates of
+// pd, which the busy lane gives up.
+template <bool VSYM>
+__device__ void donate(Lane &s, bool &busy, const KParams &p, char *tb,
+                       uint32_t *stk, uint32_t *st, const uint32_t *tbl,
+                       int lane, unsigned B) {
+  const unsigned idle = __ballot_sync(FULL, !busy);
+  if (idle == 0u || idle == FULL) return;
+  const int lo = max(p.depth, p.split_pos + 1);
+  int pd = -1;
+  uint32_t Lpd = 0u, vpd = 0u;
+  if (busy) {
+    for (int q = lo; q < s.p; ++q) {
+      const uint32_t w = stk[(q - p.depth) * B];
+      if (w & 0xffffu) {
+        pd = q;
+        Lpd = w & 0xffffu;
+        vpd = w >> 16;
+        break;
+      }
+    }
+    if (pd < 0 && s.p >= lo && s.L != 0u) {
+      pd = s.p;
+      Lpd = s.L;
+      vpd = s.v;
+    }
+  }
+  const unsigned donors = __ballot_sync(FULL, pd >= 0);
+  if (donors == 0u) return;
+  const int pairs = min(__popc(idle), __popc(donors));
+  const unsigned below = (1u << lane) - 1u;
+  int partner = lane;  // the lane this one reads from (itself if unpaired)
+  bool receiver = false, giver = false;
+  if (!busy) {
+    const int r = __popc(idle & below);
+    if (r < pairs) {
+      partner = nth_set_bit(donors, r);
+      receiver = true;
+    }
+  } else if (pd >= 0) {
+    const int r = __popc(donors & below);
+    giver = r < pairs;
+  }
+  const int d_pd = __shfl_sync(FULL, pd, partner);
+  const uint32_t d_L = __shfl_sync(FULL, Lpd, partner);
+  const uint32_t d_vpd = __shfl_sync(FULL, vpd, partner);
+  const int d_p = __shfl_sync(FULL, s.p, partner);
+  const uint32_t d_v = __shfl_sync(FULL, s.v, partner);
+  const uint32_t d_md = __shfl_sync(FULL, s.md, partner);
+  const uint32_t d_ad = __shfl_sync(FULL, s.ad, partner);
+  const long long d_prefix = __shfl_sync(FULL, s.prefix, partner);
+  const uint32_t d_sub = __shfl_sync(FULL, s.sub, partner);
+  if (receiver) {
+    const int dl = partner - lane;  // donor's thread offset from this one
+    const uint32_t *dst_words = st + (threadIdx.x + dl);
+    uint32_t *my_words = st + threadIdx.x;
+    for (int w = 0; w < 2 * p.n; ++w) my_words[w * B] = dst_words[w * B];
+    const uint32_t *dstk = stk + dl;
+    for (int q = p.depth; q < d_pd; ++q)
+      stk[(q - p.depth) * B] = dstk[(q - p.depth) * B] & 0xffff0000u;
+    s.md = d_md;
+    s.ad = d_ad;
+    // undo the donor's placements below pd
+    for (int q = d_pd + 1; q <= d_p; ++q) {
+      const uint32_t vq = (q < d_p) ? (dstk[(q - p.depth) * B] >> 16) : d_v;
+      if (vq) toggle<VSYM>(tb, tbl[q * 32 + lane], vq, s.md, s.ad, p.n);
+    }
+    s.p = d_pd;
+    s.L = d_L;
+    s.v = d_vpd;
+    s.info = tbl[d_pd * 32 + lane];
+    s.prefix = d_prefix;
+    s.sub = d_sub;
+    s.splitc = 0u;
+    s.cnt = 0ull;
+    busy = true;
+  }
+  __syncwarp();
+  if (giver) {
+    if (pd < s.p)
+      stk[(pd - p.depth) * B] &= 0xffff0000u;
+    else
+      s.L = 0u;
+  }
+  __syncwarp();
+}
+
+template <bool VSYM, bool NODES>
+__global__ void __launch_bounds__(512)
+    k_persistent(const __grid_constant__ KParams p, int diag) {
+  extern __shared__ uint32_t smem[];
+  __shared__ unsigned long long red[16];
+  const unsigned B = blockDim.x;
+  const int lane = threadIdx.x & 31;
+  uint32_t *tbl = smem;
+  uint32_t *st = smem + p.order_len * 32;
+  build_table(p, tbl, diag);
+  __syncthreads();
+  char *tb = reinterpret_cast<char *>(st + threadIdx.x);
+  uint32_t *stk = st + 2 * p.n * B + threadIdx.x;
+
+  Lane s;
+  s.nodes = 0ull;
+  s.prefix = 0;
+  s.sub = 0u;
+  s.p = 0;
+  s.L = s.v = s.md = s.ad = 0u;
+  unsigned long long lane_total = 0ull;
+  bool busy = false;
+  bool qdone = false;
+
+  for (;;) {
+    // hand queue items to idle lanes, one atomic per warp
+    unsigned idle = __ballot_sync(FULL, !busy);
+    while (idle != 0u && !qdone) {
+      const int nidle = __popc(idle);
+      unsigned long long base = 0ull;
+      if (lane == 0) base = atomicAdd(p.queue, (unsigned long long)nidle);
+      base = __shfl_sync(FULL, base, 0);
+      if (!busy) {
+        const long long item = (long long)base + __popc(idle & ((1u << lane) - 1u));
+        if (item < p.n_items) {
+          busy = !load_item<VSYM, NODES>(s, p, item, tb, tbl, lane, B);
+          if (!busy) flush_item(s, p, lane_total);
+        }
+      }
+      if ((long long)(base + (unsigned long long)nidle) >= p.n_items) qdone = true;
+      idle = __ballot_sync(FULL, !busy);
+    }
+    if (idle == FULL) break;  // queue drained and every lane idle
+    if (!qdone) {
+      // run until some lane finishes its item
+      do {
+        if (busy && dfs_step<VSYM, NODES>(s, p, tb, stk, tbl, lane, B)) {
+          busy = false;
+          flush_item(s, p, lane_total);
+        }
+      } while (__all_sync(FULL, busy));
+    } else {
+      for (int it = 0; it <= p.check_mask; ++it) {
+        if (busy && dfs_step<VSYM, NODES>(s, p, tb, stk, tbl, lane, B)) {
+          busy = false;
+          flush_item(s, p, lane_total);
+        }
+      }
+      if (p.donate) donate<VSYM>(s, busy, p, tb, stk, st, tbl, lane, B);
+    }
+  }
+  block_reduce_add(lane_total, p.total, red);
+  if (NODES) block_reduce_add(s.nodes, p.nodes, red);
+}
+
+// ------------------------------------------------------------ host side --
+
+struct Workspace {
+  unsigned long long *scratch = nullptr;  // [0] queue head
+  uint8_t *h2d = nullptr;                 // host-entry prefix buffer
+  size_t h2d_bytes = 0;
+  unsigned long long *d2h = nullptr;      // host-entry counts buffer
+  size_t d2h_count = 0;
+};
+
+static std::mutex g_ws_mutex;
+static std::map<std::pair<int, cudaStream_t>, Workspace> g_ws;
+
+static int cuda_fail(cudaError_t e) {
+  set_cuda_error(cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? DLS_ERR_NO_MEMORY : DLS_ERR_CUDA;
+}
+
+static int get_workspace(cudaStream_t stream, Workspace **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e);
+  std::lock_guard<std::mutex> g(g_ws_mutex);
+  Workspace &w = g_ws[{dev, stream}];
+  if (w.scratch == nullptr) {
+    e = cudaMalloc(&w.scratch, 256);
+    if (e != cudaSuccess) {
+      w.scratch = nullptr;
+      return cuda_fail(e);
+    }
+  }
+  *out = &w;
+  return DLS_OK;
+}
+
+struct DevInfo {
+  int sms = 0;
+  size_t smem_optin = 0;
+};
+
+static int dev_info(DevInfo *d) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e);
+  static std::mutex m;
+  static std::map<int, DevInfo> cache;
+  std::lock_guard<std::mutex> g(m);
+  auto it = cache.find(dev);
+  if (it == cache.end()) {
+    DevInfo di;
+    int v = 0;
+    e = cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    di.sms = v;
+    e = cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    di.smem_optin = (size_t)v;
+    it = cache.emplace(dev, di).first;
+  }
+  *d = it->second;
+  return DLS_OK;
+}
+
+static int ilog2_exact(int x) {
+  int r = 0;
+  while ((1 << r) < x) ++r;
+  return ((1 << r) == x) ? r : -1;
+}
+
+// Resolved launch shape.
+struct Shape {
+  int kernel;
+  int block;
+  int blocks_per_sm;
+  int lanes_log2;
+  int split_pos;
+  int donate;
+  int check_mask;
+};
+
+static int resolve_shape(const dls_launch_t *cfg, int depth, int last,
+                         Shape *sh) {
+  dls_launch_t c;
+  std::memset(&c, 0, sizeof(c));
+  if (cfg) c = *cfg;
+  sh->kernel = c.kernel;
+  if (sh->kernel != DLS_KERNEL_PERSISTENT && sh->kernel != DLS_KERNEL_PLAIN)
+    return DLS_ERR_BAD_ARG;
+  sh->block = c.block_threads ? c.block_threads : 128;
+  if (sh->block < 32 || sh->block > 512 || sh->block % 32) return DLS_ERR_BAD_ARG;
+  sh->blocks_per_sm = c.blocks_per_sm;
+  if (sh->blocks_per_sm < 0) return DLS_ERR_BAD_ARG;
+  int lanes = c.lanes_per_prefix ? c.lanes_per_prefix : 1;
+  sh->lanes_log2 = ilog2_exact(lanes);
+  if (sh->lanes_log2 < 0 || lanes > 32) return DLS_ERR_BAD_ARG;
+  // the split needs a position with a stack entry below it
+  if (depth >= last) sh->lanes_log2 = 0;
+  if (sh->lanes_log2 > 0) {
+    int sp = c.split_pos ? c.split_pos : std::min(depth + 2, last - 1);
+    if (sp < depth || sp > last - 1) return DLS_ERR_BAD_ARG;
+    sh->split_pos = sp;
+  } else {
+    sh->split_pos = -1;
+  }
+  sh->donate = (c.donate >= 0) ? 1 : 0;
+  int every = c.check_every ? c.check_every : 64;
+  if (ilog2_exact(every) < 0) return DLS_ERR_BAD_ARG;
+  sh->check_mask = every - 1;
+  return DLS_OK;
+}
+
+template <bool VSYM, bool NODES>
+static const void *kernel_ptr(int kind) {
+  return kind == DLS_KERNEL_PLAIN ? (const void *)k_plain<VSYM, NODES>
+                                  : (const void *)k_persistent<VSYM, NODES>;
+}
+
+static const void *pick_kernel(int kind, bool vsym, bool nodes) {
+  if (vsym) return nodes ? kernel_ptr<true, true>(kind) : kernel_ptr<true, false>(kind);
+  return nodes ? kernel_ptr<false, true>(kind) : kernel_ptr<false, false>(kind);
+}
+
+static size_t smem_bytes(int order_len, int n, int depth, int last, int block) {
+  const int stack = std::max(0, last - depth);
+  return (size_t)order_len * 32u * 4u + (size_t)(2 * n + stack) * block * 4u;
+}
+
+// Validates, fills the parameter block and enqueues the whole pass on
+// `stream`: zero the outputs, reset the queue, launch.
+static int enqueue_count(int n, uint32_t flags, const uint8_t *order,
+                         int order_len, const uint8_t *d_prefixes, int depth,
+                         int64_t n_prefixes, uint64_t *d_counts,
+                         uint64_t *d_total, uint64_t *d_nodes,
+                         const dls_launch_t *cfg, cudaStream_t stream,
+                         unsigned long long *scratch = nullptr) {
+  OrderInfo info;
+  int rc = validate_order(n, flags, order, order_len, &info);
+  if (rc) return rc;
+  if (depth < 0 || depth > order_len || n_prefixes < 0) return DLS_ERR_BAD_ARG;
+  if (n_prefixes > 0 && d_counts == nullptr && d_total == nullptr) return DLS_ERR_BAD_ARG;
+  if (n_prefixes > 0 && depth > 0 && d_prefixes == nullptr) return DLS_ERR_BAD_ARG;
+  Shape sh;
+  rc = resolve_shape(cfg, depth, order_len - 1, &sh);
+  if (rc) return rc;
+
+  cudaError_t e;
+  if (d_total) {
+    e = cudaMemsetAsync(d_total, 0, sizeof(uint64_t), stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  if (d_nodes) {
+    e = cudaMemsetAsync(d_nodes, 0, sizeof(uint64_t), stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  const bool zero_all = vsym_all_zero(n, flags);
+  const bool store = sh.kernel == DLS_KERNEL_PLAIN && sh.lanes_log2 == 0;
+  if (d_counts && n_prefixes > 0 && (!store || zero_all)) {
+    e = cudaMemsetAsync(d_counts, 0, (size_t)n_prefixes * sizeof(uint64_t), stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  if (n_prefixes == 0 || zero_all) return DLS_OK;
+
+  KParams kp;
+  std::memset(&kp, 0, sizeof(kp));
+  kp.n = n;
+  kp.all = (1u << n) - 1u;
+  kp.order_len = order_len;
+  kp.depth = depth;
+  kp.last = order_len - 1;
+  kp.lanes_log2 = sh.lanes_log2;
+  kp.split_pos = sh.split_pos;
+  kp.check_mask = sh.check_mask;
+  kp.donate = sh.donate;
+  kp.count_store = store ? 1 : 0;
+  kp.n_prefixes = n_prefixes;
+  kp.n_items = n_prefixes << sh.lanes_log2;
+  kp.prefixes = d_prefixes;
+  kp.counts = reinterpret_cast<unsigned long long *>(d_counts);
+  kp.total = reinterpret_cast<unsigned long long *>(d_total);
+  kp.nodes = reinterpret_cast<unsigned long long *>(d_nodes);
+  for (int t = 0; t < order_len; ++t) {
+    kp.ci[t] = info.i[t];
+    kp.cj[t] = info.j[t];
+  }
+  const int diag = (flags & DLS_DIAGONAL) ? 1 : 0;
+  const bool vsym = (flags & DLS_VSYM) != 0;
+  const void *fn = pick_kernel(sh.kernel, vsym, d_nodes != nullptr);
+  DevInfo di;
+  rc = dev_info(&di);
+  if (rc) return rc;
+  // static shared memory of the kernels: the 16-entry reduction buffer
+  const size_t static_smem = 16 * sizeof(unsigned long long);
+  size_t smem = smem_bytes(order_len, n, depth, order_len - 1, sh.block);
+  const bool default_block = cfg == nullptr || cfg->block_threads == 0;
+  while (default_block && smem + static_smem > di.smem_optin && sh.block > 32) {
+    sh.block /= 2;
+    smem = smem_bytes(order_len, n, depth, order_len - 1, sh.block);
+  }
+  if (smem + static_smem > di.smem_optin) return DLS_ERR_NO_MEMORY;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_fail(e);
+
+  unsigned grid;
+  if (sh.kernel == DLS_KERNEL_PLAIN) {
+    long long g = (kp.n_items + sh.block - 1) / sh.block;
+    if (g > 0x7fffffffll) return DLS_ERR_BAD_ARG;
+    grid = (unsigned)g;
+  } else {
+    if (scratch == nullptr) {
+      Workspace *ws = nullptr;
+      rc = get_workspace(stream, &ws);
+      if (rc) return rc;
+      scratch = ws->scratch;
+    }
+    kp.queue = scratch;
+    e = cudaMemsetAsync(scratch, 0, sizeof(unsigned long long), stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    int per_sm = sh.blocks_per_sm;
+    if (per_sm == 0) {
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, sh.block, smem);
+      if (e != cudaSuccess) return cuda_fail(e);
+      if (per_sm < 1) return DLS_ERR_NO_MEMORY;
+    }
+    long long want = (long long)di.sms * per_sm;
+    long long need = (kp.n_items + 31) / 32;  // warps with at least one item
+    long long blocks_needed = (need * 32 + sh.block - 1) / sh.block;
+    grid = (unsigned)std::max(1ll, std::min(want, blocks_needed));
+  }
+  void *args[] = {&kp, (void *)&diag};
+  e = cudaLaunchKernel(fn, dim3(grid), dim3(sh.block), args, smem, stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  return DLS_OK;
+}
+
+}  // namespace dls
+
+using namespace dls;
+
+extern "C" {
+
+int dls_count_ex(int n, uint32_t flags, const uint8_t *order, int order_len,
+                 const uint8_t *d_prefixes, int depth, int64_t n_prefixes,
+                 uint64_t *d_counts, uint64_t *d_total, uint64_t *d_nodes,
+                 const dls_launch_t *cfg, void *stream) {
+  return enqueue_count(n, flags, order, order_len, d_prefixes, depth, n_prefixes,
+                       d_counts, d_total, d_nodes, cfg,
+                       reinterpret_cast<cudaStream_t>(stream));
+}
+
+int dls_count(int n, uint32_t flags, const uint8_t *order, int order_len,
+              const uint8_t *d_prefixes, int depth, int64_t n_prefixes,
+              uint64_t *d_counts, uint64_t *d_total, void *stream) {
+  dls_launch_t cfg;
+  std::memset(&cfg, 0, sizeof(cfg));
+  cfg.kernel = DLS_KERNEL_PERSISTENT;
+  return dls_count_ex(n, flags, order, order_len, d_prefixes, depth, n_prefixes,
+                      d_counts, d_total, nullptr, &cfg, stream);
+}
+
+int dls_count_plain(int n, uint32_t flags, const uint8_t *order,
+                    int order_len, const uint8_t *d_prefixes, int depth,
+                    int64_t n_prefixes, uint64_t *d_counts, uint64_t *d_total,
+                    void *stream) {
+  dls_launch_t cfg;
+  std::memset(&cfg, 0, sizeof(cfg));
+  cfg.kernel = DLS_KERNEL_PLAIN;
+  return dls_count_ex(n, flags, order, order_len, d_prefixes, depth, n_prefixes,
+                      d_counts, d_total, nullptr, &cfg, stream);
+}
+
+int dls_count_host(int n, uint32_t flags, const uint8_t *order,
+                   int order_len, const uint8_t *h_prefixes, int depth,
+                   int64_t n_prefixes, uint64_t *h_counts,
+                   dls_u128 *total_out, const dls_launch_t *cfg,
+                   void *stream) {
+  if (n_prefixes < 0 || depth < 0) return DLS_ERR_BAD_ARG;
+  if (n_prefixes > 0 && depth > 0 && h_prefixes == nullptr) return DLS_ERR_BAD_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Workspace *ws = nullptr;
+  int rc = get_workspace(st, &ws);
+  if (rc) return rc;
+  const size_t in_bytes = (size_t)n_prefixes * (size_t)depth;
+  const size_t n_cnt = (size_t)n_prefixes;
+  cudaError_t e;
+  {
+    std::lock_guard<std::mutex> g(g_ws_mutex);
+    if (ws->h2d_bytes < in_bytes) {
+      if (ws->h2d) cudaFree(ws->h2d);
+      ws->h2d = nullptr;
+      ws->h2d_bytes = 0;
+      e = cudaMalloc(&ws->h2d, in_bytes);
+      if (e != cudaSuccess) return cuda_fail(e);
+      ws->h2d_bytes = in_bytes;
+    }
+    if (ws->d2h_count < n_cnt + 1) {
+      if (ws->d2h) cudaFree(ws->d2h);
+      ws->d2h = nullptr;
+      ws->d2h_count = 0;
+      e = cudaMalloc(&ws->d2h, (n_cnt + 1) * sizeof(unsigned long long));
+      if (e != cudaSuccess) return cuda_fail(e);
+      ws->d2h_count = n_cnt + 1;
+    }
+  }
+  if (in_bytes) {
+    e = cudaMemcpyAsync(ws->h2d, h_prefixes, in_bytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  uint64_t *d_counts = reinterpret_cast<uint64_t *>(ws->d2h);
+  rc = enqueue_count(n, flags, order, order_len, ws->h2d, depth, n_prefixes,
+                     d_counts, nullptr, nullptr, cfg, st);
+  if (rc) return rc;
+  if (h_counts && n_cnt) {
+    e = cudaMemcpyAsync(h_counts, d_counts, n_cnt * sizeof(uint64_t),
+                        cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (total_out) {
+    dls_u128 t = {0, 0};
+    if (h_counts) {
+      for (size_t k = 0; k < n_cnt; ++k) t = dls_add_u128(t, dls_u128{h_counts[k], 0});
+    } else {
+      std::vector<uint64_t> tmp(n_cnt);
+      if (n_cnt) {
+        e = cudaMemcpy(tmp.data(), d_counts, n_cnt * sizeof(uint64_t), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e);
+      }
+      for (size_t k = 0; k < n_cnt; ++k) t = dls_add_u128(t, dls_u128{tmp[k], 0});
+    }
+    *total_out = t;
+  }
+  return DLS_OK;
+}
+
+void dls_release(void) {
+  std::lock_guard<std::mutex> g(g_ws_mutex);
+  for (auto &kv : g_ws) {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(kv.first.first);
+    if (kv.second.scratch) cudaFree(kv.second.scratch);
+    if (kv.second.h2d) cudaFree(kv.second.h2d);
+    if (kv.second.d2h) cudaFree(kv.second.d2h);
+    cudaSetDevice(cur);
+  }
+  g_ws.clear();
+}
+
+// ------------------------------------------------------------------ plans
+
+}  // extern "C"
+
+struct dls_plan {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t capture = nullptr;
+  unsigned long long *scratch = nullptr;  // the plan's own queue head
+};
+
+extern "C" {
+
+int dls_plan_create(dls_plan **plan_out, int n, uint32_t flags,
+                    const uint8_t *order, int order_len,
+                    const uint8_t *d_prefixes, int depth, int64_t n_prefixes,
+                    uint64_t *d_counts, uint64_t *d_total,
+                    const dls_launch_t *cfg) {
+  if (plan_out == nullptr) return DLS_ERR_BAD_ARG;
+  *plan_out = nullptr;
+  dls_plan *pl = new (std::nothrow) dls_plan();
+  if (!pl) return DLS_ERR_NO_MEMORY;
+  cudaError_t e = cudaStreamCreateWithFlags(&pl->capture, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    delete pl;
+    return cuda_fail(e);
+  }
+  // the plan's own work area, allocated before capture (no allocation while
+  // capturing)
+  int rc = DLS_OK;
+  e = cudaMalloc(&pl->scratch, 256);
+  if (e != cudaSuccess) {
+    pl->scratch = nullptr;
+    rc = cuda_fail(e);
+  }
+  if (rc == DLS_OK) {
+    e = cudaStreamBeginCapture(pl->capture, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) rc = cuda_fail(e);
+  }
+  if (rc == DLS_OK) {
+    rc = enqueue_count(n, flags, order, order_len, d_prefixes, depth, n_prefixes,
+                       d_counts, d_total, nullptr, cfg, pl->capture, pl->scratch);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(pl->capture, &g);
+    if (rc == DLS_OK && e != cudaSuccess) rc = cuda_fail(e);
+    pl->graph = g;
+  }
+  if (rc == DLS_OK) {
+    e = cudaGraphInstantiate(&pl->exec, pl->graph, 0);
+    if (e != cudaSuccess) rc = cuda_fail(e);
+  }
+  if (rc != DLS_OK) {
+    dls_plan_destroy(pl);
+    return rc;
+  }
+  *plan_out = pl;
+  return DLS_OK;
+}
+
+int dls_plan_launch(dls_plan *plan, void *stream) {
+  if (plan == nullptr || plan->exec == nullptr) return DLS_ERR_BAD_STATE;
+  cudaError_t e = cudaGraphLaunch(plan->exec, reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e);
+  return DLS_OK;
+}
+
+void dls_plan_destroy(dls_plan *plan) {
+  if (!plan) return;
+  if (plan->exec) cudaGraphExecDestroy(plan->exec);
+  if (plan->graph) cudaGraphDestroy(plan->graph);
+  if (plan->capture) cudaStreamDestroy(plan->capture);
+  if (plan->scratch) cudaFree(plan->scratch);
+  delete plan;
+}
+
+}  // extern "C"

@@ -41,3 +41,13 @@ def fig1_order():
 @pytest.fixture(scope="session")
 def golden():
     return golden_counts()
+
+
+@pytest.fixture(scope="session")
+def dls():
+    """The product binding, with libdls.so built in-tree if needed (nvcc)."""
+    from paper_1709_02599_gb300 import build as _build
+    _build.build()
+    import paper_1709_02599_gb300 as m
+    m.lib()
+    return m

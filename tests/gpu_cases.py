@@ -1,0 +1,70 @@
+"""Workload construction for the GPU tests.
+
+Each workload is built twice from the same seeded indices (dls_inputs): once
+by the library (fill order, prefix split -- what the GPU counts) and once by
+the oracle (its own order and enumerator -- what the oracle counts).  The two
+must agree byte for byte; the oracle only ever sees its own arrays."""
+import numpy as np
+
+import dls_inputs
+import oracle
+from oracle import orders
+
+D, V = 1, 2
+
+
+class Workload:
+    def __init__(self, n, flags, order, prefixes, oracle_order, oracle_prefixes, **extra):
+        self.n, self.flags = n, flags
+        self.order, self.prefixes = order, prefixes
+        self.oracle_order, self.oracle_prefixes = oracle_order, oracle_prefixes
+        self.__dict__.update(extra)
+        assert [tuple(c) for c in order] == list(oracle_order)
+        assert prefixes.shape == oracle_prefixes.shape
+        assert (prefixes == oracle_prefixes).all()
+
+
+def split(dls, n, flags, after_row0, first_rows=1):
+    """Row 0 identity, every valid prefix `after_row0` cells past row 0."""
+    vs = bool(flags & V)
+    order = dls.fill_order(n, flags, first_rows=first_rows)
+    o_order = orders.md_ad_rows(n, vsym=vs, first_rows=first_rows)
+    w = len(orders.identity(n, vs))
+    depth = min(len(o_order), w + after_row0)
+    base = np.array([orders.identity(n, vs)], np.uint8)
+    pre, _ = dls.extend_prefixes(n, flags, order, base, depth)
+    o_pre, _ = oracle.extend(n, flags, o_order, base, depth)
+    return Workload(n, flags, order, pre, o_order, o_pre, depth=depth)
+
+
+def dls8_diag64(dls, seed=0, k=64, after_row0=20):
+    """Order 8, row 0 identity, k seed-drawn main-diagonal fillings, each split
+    `after_row0` cells past row 0."""
+    n = 8
+    order = dls.fill_order(n, D)
+    o_order = orders.md_ad_rows(n)
+    ident = np.array([orders.identity(n)], np.uint8)
+    diags, _ = dls.extend_prefixes(n, D, order, ident, n + (n - 1))
+    o_diags, _ = oracle.extend(n, D, o_order, ident, n + (n - 1))
+    assert (diags == o_diags).all()
+    picks = dls_inputs.choose(len(diags), k, seed)
+    pre, par = dls.extend_prefixes(n, D, order, diags[picks], n + after_row0)
+    o_pre, o_par = oracle.extend(n, D, o_order, o_diags[picks], n + after_row0)
+    assert (par == o_par).all()
+    return Workload(n, D, order, pre, o_order, o_pre, parents=par, picks=picks,
+                    n_diags=len(diags), depth=n + after_row0)
+
+
+def vsym10_rows2(dls, seed=0, k=2000):
+    """Order 10 vertically symmetric, rows 1-2 fixed after the identity row;
+    k seed-drawn prefixes out of all valid ones."""
+    n = 10
+    order = dls.fill_order(n, D | V, first_rows=3)
+    o_order = orders.md_ad_rows(n, vsym=True, first_rows=3)
+    ident = np.array([orders.identity(n, True)], np.uint8)
+    allp, _ = dls.extend_prefixes(n, D | V, order, ident, 3 * (n // 2))
+    o_allp, _ = oracle.extend(n, D | V, o_order, ident, 3 * (n // 2))
+    assert (allp == o_allp).all()
+    picks = dls_inputs.choose(len(allp), k, seed)
+    return Workload(n, D | V, order, allp[picks], o_order, o_allp[picks],
+                    population=len(allp), depth=3 * (n // 2))

@@ -1,0 +1,223 @@
+"""GPU parity: the CUDA path against the oracle, bit-exact per prefix, on every
+workload, both kernels and a range of launch shapes; the paper's printed
+counts where the GPU reaches them; edge cases."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import orders
+import gpu_cases
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+D, V = 1, 2
+THREADS = max(1, min(16, os.cpu_count() or 1))
+
+
+def _gpu_counts(dls, n, flags, order, pre, launch=None, plain=False):
+    t = torch.from_numpy(np.ascontiguousarray(pre)).cuda()
+    total = torch.zeros(1, dtype=torch.uint64, device="cuda")
+    if plain:
+        c = dls.count_plain(n, flags, order, t, total=total)
+    else:
+        c = dls.count(n, flags, order, t, total=total, launch=launch)
+    torch.cuda.synchronize()
+    c = c.cpu().numpy()
+    tot = int(total.cpu().numpy()[0])
+    assert tot == int(c.sum(dtype=np.uint64))
+    return c
+
+
+SHAPES = [
+    dict(),
+    dict(block_threads=32),
+    dict(block_threads=512),
+    dict(lanes_per_prefix=4),
+    dict(lanes_per_prefix=32),
+    dict(donate=-1),
+    dict(check_every=1),
+    dict(blocks_per_sm=1, block_threads=64),
+]
+
+
+def test_config1_order6_single_subproblem(dls, golden):
+    wl = gpu_cases.split(dls, 6, D, 0)
+    assert wl.prefixes.shape == (1, 6)
+    ref, _ = oracle.count_many(6, D, wl.oracle_order, wl.oracle_prefixes)
+    for sh in SHAPES:
+        c = _gpu_counts(dls, 6, D, wl.order, wl.prefixes, dls.Launch(**sh))
+        assert (c == ref).all(), sh
+        assert int(c[0]) * dls.multiplier(6, D) == golden["dls_total_6"]
+    c = _gpu_counts(dls, 6, D, wl.order, wl.prefixes, plain=True)
+    assert (c == ref).all()
+
+
+@pytest.mark.parametrize("n,flags,after", [(4, D, 0), (5, D, 3), (5, 0, 4), (6, D, 5),
+                                           (6, D, 9), (6, D | V, 2), (6, 0, 8), (7, D, 4),
+                                           (8, D | V, 6), (7, D, 14)])
+def test_small_workloads_all_shapes(dls, n, flags, after):
+    wl = gpu_cases.split(dls, n, flags, after)
+    ref, _ = oracle.count_many(n, flags, wl.oracle_order, wl.oracle_prefixes, threads=THREADS)
+    for sh in SHAPES:
+        c = _gpu_counts(dls, n, flags, wl.order, wl.prefixes, dls.Launch(**sh))
+        assert (c == ref).all(), sh
+        c = _gpu_counts(dls, n, flags, wl.order, wl.prefixes,
+                        dls.Launch(kernel=dls.KERNEL_PLAIN, **sh))
+        assert (c == ref).all(), ("plain", sh)
+
+
+def test_config2_order7_split10(dls):
+    wl = gpu_cases.split(dls, 7, D, 10)
+    assert len(wl.prefixes) > 1000
+    ref, _ = oracle.count_many(7, D, wl.oracle_order, wl.oracle_prefixes, threads=THREADS)
+    for sh in (dict(), dict(lanes_per_prefix=8), dict(block_threads=256)):
+        c = _gpu_counts(dls, 7, D, wl.order, wl.prefixes, dls.Launch(**sh))
+        assert (c == ref).all(), sh
+    c = _gpu_counts(dls, 7, D, wl.order, wl.prefixes, plain=True)
+    assert (c == ref).all()
+    assert int(ref.sum()) == oracle.count(7, D, orders.md_ad_rows(7), orders.identity(7))[0]
+
+
+def test_node_counts_match_oracle(dls):
+    for n, flags, after in ((6, D, 0), (7, D, 10), (6, D | V, 3), (5, 0, 5)):
+        wl = gpu_cases.split(dls, n, flags, after)
+        ref_c, ref_n = oracle.count_many(n, flags, wl.oracle_order, wl.oracle_prefixes,
+                                         threads=THREADS)
+        t = torch.from_numpy(wl.prefixes).cuda()
+        for sh in (dict(), dict(lanes_per_prefix=4), dict(kernel=dls.KERNEL_PLAIN)):
+            nodes = torch.zeros(1, dtype=torch.uint64, device="cuda")
+            c = dls.count(n, flags, wl.order, t, nodes=nodes, launch=dls.Launch(**sh))
+            torch.cuda.synchronize()
+            assert (c.cpu().numpy() == ref_c).all()
+            assert int(nodes.cpu().numpy()[0]) == int(ref_n.sum()), (n, flags, sh)
+
+
+@pytest.mark.slow
+def test_config3_order8_diag64_sampled_against_oracle(dls):
+    wl = gpu_cases.dls8_diag64(dls)
+    c = _gpu_counts(dls, 8, D, wl.order, wl.prefixes)
+    # the diagonals the oracle recounts: 4 of the 64, seed-chosen
+    import dls_inputs
+    check = dls_inputs.choose(64, 4, seed=1)
+    sel = np.isin(wl.parents, check)
+    ref, _ = oracle.count_many(8, D, wl.oracle_order, wl.oracle_prefixes[sel], threads=THREADS)
+    assert (c[sel] == ref).all()
+    # plain launch agrees everywhere
+    c2 = _gpu_counts(dls, 8, D, wl.order, wl.prefixes, plain=True)
+    assert (c2 == c).all()
+    # and a lane-split launch
+    c3 = _gpu_counts(dls, 8, D, wl.order, wl.prefixes, dls.Launch(lanes_per_prefix=4))
+    assert (c3 == c).all()
+
+
+@pytest.mark.slow
+def test_config4_vsym10_smallest_against_oracle(dls):
+    wl = gpu_cases.vsym10_rows2(dls)
+    assert len(wl.prefixes) == 2000
+    c = _gpu_counts(dls, 10, D | V, wl.order, wl.prefixes)
+    c2 = _gpu_counts(dls, 10, D | V, wl.order, wl.prefixes, plain=True)
+    assert (c2 == c).all()
+    idx = np.argsort(c, kind="stable")[:20]
+    ref, _ = oracle.count_many(10, D | V, wl.oracle_order, wl.oracle_prefixes[idx],
+                               threads=THREADS)
+    assert (c[idx] == ref).all()
+
+
+@pytest.mark.slow
+def test_paper_order8_total(dls, golden):
+    # Section 5.1: 7 447 587 840 diagonal Latin squares of order 8 with row 0
+    # fixed; split after both diagonals (14 cells past row 0)
+    wl = gpu_cases.split(dls, 8, D, 14)
+    c = _gpu_counts(dls, 8, D, wl.order, wl.prefixes)
+    assert int(c.sum(dtype=np.uint64)) == golden["dls8_row0_fixed"]
+
+
+def test_paper_hourglass8_on_gpu(dls, golden):
+    # Section 4.2: 22 192 248 hourglass designs of order 8
+    n = 8
+    order = dls.fill_order(n, D, dls.ORDER_HOURGLASS)[:8 + 7 + 7 + 6]
+    base = np.arange(n, dtype=np.uint8)[None]
+    pre, _ = dls.extend_prefixes(n, D, order, base, 8 + 7)
+    c = _gpu_counts(dls, n, D, order, pre)
+    assert int(c.sum(dtype=np.uint64)) == golden["hourglass8"]
+
+
+def test_edge_cases(dls):
+    order = dls.fill_order(6, D)
+    # empty batch
+    t = torch.zeros((0, 6), dtype=torch.uint8, device="cuda")
+    c = dls.count(6, D, order, t)
+    torch.cuda.synchronize()
+    assert c.numel() == 0
+    # complete squares as prefixes: 1 if valid, 0 if not
+    o_order = orders.md_ad_rows(6)
+    full, _ = oracle.extend(6, D, o_order, np.array([orders.identity(6)], np.uint8), 36)
+    assert len(full) == 128
+    bad = full[:5].copy()
+    bad[:, 20] = (bad[:, 20] + 1) % 6
+    pre = np.concatenate([full, bad])
+    c = _gpu_counts(dls, 6, D, order, pre)
+    ref, _ = oracle.count_many(6, D, o_order, pre)
+    assert (c == ref).all() and c[:128].sum() == 128
+    # one cell left
+    c = _gpu_counts(dls, 6, D, order, full[:, :35])
+    assert (c == 1).all()
+    # invalid prefixes: repeated value, value out of range
+    ok, _ = oracle.extend(6, D, o_order, np.array([orders.identity(6)], np.uint8), 10)
+    bad = ok[:40].copy()
+    bad[::2, 7] = 9
+    bad[1::2, 9] = bad[1::2, 8]
+    c = _gpu_counts(dls, 6, D, order, np.concatenate([ok[:40], bad]))
+    ref, _ = oracle.count_many(6, D, o_order, np.concatenate([ok[:40], bad]))
+    assert (c == ref).all() and (c[40:] == 0).all()
+    # orders 1..3
+    assert _gpu_counts(dls, 1, D, [(0, 0)], np.zeros((1, 0), np.uint8))[0] == 1
+    for n in (2, 3):
+        o = dls.fill_order(n, D)
+        assert _gpu_counts(dls, n, D, o, np.arange(n, dtype=np.uint8)[None])[0] == 0
+    # vertically symmetric odd orders are empty
+    for n in (5, 7):
+        o = dls.fill_order(n, D | V)
+        c = _gpu_counts(dls, n, D | V, o, np.arange(n // 2, dtype=np.uint8)[None])
+        assert c[0] == 0
+    # the largest order: partial order of 16 + 6 cells, every mask bit in use
+    o16 = [(0, j) for j in range(16)] + [(1, 1), (1, 14), (2, 2), (15, 0), (15, 15), (3, 5)]
+    pre16 = np.arange(16, dtype=np.uint8)[None]
+    c = _gpu_counts(dls, 16, D, o16, pre16)
+    assert c[0] == oracle.count(16, D, o16, list(range(16)))[0]
+
+
+def test_host_buffers_and_plan_and_streams(dls):
+    wl = gpu_cases.split(dls, 7, D, 8)
+    ref, _ = oracle.count_many(7, D, wl.oracle_order, wl.oracle_prefixes, threads=THREADS)
+    # host-buffer entry point (pinned and pageable)
+    pinned = torch.from_numpy(wl.prefixes).pin_memory()
+    cnt, tot = dls.count_host(7, D, wl.order, pinned)
+    assert (cnt == ref).all() and tot == int(ref.sum())
+    cnt, tot = dls.count_host(7, D, wl.order, wl.prefixes,
+                              launch=dls.Launch(kernel=dls.KERNEL_PLAIN))
+    assert (cnt == ref).all()
+    # graph plan, launched repeatedly
+    t = torch.from_numpy(wl.prefixes).cuda()
+    counts = torch.empty(len(t), dtype=torch.uint64, device="cuda")
+    total = torch.empty(1, dtype=torch.uint64, device="cuda")
+    plan = dls.Plan(7, D, wl.order, t, counts, total)
+    for _ in range(3):
+        counts.fill_(7)
+        plan.launch()
+        torch.cuda.synchronize()
+        assert (counts.cpu().numpy() == ref).all()
+        assert int(total.cpu().numpy()[0]) == int(ref.sum())
+    plan.close()
+    # two streams at once
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    c1 = torch.empty(len(t), dtype=torch.uint64, device="cuda")
+    c2 = torch.empty(len(t), dtype=torch.uint64, device="cuda")
+    torch.cuda.synchronize()
+    dls.count(7, D, wl.order, t, counts=c1, stream=s1)
+    dls.count(7, D, wl.order, t, counts=c2, stream=s2, launch=dls.Launch(lanes_per_prefix=2))
+    torch.cuda.synchronize()
+    assert (c1.cpu().numpy() == ref).all() and (c2.cpu().numpy() == ref).all()

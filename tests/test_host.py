@@ -1,0 +1,145 @@
+"""CPU tests of the library's host side: it loads, exports what include/dls.h
+declares, and its fill orders, prefix split and prefix sampler agree exactly
+with the oracle's independent versions (or with Fig. 1 of the paper)."""
+import subprocess
+
+import numpy as np
+import pytest
+
+import dls_inputs
+import oracle
+from oracle import orders
+from conftest import fig1_order
+
+D, V = 1, 2
+
+
+def test_library_exports_every_declared_symbol(dls):
+    from paper_1709_02599_gb300 import _lib
+    declared = _lib.declared_symbols()
+    assert "dls_count" in declared and "dls_make_prefixes" not in declared
+    out = subprocess.run(["nm", "-D", "--defined-only", _lib.LIB_PATH],
+                         capture_output=True, text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    missing = [s for s in declared if s not in exported]
+    assert not missing, missing
+    lib = dls.lib()
+    for s in declared:
+        getattr(lib, s)
+
+
+def test_strerror_and_version(dls):
+    lib = dls.lib()
+    assert lib.dls_strerror(0) == b"ok"
+    assert lib.dls_version() >= (1 << 16)
+
+
+@pytest.mark.parametrize("n", [4, 5, 6, 7, 8, 9, 10])
+def test_fill_orders_match_oracle(dls, n):
+    got = [tuple(c) for c in dls.fill_order(n, D, dls.ORDER_MD_AD_ROWS)]
+    assert got == orders.md_ad_rows(n)
+    got = [tuple(c) for c in dls.fill_order(n, D, dls.ORDER_ROW_MAJOR)]
+    assert got == orders.row_major(n)
+    got = [tuple(c) for c in dls.fill_order(n, D, dls.ORDER_HOURGLASS)]
+    assert got == orders.hourglass(n)
+    if n % 2 == 0:
+        got = [tuple(c) for c in dls.fill_order(n, D | V, dls.ORDER_MD_AD_ROWS)]
+        assert got == orders.md_ad_rows(n, vsym=True)
+    for k in (2, 3):
+        got = [tuple(c) for c in dls.fill_order(n, D, dls.ORDER_MD_AD_ROWS, first_rows=k)]
+        assert got == orders.md_ad_rows(n, first_rows=k)
+
+
+def test_heuristic_order_reproduces_fig1(dls):
+    got = [tuple(c) for c in dls.fill_order(9, D, dls.ORDER_HEURISTIC)]
+    assert got[:9] == orders.row0(9)
+    assert got[9:] == fig1_order()
+
+
+@pytest.mark.parametrize("n", [4, 5, 6, 7, 8])
+def test_heuristic_order_is_a_permutation_and_counts_agree(dls, n):
+    o = [tuple(c) for c in dls.fill_order(n, D, dls.ORDER_HEURISTIC)]
+    assert sorted(o) == sorted(orders.row_major(n))
+    if n <= 6:
+        ref = oracle.count(n, D, orders.md_ad_rows(n), orders.identity(n))[0]
+        assert oracle.count(n, D, o, orders.identity(n))[0] == ref
+
+
+@pytest.mark.parametrize("n,flags,extra", [(6, D, 0), (6, D, 5), (6, D, 12), (7, D, 10),
+                                           (8, D, 7), (6, D | V, 4), (8, D | V, 6),
+                                           (5, 0, 6), (6, D, 30)])
+def test_extend_prefixes_match_oracle(dls, n, flags, extra):
+    vs = bool(flags & V)
+    order = orders.md_ad_rows(n, vsym=vs)
+    base = np.array([orders.identity(n, vs)], np.uint8)
+    depth = min(len(order), base.shape[1] + extra)
+    got, gp = dls.extend_prefixes(n, flags, order, base, depth)
+    ref, rp = oracle.extend(n, flags, order, base, depth)
+    assert got.shape == ref.shape
+    assert (got == ref).all() and (gp == rp).all()
+
+
+def test_extend_from_many_bases(dls):
+    n = 7
+    order = orders.md_ad_rows(n)
+    base, _ = oracle.extend(n, D, order, np.array([orders.identity(n)], np.uint8), n + 4)
+    base = base[::7]
+    got, gp = dls.extend_prefixes(n, D, order, base, n + 9)
+    ref, rp = oracle.extend(n, D, order, base, n + 9)
+    assert (got == ref).all() and (gp == rp).all()
+    # an invalid base prefix has no extensions
+    bad = base.copy()
+    bad[0, n] = bad[0, 0]
+    got2, gp2 = dls.extend_prefixes(n, D, order, bad, n + 9)
+    ref2, rp2 = oracle.extend(n, D, order, bad, n + 9)
+    assert (got2 == ref2).all() and (gp2 == rp2).all()
+
+
+def test_sample_prefix_matches_oracle(dls):
+    jobs = dls_inputs.serving_jobs(40, seed=3)
+    for job in jobs:
+        n, k = job["n"], job["rows"]
+        flags = D | (V if job["vsym"] else 0)
+        vs = job["vsym"]
+        order = orders.md_ad_rows(n, vsym=vs, first_rows=k)
+        depth = k * len(orders.identity(n, vs))
+        got, gu = dls.sample_prefix(n, flags, order, depth, job["draws"])
+        ref, ru = oracle.sample_prefix(n, flags, order, depth, job["draws"])
+        assert gu == ru
+        if ref is None:
+            assert got is None
+        else:
+            assert (got == ref).all()
+
+
+def test_multipliers(dls):
+    for n in range(1, 13):
+        for flags in (0, D, D | V):
+            assert dls.multiplier(n, flags) == oracle.multiplier(n, flags)
+    assert dls.multiplier(9, D) == 362880
+
+
+def test_u128_helpers(dls):
+    from paper_1709_02599_gb300 import _lib
+    lib = dls.lib()
+    a = (1 << 64) - 1
+    r = lib.dls_mul_u64(a, _lib.U128(a, 0))
+    assert r.value() == a * a
+    r = lib.dls_add_u128(_lib.U128(a, 1), _lib.U128(1, 0))
+    assert r.value() == (2 << 64)
+
+
+def test_argument_errors(dls):
+    from paper_1709_02599_gb300._lib import DlsError
+    with pytest.raises(DlsError) as e:
+        dls.fill_order(17, D)
+    assert e.value.code == 1
+    with pytest.raises(DlsError) as e:
+        dls.extend_prefixes(6, D, [(0, 0), (0, 0)], np.zeros((1, 0), np.uint8), 1)
+    assert e.value.code == 2
+    with pytest.raises(DlsError) as e:   # right-half cell with vertical symmetry
+        dls.extend_prefixes(6, D | V, [(0, 0), (0, 4)], np.zeros((1, 0), np.uint8), 1)
+    assert e.value.code == 2
+    with pytest.raises(DlsError) as e:   # depth beyond the order
+        dls.extend_prefixes(6, D, orders.md_ad_rows(6), np.zeros((1, 0), np.uint8), 37)
+    assert e.value.code == 3
