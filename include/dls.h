@@ -223,6 +223,29 @@ int dls_count_host(int n, uint32_t flags, const uint8_t *order,
                    dls_u128 *total_out, const dls_launch_t *cfg,
                    void *stream);
 
+/* Allocation-free variant of dls_count_host() -- the paper has no
+ * counterpart; it exists for callers that cannot let a library call
+ * cudaMalloc: programs whose own pool already owns the device memory, and
+ * latency-critical paths that must not pay the implicit device
+ * synchronisation of cudaMalloc/cudaFree.  The staged prefixes, the staged
+ * counts and the persistent kernel's queue head live in one fixed array of
+ * DLS_NOALLOC_SCRATCH_BYTES compiled into the library (held on every GPU
+ * that loads the library until the process exits).  A call needs 256 +
+ * (n_prefixes * depth rounded up to 256) + 8 * n_prefixes bytes of it;
+ * bigger calls return DLS_ERR_CAPACITY before any copy.  Arguments and
+ * results are those of dls_count_host() (h_counts or total_out may be NULL,
+ * not both).  Synchronous.  Every call shares the array: calls that overlap
+ * on the GPU race and give wrong counts, so serialise them.  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress);
+ * make it before any stream capture.  Allocates no device memory and calls
+ * no cudaMalloc/cudaFree. */
+#define DLS_NOALLOC_SCRATCH_BYTES (4u << 20)
+int dls_count_host_noalloc(int n, uint32_t flags, const uint8_t *order,
+                           int order_len, const uint8_t *h_prefixes, int depth,
+                           int64_t n_prefixes, uint64_t *h_counts,
+                           dls_u128 *total_out, const dls_launch_t *cfg,
+                           void *stream);
+
 /* Free the library's per-(device, stream) work areas and cached plans. */
 void dls_release(void);
 

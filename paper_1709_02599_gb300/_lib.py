@@ -86,6 +86,8 @@ def load():
                                  ctypes.POINTER(LaunchT), vp]),
         "dls_count_host": (c_int, [c_int, c_u32, u8p, c_int, vp, c_int, c_i64, vp,
                                    ctypes.POINTER(U128), ctypes.POINTER(LaunchT), vp]),
+        "dls_count_host_noalloc": (c_int, [c_int, c_u32, u8p, c_int, vp, c_int, c_i64, vp,
+                                           ctypes.POINTER(U128), ctypes.POINTER(LaunchT), vp]),
         "dls_release": (None, []),
         "dls_plan_create": (c_int, [ctypes.POINTER(vp), c_int, c_u32, u8p, c_int, vp,
                                     c_int, c_i64, vp, vp, ctypes.POINTER(LaunchT)]),

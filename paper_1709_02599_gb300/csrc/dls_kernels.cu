@@ -676,6 +676,18 @@ static int enqueue_count(int n, uint32_t flags, const uint8_t *order,
   return DLS_OK;
 }
 
+// The persistent or plain launch of enqueue_count with the queue head at a
+// caller-chosen device address (used by the allocation-free entry point).
+int enqueue_count_with_scratch(int n, uint32_t flags, const uint8_t *order,
+                               int order_len, const uint8_t *d_prefixes,
+                               int depth, int64_t n_prefixes,
+                               uint64_t *d_counts, const dls_launch_t *cfg,
+                               cudaStream_t stream,
+                               unsigned long long *scratch) {
+  return enqueue_count(n, flags, order, order_len, d_prefixes, depth, n_prefixes,
+                       d_counts, nullptr, nullptr, cfg, stream, scratch);
+}
+
 }  // namespace dls
 
 using namespace dls;
