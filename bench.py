@@ -58,6 +58,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--diagonals", type=int, default=DIAGS,
+                    help="main-diagonal fillings per rank (64 = the benchmark workload; "
+                         "fewer only for profiling captures)")
     ap.add_argument("--launch", default="", help="json dict of Launch fields")
     return ap.parse_args()
 
@@ -71,11 +75,11 @@ def dist_env():
 
 # ------------------------------------------------------------ workloads --
 
-def product_workload(dls, seed):
+def product_workload(dls, seed, k=DIAGS):
     order = dls.fill_order(N, FLAGS)
     ident = np.arange(N, dtype=np.uint8)[None]
     diags, _ = dls.extend_prefixes(N, FLAGS, order, ident, N + (N - 1))
-    picks = dls_inputs.choose(len(diags), DIAGS, seed)
+    picks = dls_inputs.choose(len(diags), k, seed)
     pre, par = dls.extend_prefixes(N, FLAGS, order, diags[picks], N + AFTER_ROW0)
     return order, pre, par, picks
 
@@ -245,7 +249,7 @@ def main():
     stream = torch.cuda.Stream()
 
     seed = rank
-    order, pre, par, picks = product_workload(dls, seed)
+    order, pre, par, picks = product_workload(dls, seed, args.diagonals)
     P, depth = pre.shape
     d_pre = torch.from_numpy(pre).to("cuda")
     counts = torch.empty(P, dtype=torch.uint64, device="cuda")
@@ -310,18 +314,20 @@ def main():
         pplan.close()
 
     # end to end through the host-buffer entry point
-    pinned_in = torch.from_numpy(pre).pin_memory()
-    pinned_out = torch.empty(P, dtype=torch.int64).pin_memory()
-    for _ in range(2):
-        dls.count_host(N, FLAGS, order, pinned_in, pinned_out, launch, stream)
-    e2e_t = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        _, tot = dls.count_host(N, FLAGS, order, pinned_in, pinned_out, launch, stream)
-        e2e_t.append(time.perf_counter() - t0)
-        if tot != squares:
-            raise RuntimeError("host-buffer count differs")
-    e2e_step = sum(e2e_t) / len(e2e_t)
+    e2e_step = None
+    if not args.no_e2e:
+        pinned_in = torch.from_numpy(pre).pin_memory()
+        pinned_out = torch.empty(P, dtype=torch.int64).pin_memory()
+        for _ in range(2):
+            dls.count_host(N, FLAGS, order, pinned_in, pinned_out, launch, stream)
+        e2e_t = []
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            _, tot = dls.count_host(N, FLAGS, order, pinned_in, pinned_out, launch, stream)
+            e2e_t.append(time.perf_counter() - t0)
+            if tot != squares:
+                raise RuntimeError("host-buffer count differs")
+        e2e_step = sum(e2e_t) / len(e2e_t)
 
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
@@ -333,15 +339,18 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * step_s, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": N, "flags": "diagonal", "row0": "identity",
-                   "diagonal_fillings": DIAGS, "seed": "rank", "split_after_row0": AFTER_ROW0,
+        "config": {"workload": WORKLOAD if args.diagonals == DIAGS else
+                   "%s (profiling case: %d diagonals)" % (WORKLOAD, args.diagonals),
+                   "n": N, "flags": "diagonal", "row0": "identity",
+                   "diagonal_fillings": args.diagonals, "seed": "rank", "split_after_row0": AFTER_ROW0,
                    "prefixes": int(P), "squares_per_step": squares, "nodes_per_step": nodes,
                    "kernel": "k_persistent (CUDA graph)", "launch": cfg,
                    "l2": "flushed: 256 MiB write between timed steps"},
         "plain": plain,
-        "e2e": {"value": squares_all / e2e_step if ws == 1 else squares / e2e_step,
-                "unit": UNIT, "h2d_bytes_per_step": int(P * depth),
-                "d2h_bytes_per_step": int(P * 8), "entry": "dls_count_host"},
+        "e2e": None if e2e_step is None else {
+            "value": squares_all / e2e_step if ws == 1 else squares / e2e_step,
+            "unit": UNIT, "h2d_bytes_per_step": int(P * depth),
+            "d2h_bytes_per_step": int(P * 8), "entry": "dls_count_host"},
         "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops,
                      "unit": "Tops/s", "frac": achieved_tops / peak_tops, "traffic": None,
                      "ops_per_node": OPS_PER_NODE,
