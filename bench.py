@@ -62,7 +62,12 @@ def parse():
     ap.add_argument("--diagonals", type=int, default=DIAGS,
                     help="main-diagonal fillings per rank (64 = the benchmark workload; "
                          "fewer only for profiling captures)")
-    ap.add_argument("--launch", default="", help="json dict of Launch fields")
+    ap.add_argument("--launch", default="", help="json dict of Launch fields (skips the "
+                    "launch-shape stage of the autotuner)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="split 20 cells past row 0, cells after the split row by row")
+    ap.add_argument("--suffix", default="", choices=["", "given", "heuristic"],
+                    help="fix the order of the cells after the split")
     return ap.parse_args()
 
 
@@ -75,25 +80,29 @@ def dist_env():
 
 # ------------------------------------------------------------ workloads --
 
-def product_workload(dls, seed, k=DIAGS):
+def product_base(dls, seed, k=DIAGS):
+    """Fill order (row 0, main diagonal, anti-diagonal, rows) and the k drawn
+    main-diagonal fillings (row 0 + main diagonal) the workload starts from."""
     order = dls.fill_order(N, FLAGS)
     ident = np.arange(N, dtype=np.uint8)[None]
     diags, _ = dls.extend_prefixes(N, FLAGS, order, ident, N + (N - 1))
     picks = dls_inputs.choose(len(diags), k, seed)
-    pre, par = dls.extend_prefixes(N, FLAGS, order, diags[picks], N + AFTER_ROW0)
-    return order, pre, par, picks
+    return order, diags[picks], picks
 
 
-def oracle_sample(seed, n_diags):
-    """The oracle's own prefixes for `n_diags` of the run's diagonals."""
+def oracle_sample(seed, n_diags, depth=N + AFTER_ROW0, suffix="heuristic"):
+    """The oracle's own order and prefixes for `n_diags` of the run's
+    diagonals, split at `depth`, cells after the split in the given rule."""
     import oracle
     from oracle import orders
     o_order = orders.md_ad_rows(N)
+    if suffix == "heuristic":
+        o_order = orders.heuristic_complete(N, o_order[:depth])
     ident = np.array([orders.identity(N)], np.uint8)
     diags, _ = oracle.extend(N, FLAGS, o_order, ident, N + (N - 1))
     picks = dls_inputs.choose(len(diags), DIAGS, seed)
     sub = picks[dls_inputs.choose(len(picks), n_diags, seed + 1000)]
-    pre, _ = oracle.extend(N, FLAGS, o_order, diags[sub], N + AFTER_ROW0)
+    pre, _ = oracle.extend(N, FLAGS, o_order, diags[sub], depth)
     return o_order, pre
 
 
@@ -248,14 +257,32 @@ def main():
     dev = torch.cuda.current_device()
     stream = torch.cuda.Stream()
 
+    from paper_1709_02599_gb300 import autotune
     seed = rank
-    order, pre, par, picks = product_workload(dls, seed, args.diagonals)
+    order0, base, picks = product_base(dls, seed, args.diagonals)
+    fixed = json.loads(args.launch) if args.launch else None
+    tuned = None
+    if args.no_autotune:
+        depth_sel, suffix_sel, cfg = N + AFTER_ROW0, args.suffix or "given", fixed or {}
+    else:
+        t0 = time.perf_counter()
+        suffixes = (args.suffix,) if args.suffix else ("given", "heuristic")
+        shapes = [{}] if fixed is not None else None
+        best = autotune.tune(N, FLAGS, order0, base, [N + 14, N + 17, N + 20, N + 23],
+                             suffixes=suffixes, shapes=shapes)
+        depth_sel, suffix_sel = best["depth"], best["suffix"]
+        cfg = fixed if fixed is not None else best["launch"]
+        tuned = {"trials": len(best["trials"]), "cached": best["cached"],
+                 "seconds": round(time.perf_counter() - t0, 2),
+                 "candidates": "split 14/17/20/23 cells past row 0 x suffix order "
+                               "{given, heuristic}, then %d launch shapes" % (
+                                   len(shapes or autotune.SHAPES) - 1)}
+    order, pre, par = autotune.build_problem(N, FLAGS, order0, base, depth_sel, suffix_sel)
     P, depth = pre.shape
     d_pre = torch.from_numpy(pre).to("cuda")
     counts = torch.empty(P, dtype=torch.uint64, device="cuda")
     total = torch.empty(1, dtype=torch.uint64, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
-    cfg = json.loads(args.launch) if args.launch else {}
     launch = dls.Launch(**cfg)
     plan = dls.Plan(N, FLAGS, order, d_pre, counts, total, launch)
 
@@ -301,7 +328,7 @@ def main():
     plain = None
     if not args.no_plain:
         pplan = dls.Plan(N, FLAGS, order, d_pre, counts, total,
-                         dls.Launch(kernel=dls.KERNEL_PLAIN))
+                         dls.Launch(kernel=dls.KERNEL_PLAIN, words=cfg.get("words", 0)))
         for _ in range(max(args.warmup, 1)):
             pplan.launch(stream)
         torch.cuda.synchronize()
@@ -342,9 +369,10 @@ def main():
         "config": {"workload": WORKLOAD if args.diagonals == DIAGS else
                    "%s (profiling case: %d diagonals)" % (WORKLOAD, args.diagonals),
                    "n": N, "flags": "diagonal", "row0": "identity",
-                   "diagonal_fillings": args.diagonals, "seed": "rank", "split_after_row0": AFTER_ROW0,
+                   "diagonal_fillings": args.diagonals, "seed": "rank",
+                   "split_after_row0": int(depth_sel - N), "suffix_order": suffix_sel,
                    "prefixes": int(P), "squares_per_step": squares, "nodes_per_step": nodes,
-                   "kernel": "k_persistent (CUDA graph)", "launch": cfg,
+                   "kernel": "k_persistent (CUDA graph)", "launch": cfg, "autotune": tuned,
                    "l2": "flushed: 256 MiB write between timed steps"},
         "plain": plain,
         "e2e": None if e2e_step is None else {
@@ -361,11 +389,12 @@ def main():
     }
     if rank == 0 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
-        o_order, opre = oracle_sample(seed, 2)
+        o_order, opre = oracle_sample(seed, 2, depth_sel, suffix_sel)
         c, _, dt = run_oracle(o_order, opre, threads)
         line["cpu_baseline"] = {"value": c / dt, "unit": UNIT, "cores": threads,
                                 "kind": "oracle",
-                                "sample": "all %d prefixes of 2 seed-chosen diagonals of the 64 "
+                                "sample": "all %d prefixes of 2 seed-chosen diagonals of the 64, "
+                                          "same split and fill order as the GPU run "
                                           "(%d squares, %.1f s)" % (len(opre), c, dt)}
     plan.close()
     if ws > 1:

@@ -112,6 +112,19 @@ int dls_version(void);
 int dls_fill_order(int n, uint32_t flags, int kind, int first_rows,
                    uint8_t *ij_out, int cap, int *len_out);
 
+/* Completes a fill order: keeps its first `keep` cells and appends every
+ * other cell of the square (left half with DLS_VSYM) by the rule of `kind`
+ * applied from the kept cells -- DLS_ORDER_HEURISTIC: the greedy
+ * most-constrained-cell order with the forced-last-cell rule of Section 2.3
+ * (the cell values never matter, so the completion depends only on which
+ * cells are kept); DLS_ORDER_MD_AD_ROWS: remaining diagonal cells, then the
+ * rest row by row; DLS_ORDER_ROW_MAJOR: the rest row by row.  Counts do not
+ * depend on the order of the cells after a prefix, so this changes only the
+ * size of the search (Section 2.3).  Host memory, caller-owned.  Errors as
+ * dls_fill_order, BAD_ORDER for a bad kept part. */
+int dls_order_complete(int n, uint32_t flags, const uint8_t *order, int keep,
+                       int kind, uint8_t *ij_out, int cap, int *len_out);
+
 /* The prefix split of Section 5.2: every valid assignment of the first
  * `depth` order cells that extends one of the n_base base prefixes (each
  * base_depth bytes), base prefixes in turn, each one's extensions in
@@ -173,6 +186,11 @@ typedef struct {
                              (default), -1 = off                            */
     int check_every;      /* persistent only: iterations between donation
                              checks (power of two, default 64)               */
+    int words;            /* where a lane keeps its row and column words:
+                             0 = registers when they fit (n <= 8, or even
+                             n <= 10 with DLS_VSYM), else shared memory;
+                             1 = shared memory; 2 = registers (BAD_ARG if
+                             they do not fit)                                */
 } dls_launch_t;
 
 /* Count completions of every prefix on the GPU (Algorithm 4 on the device).

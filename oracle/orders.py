@@ -76,3 +76,62 @@ def hourglass(n):
 def identity(n, vsym=False):
     """Values of row 0 fixed to 0..N-1 (left half only when vsym)."""
     return [j for j in _cols(n, vsym)]
+
+
+def heuristic_complete(n, kept, diagonal=True, vsym=False):
+    """Section 2.3: starting from the `kept` cells (row 0 for a whole
+    order), repeatedly take the unassigned cell with the largest
+    V = r_i + c_j + md(i,j) + ad(i,j) -- the numbers of assigned cells in its
+    row, its column and, when it lies on them, the two diagonals -- ties
+    going to the first cell in row-major order.  When an assignment leaves
+    one unassigned cell in one of its lines (row, column, main diagonal,
+    anti-diagonal, looked at in that order), that cell is taken next
+    (first-in first-out).  With vsym only left-half cells exist: a row has
+    N/2 of them, a column N, and the diagonals form one line made of the
+    left cells on either diagonal.  Returns kept + the appended cells."""
+    w = n // 2 if vsym else n
+    lines = [[(i, j) for j in range(w)] for i in range(n)]
+    lines += [[(i, j) for i in range(n)] for j in range(w)]
+    if diagonal and not vsym:
+        lines.append([(i, i) for i in range(n)])
+        lines.append([(i, n - 1 - i) for i in range(n)])
+    elif diagonal and vsym:
+        lines.append([(i, i) if i < w else (i, n - 1 - i) for i in range(n)])
+    of_cell = {}
+    for li, line in enumerate(lines):
+        for c in line:
+            of_cell.setdefault(c, []).append(li)
+    assigned = set()
+    out = []
+    queue = []
+
+    def assign(c, forced_rule):
+        assigned.add(c)
+        out.append(c)
+        if not forced_rule:
+            return
+        for li in of_cell[c]:
+            rest = [x for x in lines[li] if x not in assigned]
+            if len(rest) == 1:
+                queue.append(rest[0])
+
+    for c in kept:
+        assign(tuple(c), False)
+    while len(out) < n * w:
+        cell = None
+        while queue:
+            x = queue.pop(0)
+            if x not in assigned:
+                cell = x
+                break
+        if cell is None:
+            best = -1
+            for i in range(n):
+                for j in range(w):
+                    if (i, j) in assigned:
+                        continue
+                    v = sum(sum(1 for x in lines[li] if x in assigned) for li in of_cell[(i, j)])
+                    if v > best:
+                        best, cell = v, (i, j)
+        assign(cell, True)
+    return out

@@ -32,11 +32,12 @@ class Launch:
     split_pos: int = 0
     donate: int = 0
     check_every: int = 0
+    words: int = 0
 
     def c(self):
         return _lib.LaunchT(self.kernel, self.block_threads, self.blocks_per_sm,
                             self.lanes_per_prefix, self.split_pos, self.donate,
-                            self.check_every)
+                            self.check_every, self.words)
 
 
 def lib():
@@ -59,6 +60,21 @@ def fill_order(n, flags=DIAGONAL, kind=ORDER_MD_AD_ROWS, first_rows=1):
     ln = ctypes.c_int(0)
     _lib.check(L.dls_fill_order(n, flags, kind, first_rows, buf.ctypes.data_as(_lib.u8p),
                                 DLS_MAX_N * DLS_MAX_N, ctypes.byref(ln)), "dls_fill_order")
+    return buf[:ln.value].copy()
+
+
+def order_complete(n, flags, order, keep, kind=ORDER_HEURISTIC):
+    """Keep the first ``keep`` cells of ``order`` and append the rest of the
+    square by the rule of ``kind`` (dls_order_complete)."""
+    L = lib()
+    o, op, ol = _order(order)
+    if keep > ol:
+        raise ValueError("keep exceeds the order length")
+    buf = np.zeros((DLS_MAX_N * DLS_MAX_N, 2), np.uint8)
+    ln = ctypes.c_int(0)
+    _lib.check(L.dls_order_complete(n, flags, op, keep, kind, buf.ctypes.data_as(_lib.u8p),
+                                    DLS_MAX_N * DLS_MAX_N, ctypes.byref(ln)),
+               "dls_order_complete")
     return buf[:ln.value].copy()
 
 

@@ -42,7 +42,8 @@ class LaunchT(ctypes.Structure):
                 ("lanes_per_prefix", ctypes.c_int),
                 ("split_pos", ctypes.c_int),
                 ("donate", ctypes.c_int),
-                ("check_every", ctypes.c_int)]
+                ("check_every", ctypes.c_int),
+                ("words", ctypes.c_int)]
 
 
 class DlsError(RuntimeError):
@@ -72,6 +73,8 @@ def load():
         "dls_version": (c_int, []),
         "dls_fill_order": (c_int, [c_int, c_u32, c_int, c_int, u8p, c_int,
                                    ctypes.POINTER(c_int)]),
+        "dls_order_complete": (c_int, [c_int, c_u32, u8p, c_int, c_int, u8p, c_int,
+                                       ctypes.POINTER(c_int)]),
         "dls_extend_prefixes": (c_int, [c_int, c_u32, u8p, c_int, u8p, c_int, c_i64,
                                         c_int, u8p, c_i64, i64p, i64p]),
         "dls_sample_prefix": (c_int, [c_int, c_u32, u8p, c_int, c_int, u32p, c_i64,

@@ -158,6 +158,7 @@ static void order_hourglass(int n, std::vector<std::pair<int, int>> &out) {
 // and the two diagonals become one line (the left cells on the main diagonal
 // and those on the anti-diagonal, whose mirrors complete the main diagonal).
 static void order_heuristic(int n, bool diag, bool vsym,
+                            const std::vector<std::pair<int, int>> &kept,
                             std::vector<std::pair<int, int>> &out) {
   const int w = vsym ? n / 2 : n;
   std::vector<std::vector<std::pair<int, int>>> lines;
@@ -198,7 +199,8 @@ static void order_heuristic(int n, bool diag, bool vsym,
           if (!asg[c.first * w + c.second]) queue.push_back(c);
     }
   };
-  for (int j = 0; j < w; ++j) assign(0, j, false);
+  // the kept cells (row 0 for a whole order) are assigned without queuing
+  for (auto &c : kept) assign(c.first, c.second, false);
   const int total = n * w;
   while ((int)out.size() < total) {
     std::pair<int, int> cell{-1, -1};
@@ -275,11 +277,58 @@ int dls_fill_order(int n, uint32_t flags, int kind, int first_rows,
       if (vsym) return DLS_ERR_BAD_ARG;
       order_hourglass(n, cells);
       break;
-    case DLS_ORDER_HEURISTIC:
-      order_heuristic(n, diag, vsym, cells);
+    case DLS_ORDER_HEURISTIC: {
+      std::vector<std::pair<int, int>> row0;
+      for (int j = 0; j < (vsym ? n / 2 : n); ++j) row0.push_back({0, j});
+      order_heuristic(n, diag, vsym, row0, cells);
       break;
+    }
     default:
       return DLS_ERR_BAD_ARG;
+  }
+  *len_out = (int)cells.size();
+  if ((int)cells.size() > cap) return DLS_ERR_CAPACITY;
+  for (size_t t = 0; t < cells.size(); ++t) {
+    ij_out[2 * t] = (uint8_t)cells[t].first;
+    ij_out[2 * t + 1] = (uint8_t)cells[t].second;
+  }
+  return DLS_OK;
+}
+
+int dls_order_complete(int n, uint32_t flags, const uint8_t *order, int keep,
+                       int kind, uint8_t *ij_out, int cap, int *len_out) {
+  if (n < 1 || n > DLS_MAX_N) return DLS_ERR_INVALID_N;
+  if (len_out == nullptr || keep < 0 || cap < 0 || (cap > 0 && ij_out == nullptr))
+    return DLS_ERR_BAD_ARG;
+  OrderInfo info;
+  int rc = validate_order(n, flags, order, keep, &info);
+  if (rc) return rc;
+  const bool vsym = (flags & DLS_VSYM) != 0;
+  const bool diag = (flags & DLS_DIAGONAL) != 0;
+  const int w = vsym ? n / 2 : n;
+  std::vector<std::pair<int, int>> kept, cells;
+  for (int t = 0; t < keep; ++t) kept.push_back({info.i[t], info.j[t]});
+  if (kind == DLS_ORDER_HEURISTIC) {
+    order_heuristic(n, diag, vsym, kept, cells);
+  } else if (kind == DLS_ORDER_MD_AD_ROWS || kind == DLS_ORDER_ROW_MAJOR) {
+    bool used[DLS_MAX_N][DLS_MAX_N] = {};
+    for (auto &c : kept) {
+      used[c.first][c.second] = true;
+      cells.push_back(c);
+    }
+    auto add = [&](int i, int j) {
+      if (j >= w || used[i][j]) return;
+      used[i][j] = true;
+      cells.push_back({i, j});
+    };
+    if (kind == DLS_ORDER_MD_AD_ROWS) {
+      for (int i = 0; i < n; ++i) add(i, i);
+      for (int i = 0; i < n; ++i) add(i, n - 1 - i);
+    }
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < w; ++j) add(i, j);
+  } else {
+    return DLS_ERR_BAD_ARG;
   }
   *len_out = (int)cells.size();
   if ((int)cells.size() > cap) return DLS_ERR_CAPACITY;

@@ -56,6 +56,7 @@ constexpr unsigned FULL = 0xffffffffu;
 struct KParams {
   int n;
   uint32_t all;          // (1 << n) - 1
+  uint32_t pairmask;     // (1 << n/2) - 1, value pairs of a symmetric row
   int order_len;
   int depth;             // prefix length
   int last;              // order_len - 1
@@ -64,6 +65,7 @@ struct KParams {
   int check_mask;        // donation check period - 1
   int donate;
   int count_store;       // 1: counts[p] = cnt (one item per prefix, no donation)
+  int wr, wc;            // register words: bit width of a row / column field
   long long n_prefixes;
   long long n_items;
   const uint8_t *prefixes;
@@ -75,33 +77,6 @@ struct KParams {
   uint8_t cj[DLS_MAX_CELLS];
 };
 
-// Per-lane search state kept in registers.
-struct Lane {
-  int p;                 // current order position
-  uint32_t L;            // untried candidates at p
-  uint32_t v;            // value placed at p (one-hot), 0 = none yet
-  uint32_t info;         // cell descriptor of p (see cell_info)
-  uint32_t md, ad;       // diagonal words
-  uint32_t splitc;       // nodes met at split_pos so far
-  uint32_t sub;          // residue class of split nodes this item keeps
-  long long prefix;      // prefix index of the current item
-  unsigned long long cnt;    // completions found for the current item
-  unsigned long long nodes;  // placements made (node counting variant)
-};
-
-// Cell descriptor: byte offsets (from the lane's first state word) of the
-// row word and of the column word, with the main-diagonal flag in bit 0 and
-// the anti-diagonal flag in bit 16.
-__device__ __forceinline__ uint32_t cell_info(const KParams &p, int pos,
-                                              int diag, unsigned B) {
-  const int i = p.ci[pos], j = p.cj[pos];
-  const uint32_t roff = (uint32_t)i * B * 4u;
-  const uint32_t coff = (uint32_t)(p.n + j) * B * 4u;
-  const uint32_t md = (diag && i == j) ? 1u : 0u;
-  const uint32_t ad = (diag && i + j == p.n - 1) ? 1u : 0u;
-  return roff | md | ((coff | ad) << 16);
-}
-
 __device__ __forceinline__ uint32_t &word_at(char *tb, uint32_t off) {
   return *reinterpret_cast<uint32_t *>(tb + off);
 }
@@ -111,95 +86,176 @@ __device__ __forceinline__ uint32_t mirror(uint32_t d, int n) {
   return VSYM ? (__brev(d) >> (32 - n)) : 0u;
 }
 
-// Admissible values of the cell described by `info`.
-__device__ __forceinline__ uint32_t cands(char *tb, uint32_t info, uint32_t md,
-                                          uint32_t ad, uint32_t all) {
-  uint32_t f = word_at(tb, info & 0xfffcu) | word_at(tb, (info >> 16) & 0xfffcu);
-  f |= (info & 1u) ? md : 0u;
-  f |= (info & 0x10000u) ? ad : 0u;
-  return all & ~f;
-}
+// The row/column/diagonal words of one lane (Section 3: one word per line,
+// bit v set when value v is used on it).
+//
+// REG = false: row i and column j words in shared memory, word w of thread t
+//   at st[w * blockDim + t] (rows 0..n-1, then columns); a cell descriptor
+//   holds the byte offsets of its row and column word (main-diagonal flag in
+//   bit 0, anti-diagonal flag in bit 16).
+// REG = true: every row word packed into one 64-bit register R (row i at bit
+//   i * wr) and every column word into C (column j at bit j * wc); a cell
+//   descriptor holds the two shifts (bits 0-5 and 8-13) and the diagonal
+//   flags (bits 16, 17).  With vertical symmetry a row field records the
+//   value pairs {v, n-1-v} in use (bit min(v, n-1-v)) -- a row takes each
+//   pair exactly once -- which halves its width.
+// md / ad, the diagonal words, are registers in both.
+template <bool REG, bool VSYM>
+struct Words {
+  unsigned long long R, C;
+  char *tb;
+  uint32_t md, ad;
 
-// XOR value bits d into the words of the cell described by `info`.
-template <bool VSYM>
-__device__ __forceinline__ void toggle(char *tb, uint32_t info, uint32_t d,
-                                       uint32_t &md, uint32_t &ad, int n) {
-  const uint32_t dm = mirror<VSYM>(d, n);
-  word_at(tb, info & 0xfffcu) ^= d ^ dm;
-  word_at(tb, (info >> 16) & 0xfffcu) ^= d;
-  const bool onmd = (info & 1u) != 0, onad = (info & 0x10000u) != 0;
-  // with vertical symmetry the mirror of a main-diagonal cell is on the
-  // anti-diagonal and vice versa
-  md ^= (onmd ? d : 0u) ^ ((VSYM && onad) ? dm : 0u);
-  ad ^= (onad ? d : 0u) ^ ((VSYM && onmd) ? dm : 0u);
-}
+  __device__ static uint32_t describe(const KParams &p, int pos, int diag,
+                                      unsigned B) {
+    const int i = p.ci[pos], j = p.cj[pos];
+    const uint32_t m = (diag && i == j) ? 1u : 0u;
+    const uint32_t a = (diag && i + j == p.n - 1) ? 1u : 0u;
+    if (REG)
+      return (uint32_t)(i * p.wr) | ((uint32_t)(j * p.wc) << 8) | (m << 16) | (a << 17);
+    const uint32_t roff = (uint32_t)i * B * 4u;
+    const uint32_t coff = (uint32_t)(p.n + j) * B * 4u;
+    return roff | m | ((coff | a) << 16);
+  }
+  __device__ static bool on_md(uint32_t info) {
+    return REG ? ((info >> 16) & 1u) != 0 : (info & 1u) != 0;
+  }
+  __device__ static bool on_ad(uint32_t info) {
+    return REG ? ((info >> 17) & 1u) != 0 : ((info >> 16) & 1u) != 0;
+  }
+  // Admissible values of the cell: ALL & ~(row | col | md | ad).
+  __device__ uint32_t cands(uint32_t info, const KParams &p) const {
+    uint32_t f;
+    if (REG) {
+      uint32_t r = (uint32_t)(R >> (info & 63u));
+      if (VSYM) {
+        r &= p.pairmask;
+        r |= mirror<true>(r, p.n);
+      }
+      f = r | (uint32_t)(C >> ((info >> 8) & 63u));
+    } else {
+      f = word_at(tb, info & 0xfffcu) | word_at(tb, (info >> 16) & 0xfffcu);
+    }
+    f |= on_md(info) ? md : 0u;
+    f |= on_ad(info) ? ad : 0u;
+    return p.all & ~f;
+  }
+  // XOR value bits d (the old value and/or the new one) into the words of the
+  // cell; with vertical symmetry the mirror cell (i, n-1-j) takes n-1-v, and
+  // the mirror of a main-diagonal cell lies on the anti-diagonal and vice
+  // versa.
+  __device__ void toggle(uint32_t info, uint32_t d, const KParams &p) {
+    const uint32_t dm = mirror<VSYM>(d, p.n);
+    if (REG) {
+      const uint32_t rd = VSYM ? ((d ^ dm) & p.pairmask) : d;
+      R ^= (unsigned long long)rd << (info & 63u);
+      C ^= (unsigned long long)d << ((info >> 8) & 63u);
+    } else {
+      word_at(tb, info & 0xfffcu) ^= d ^ dm;
+      word_at(tb, (info >> 16) & 0xfffcu) ^= d;
+    }
+    const bool onmd = on_md(info), onad = on_ad(info);
+    md ^= (onmd ? d : 0u) ^ ((VSYM && onad) ? dm : 0u);
+    ad ^= (onad ? d : 0u) ^ ((VSYM && onmd) ? dm : 0u);
+  }
+  __device__ void clear(const KParams &p, unsigned B) {
+    md = ad = 0u;
+    if (REG) {
+      R = C = 0ull;
+    } else {
+      for (int w = 0; w < 2 * p.n; ++w) word_at(tb, (uint32_t)w * B * 4u) = 0u;
+    }
+  }
+};
+
+// Per-lane search state.
+template <bool REG, bool VSYM>
+struct Lane {
+  Words<REG, VSYM> w;
+  int p;                 // current order position
+  uint32_t L;            // untried candidates at p
+  uint32_t v;            // value placed at p (one-hot), 0 = none yet
+  uint32_t info;         // cell descriptor of p
+  uint32_t splitc;       // nodes met at split_pos so far
+  uint32_t sub;          // residue class of split nodes this item keeps
+  long long prefix;      // prefix index of the current item
+  unsigned long long cnt;    // completions found for the current item
+  unsigned long long nodes;  // placements made (node counting variant)
+};
 
 // One search iteration.  Returns true when the lane's item is finished.
-template <bool VSYM, bool NODES>
-__device__ __forceinline__ bool dfs_step(Lane &s, const KParams &p, char *tb,
+//
+// Written without data-dependent branches so that the lanes of a warp -- each
+// at its own position of its own subtree -- stay converged: every lane
+// computes the candidates of the next cell, and the outcome (descend, dead
+// end, last cell, exhausted level) only selects which registers change and
+// whether the stack is written or read.
+template <bool REG, bool VSYM, bool NODES, bool SPLIT>
+__device__ __forceinline__ bool dfs_step(Lane<REG, VSYM> &s, const KParams &p,
                                          uint32_t *stk, const uint32_t *tbl,
-                                         int lane, unsigned B) {
+                                         unsigned B) {
   const uint32_t nv = s.L & (0u - s.L);
-  toggle<VSYM>(tb, s.info, s.v ^ nv, s.md, s.ad, p.n);
+  s.w.toggle(s.info, s.v ^ nv, p);
   s.L ^= nv;
   s.v = nv;
-  if (nv == 0u) {
-    if (--s.p < p.depth) return true;
-    const uint32_t w = stk[(s.p - p.depth) * B];
-    s.L = w & 0xffffu;
-    s.v = w >> 16;
-    s.info = tbl[s.p * 32 + lane];
-    return false;
+  const bool pop = nv == 0u;
+  bool skip = false;
+  if (SPLIT) {
+    const bool at = (s.p == p.split_pos) && !pop;
+    skip = at && ((s.splitc & ((1u << p.lanes_log2) - 1u)) != s.sub);
+    s.splitc += at ? 1u : 0u;
+    if (NODES && !pop && !skip && (s.p >= p.split_pos || s.sub == 0u)) s.nodes++;
+  } else if (NODES && !pop) {
+    s.nodes++;
   }
-  if (s.p == p.split_pos) {
-    const uint32_t c = s.splitc++;
-    if ((c & ((1u << p.lanes_log2) - 1u)) != s.sub) return false;
-    if (NODES) s.nodes++;
-  } else if (NODES) {
-    if (s.p > p.split_pos || s.sub == 0u) s.nodes++;
+  const int q = s.p + 1;  // <= last: a lane never stands on the last cell
+  const uint32_t info1 = tbl[q];
+  const uint32_t L1 = s.w.cands(info1, p);
+  const bool live = !pop && !skip;
+  const bool leaf = q == p.last;
+  const unsigned leaves = (live && leaf) ? (unsigned)__popc(L1) : 0u;
+  s.cnt += leaves;
+  if (NODES) s.nodes += leaves;
+  const bool down = live && !leaf && L1 != 0u;
+  if (down) stk[(s.p - p.depth) * B] = s.L | (s.v << 16);
+  const int pp = s.p - 1;
+  const bool up = pop && pp >= p.depth;
+  uint32_t e = 0u, infoP = 0u;
+  if (up) {
+    e = stk[(pp - p.depth) * B];
+    infoP = tbl[pp];
   }
-  const int q = s.p + 1;
-  const uint32_t info1 = tbl[q * 32 + lane];
-  const uint32_t L1 = cands(tb, info1, s.md, s.ad, p.all);
-  if (q == p.last) {
-    s.cnt += (unsigned)__popc(L1);
-    if (NODES) s.nodes += (unsigned)__popc(L1);
-    return false;
-  }
-  if (L1 == 0u) return false;
-  stk[(s.p - p.depth) * B] = s.L | (s.v << 16);
-  s.p = q;
-  s.L = L1;
-  s.v = 0u;
-  s.info = info1;
-  return false;
+  s.p = down ? q : (pop ? pp : s.p);
+  s.L = down ? L1 : (up ? (e & 0xffffu) : s.L);
+  s.v = down ? 0u : (up ? (e >> 16) : s.v);
+  s.info = down ? info1 : (up ? infoP : s.info);
+  return pop && !up;
 }
 
 // Load work item `item` into the lane.  Returns true if it is already
 // finished (invalid prefix, or nothing left to search).
-template <bool VSYM, bool NODES>
-__device__ bool load_item(Lane &s, const KParams &p, long long item, char *tb,
-                          const uint32_t *tbl, int lane, unsigned B) {
+template <bool REG, bool VSYM, bool NODES>
+__device__ bool load_item(Lane<REG, VSYM> &s, const KParams &p, long long item,
+                          const uint32_t *tbl, unsigned B) {
   s.prefix = item >> p.lanes_log2;
   s.sub = (uint32_t)(item & ((1ll << p.lanes_log2) - 1));
   s.cnt = 0ull;
   s.splitc = 0u;
-  s.md = s.ad = 0u;
-  for (int w = 0; w < 2 * p.n; ++w) word_at(tb, (uint32_t)w * B * 4u) = 0u;
+  s.w.clear(p, B);
   const uint8_t *rec = p.prefixes + (size_t)s.prefix * (size_t)p.depth;
   for (int t = 0; t < p.depth; ++t) {
     const uint32_t val = rec[t];
-    const uint32_t info = tbl[t * 32 + lane];
+    const uint32_t info = tbl[t];
     const uint32_t b = (val < (uint32_t)p.n) ? (1u << val) : 0u;
-    if ((cands(tb, info, s.md, s.ad, p.all) & b) == 0u) return true;
-    toggle<VSYM>(tb, info, b, s.md, s.ad, p.n);
+    if ((s.w.cands(info, p) & b) == 0u) return true;
+    s.w.toggle(info, b, p);
   }
   if (p.depth == p.order_len) {
     s.cnt = (s.sub == 0u) ? 1ull : 0ull;
     return true;
   }
-  const uint32_t info = tbl[p.depth * 32 + lane];
-  const uint32_t L = cands(tb, info, s.md, s.ad, p.all);
+  const uint32_t info = tbl[p.depth];
+  const uint32_t L = s.w.cands(info, p);
   if (p.depth == p.last) {
     if (s.sub == 0u) {
       s.cnt = (unsigned)__popc(L);
@@ -214,14 +270,15 @@ __device__ bool load_item(Lane &s, const KParams &p, long long item, char *tb,
   return L == 0u;
 }
 
-__device__ __forceinline__ void flush_item(const Lane &s, const KParams &p,
-                                           unsigned long long &lane_total) {
-  lane_total += s.cnt;
+__device__ __forceinline__ void flush_count(long long prefix, unsigned long long cnt,
+                                            const KParams &p,
+                                            unsigned long long &lane_total) {
+  lane_total += cnt;
   if (p.counts != nullptr) {
     if (p.count_store)
-      p.counts[s.prefix] = s.cnt;
-    else if (s.cnt)
-      atomicAdd(p.counts + s.prefix, s.cnt);
+      p.counts[prefix] = cnt;
+    else if (cnt)
+      atomicAdd(p.counts + prefix, cnt);
   }
 }
 
@@ -240,41 +297,55 @@ __device__ void block_reduce_add(unsigned long long v, unsigned long long *dst,
   }
 }
 
-// Shared memory: [table: order_len * 32 words][state: (2n + stack) * B words]
-__device__ __forceinline__ void build_table(const KParams &p, uint32_t *tbl,
-                                            int diag) {
+// Shared memory: [table: order_len words, the cell descriptor of each position]
+//                [words: 2n * B, shared-memory variant only]
+//                [stack: (last - depth) * B]
+template <bool REG, bool VSYM>
+__device__ __forceinline__ void setup(const KParams &p, int diag, uint32_t *smem,
+                                      const uint32_t *&tbl, uint32_t *&stk,
+                                      Lane<REG, VSYM> &s) {
   const unsigned B = blockDim.x;
-  for (int idx = threadIdx.x; idx < p.order_len * 32; idx += B)
-    tbl[idx] = cell_info(p, idx >> 5, diag, B);
+  uint32_t *t = smem;
+  for (int idx = threadIdx.x; idx < p.order_len; idx += B)
+    t[idx] = Words<REG, VSYM>::describe(p, idx, diag, B);
+  uint32_t *st = smem + ((p.order_len + 31) & ~31);
+  s.w.tb = reinterpret_cast<char *>(st + threadIdx.x);
+  stk = st + (REG ? 0 : 2 * p.n * (int)B) + threadIdx.x;
+  tbl = t;
+  s.nodes = 0ull;
+  s.prefix = 0;
+  s.sub = 0u;
+  s.p = 0;
+  s.L = s.v = s.info = 0u;
+  s.cnt = 0ull;
+  s.w.md = s.w.ad = 0u;
+  s.w.R = s.w.C = 0ull;
+  __syncthreads();
 }
 
-template <bool VSYM, bool NODES>
+template <bool REG, bool VSYM, bool NODES, bool SPLIT>
 __global__ void __launch_bounds__(512) k_plain(const __grid_constant__ KParams p,
                                                int diag) {
   extern __shared__ uint32_t smem[];
   __shared__ unsigned long long red[16];
   const unsigned B = blockDim.x;
   const int lane = threadIdx.x & 31;
-  uint32_t *tbl = smem;
-  uint32_t *st = smem + p.order_len * 32;
-  build_table(p, tbl, diag);
-  __syncthreads();
-  char *tb = reinterpret_cast<char *>(st + threadIdx.x);
-  uint32_t *stk = st + 2 * p.n * B + threadIdx.x;
+  const uint32_t *tbl;
+  uint32_t *stk;
+  Lane<REG, VSYM> s;
+  setup(p, diag, smem, tbl, stk, s);
 
-  Lane s;
-  s.nodes = 0ull;
   unsigned long long lane_total = 0ull;
   const long long item = (long long)blockIdx.x * B + threadIdx.x;
   bool busy = false;
   if (item < p.n_items) {
-    busy = !load_item<VSYM, NODES>(s, p, item, tb, tbl, lane, B);
-    if (!busy) flush_item(s, p, lane_total);
+    busy = !load_item<REG, VSYM, NODES>(s, p, item, tbl, B);
+    if (!busy) flush_count(s.prefix, s.cnt, p, lane_total);
   }
   while (__any_sync(FULL, busy)) {
-    if (busy && dfs_step<VSYM, NODES>(s, p, tb, stk, tbl, lane, B)) {
+    if (busy && dfs_step<REG, VSYM, NODES, SPLIT>(s, p, stk, tbl, B)) {
       busy = false;
-      flush_item(s, p, lane_total);
+      flush_count(s.prefix, s.cnt, p, lane_total);
     }
   }
   block_reduce_add(lane_total, p.total, red);
@@ -292,10 +363,9 @@ __device__ __forceinline__ int nth_set_bit(unsigned m, int r) {
 // or below the item split); the idle lane copies the busy lane's words and
 // path, undoes its placements below pd and takes the untried candidates of
 // pd, which the busy lane gives up.
-template <bool VSYM>
-__device__ void donate(Lane &s, bool &busy, const KParams &p, char *tb,
-                       uint32_t *stk, uint32_t *st, const uint32_t *tbl,
-                       int lane, unsigned B) {
+template <bool REG, bool VSYM>
+__device__ void donate(Lane<REG, VSYM> &s, bool &busy, const KParams &p,
+                       uint32_t *stk, const uint32_t *tbl, int lane, unsigned B) {
   const unsigned idle = __ballot_sync(FULL, !busy);
   if (idle == 0u || idle == FULL) return;
   const int lo = max(p.depth, p.split_pos + 1);
@@ -303,11 +373,11 @@ __device__ void donate(Lane &s, bool &busy, const KParams &p, char *tb,
   uint32_t Lpd = 0u, vpd = 0u;
   if (busy) {
     for (int q = lo; q < s.p; ++q) {
-      const uint32_t w = stk[(q - p.depth) * B];
-      if (w & 0xffffu) {
+      const uint32_t e = stk[(q - p.depth) * B];
+      if (e & 0xffffu) {
         pd = q;
-        Lpd = w & 0xffffu;
-        vpd = w >> 16;
+        Lpd = e & 0xffffu;
+        vpd = e >> 16;
         break;
       }
     }
@@ -330,37 +400,43 @@ __device__ void donate(Lane &s, bool &busy, const KParams &p, char *tb,
       receiver = true;
     }
   } else if (pd >= 0) {
-    const int r = __popc(donors & below);
-    giver = r < pairs;
+    giver = __popc(donors & below) < pairs;
   }
   const int d_pd = __shfl_sync(FULL, pd, partner);
   const uint32_t d_L = __shfl_sync(FULL, Lpd, partner);
   const uint32_t d_vpd = __shfl_sync(FULL, vpd, partner);
   const int d_p = __shfl_sync(FULL, s.p, partner);
   const uint32_t d_v = __shfl_sync(FULL, s.v, partner);
-  const uint32_t d_md = __shfl_sync(FULL, s.md, partner);
-  const uint32_t d_ad = __shfl_sync(FULL, s.ad, partner);
+  const uint32_t d_md = __shfl_sync(FULL, s.w.md, partner);
+  const uint32_t d_ad = __shfl_sync(FULL, s.w.ad, partner);
+  const unsigned long long d_R = __shfl_sync(FULL, s.w.R, partner);
+  const unsigned long long d_C = __shfl_sync(FULL, s.w.C, partner);
   const long long d_prefix = __shfl_sync(FULL, s.prefix, partner);
   const uint32_t d_sub = __shfl_sync(FULL, s.sub, partner);
   if (receiver) {
     const int dl = partner - lane;  // donor's thread offset from this one
-    const uint32_t *dst_words = st + (threadIdx.x + dl);
-    uint32_t *my_words = st + threadIdx.x;
-    for (int w = 0; w < 2 * p.n; ++w) my_words[w * B] = dst_words[w * B];
+    if (REG) {
+      s.w.R = d_R;
+      s.w.C = d_C;
+    } else {
+      uint32_t *mine = reinterpret_cast<uint32_t *>(s.w.tb);
+      const uint32_t *theirs = mine + dl;
+      for (int w = 0; w < 2 * p.n; ++w) mine[w * B] = theirs[w * B];
+    }
     const uint32_t *dstk = stk + dl;
     for (int q = p.depth; q < d_pd; ++q)
       stk[(q - p.depth) * B] = dstk[(q - p.depth) * B] & 0xffff0000u;
-    s.md = d_md;
-    s.ad = d_ad;
+    s.w.md = d_md;
+    s.w.ad = d_ad;
     // undo the donor's placements below pd
     for (int q = d_pd + 1; q <= d_p; ++q) {
       const uint32_t vq = (q < d_p) ? (dstk[(q - p.depth) * B] >> 16) : d_v;
-      if (vq) toggle<VSYM>(tb, tbl[q * 32 + lane], vq, s.md, s.ad, p.n);
+      if (vq) s.w.toggle(tbl[q], vq, p);
     }
     s.p = d_pd;
     s.L = d_L;
     s.v = d_vpd;
-    s.info = tbl[d_pd * 32 + lane];
+    s.info = tbl[d_pd];
     s.prefix = d_prefix;
     s.sub = d_sub;
     s.splitc = 0u;
@@ -377,26 +453,18 @@ __device__ void donate(Lane &s, bool &busy, const KParams &p, char *tb,
   __syncwarp();
 }
 
-template <bool VSYM, bool NODES>
+template <bool REG, bool VSYM, bool NODES, bool SPLIT>
 __global__ void __launch_bounds__(512)
     k_persistent(const __grid_constant__ KParams p, int diag) {
   extern __shared__ uint32_t smem[];
   __shared__ unsigned long long red[16];
   const unsigned B = blockDim.x;
   const int lane = threadIdx.x & 31;
-  uint32_t *tbl = smem;
-  uint32_t *st = smem + p.order_len * 32;
-  build_table(p, tbl, diag);
-  __syncthreads();
-  char *tb = reinterpret_cast<char *>(st + threadIdx.x);
-  uint32_t *stk = st + 2 * p.n * B + threadIdx.x;
+  const uint32_t *tbl;
+  uint32_t *stk;
+  Lane<REG, VSYM> s;
+  setup(p, diag, smem, tbl, stk, s);
 
-  Lane s;
-  s.nodes = 0ull;
-  s.prefix = 0;
-  s.sub = 0u;
-  s.p = 0;
-  s.L = s.v = s.md = s.ad = 0u;
   unsigned long long lane_total = 0ull;
   bool busy = false;
   bool qdone = false;
@@ -412,8 +480,8 @@ __global__ void __launch_bounds__(512)
       if (!busy) {
         const long long item = (long long)base + __popc(idle & ((1u << lane) - 1u));
         if (item < p.n_items) {
-          busy = !load_item<VSYM, NODES>(s, p, item, tb, tbl, lane, B);
-          if (!busy) flush_item(s, p, lane_total);
+          busy = !load_item<REG, VSYM, NODES>(s, p, item, tbl, B);
+          if (!busy) flush_count(s.prefix, s.cnt, p, lane_total);
         }
       }
       if ((long long)(base + (unsigned long long)nidle) >= p.n_items) qdone = true;
@@ -423,19 +491,19 @@ __global__ void __launch_bounds__(512)
     if (!qdone) {
       // run until some lane finishes its item
       do {
-        if (busy && dfs_step<VSYM, NODES>(s, p, tb, stk, tbl, lane, B)) {
+        if (busy && dfs_step<REG, VSYM, NODES, SPLIT>(s, p, stk, tbl, B)) {
           busy = false;
-          flush_item(s, p, lane_total);
+          flush_count(s.prefix, s.cnt, p, lane_total);
         }
       } while (__all_sync(FULL, busy));
     } else {
       for (int it = 0; it <= p.check_mask; ++it) {
-        if (busy && dfs_step<VSYM, NODES>(s, p, tb, stk, tbl, lane, B)) {
+        if (busy && dfs_step<REG, VSYM, NODES, SPLIT>(s, p, stk, tbl, B)) {
           busy = false;
-          flush_item(s, p, lane_total);
+          flush_count(s.prefix, s.cnt, p, lane_total);
         }
       }
-      if (p.donate) donate<VSYM>(s, busy, p, tb, stk, st, tbl, lane, B);
+      if (p.donate) donate<REG, VSYM>(s, busy, p, stk, tbl, lane, B);
     }
   }
   block_reduce_add(lane_total, p.total, red);
@@ -520,6 +588,7 @@ struct Shape {
   int split_pos;
   int donate;
   int check_mask;
+  int words;  // 0 auto, 1 shared memory, 2 registers
 };
 
 static int resolve_shape(const dls_launch_t *cfg, int depth, int last,
@@ -550,23 +619,53 @@ static int resolve_shape(const dls_launch_t *cfg, int depth, int last,
   int every = c.check_every ? c.check_every : 64;
   if (ilog2_exact(every) < 0) return DLS_ERR_BAD_ARG;
   sh->check_mask = every - 1;
+  sh->words = c.words;
+  if (sh->words < 0 || sh->words > 2) return DLS_ERR_BAD_ARG;
   return DLS_OK;
 }
 
-template <bool VSYM, bool NODES>
+template <bool REG, bool VSYM, bool NODES, bool SPLIT>
 static const void *kernel_ptr(int kind) {
-  return kind == DLS_KERNEL_PLAIN ? (const void *)k_plain<VSYM, NODES>
-                                  : (const void *)k_persistent<VSYM, NODES>;
+  return kind == DLS_KERNEL_PLAIN ? (const void *)k_plain<REG, VSYM, NODES, SPLIT>
+                                  : (const void *)k_persistent<REG, VSYM, NODES, SPLIT>;
 }
 
-static const void *pick_kernel(int kind, bool vsym, bool nodes) {
-  if (vsym) return nodes ? kernel_ptr<true, true>(kind) : kernel_ptr<true, false>(kind);
-  return nodes ? kernel_ptr<false, true>(kind) : kernel_ptr<false, false>(kind);
+template <bool REG, bool VSYM, bool NODES>
+static const void *pick3(int kind, bool split) {
+  return split ? kernel_ptr<REG, VSYM, NODES, true>(kind)
+               : kernel_ptr<REG, VSYM, NODES, false>(kind);
 }
 
-static size_t smem_bytes(int order_len, int n, int depth, int last, int block) {
+template <bool REG>
+static const void *pick2(int kind, bool vsym, bool nodes, bool split) {
+  if (vsym) return nodes ? pick3<REG, true, true>(kind, split) : pick3<REG, true, false>(kind, split);
+  return nodes ? pick3<REG, false, true>(kind, split) : pick3<REG, false, false>(kind, split);
+}
+
+static const void *pick_kernel(int kind, bool reg, bool vsym, bool nodes, bool split) {
+  return reg ? pick2<true>(kind, vsym, nodes, split) : pick2<false>(kind, vsym, nodes, split);
+}
+
+// Do all row words and all column words fit one 64-bit register each?
+// Field widths: 8 bits per row and column for n <= 8; with vertical
+// symmetry n/2 bits per row (value pairs) and n bits per left column.
+static bool words_fit_registers(int n, bool vsym, int *wr, int *wc) {
+  if (!vsym) {
+    if (n > 8) return false;
+    *wr = 8;
+    *wc = 8;
+    return true;
+  }
+  if (n % 2) return false;
+  *wr = n / 2;
+  *wc = n;
+  return n * (n / 2) <= 64;
+}
+
+static size_t smem_bytes(int order_len, int n, int depth, int last, int block,
+                         bool reg) {
   const int stack = std::max(0, last - depth);
-  return (size_t)order_len * 32u * 4u + (size_t)(2 * n + stack) * block * 4u;
+  return (size_t)((order_len + 31) & ~31) * 4u + (size_t)((reg ? 0 : 2 * n) + stack) * block * 4u;
 }
 
 // Validates, fills the parameter block and enqueues the whole pass on
@@ -608,6 +707,7 @@ static int enqueue_count(int n, uint32_t flags, const uint8_t *order,
   std::memset(&kp, 0, sizeof(kp));
   kp.n = n;
   kp.all = (1u << n) - 1u;
+  kp.pairmask = (1u << (n / 2)) - 1u;
   kp.order_len = order_len;
   kp.depth = depth;
   kp.last = order_len - 1;
@@ -628,17 +728,23 @@ static int enqueue_count(int n, uint32_t flags, const uint8_t *order,
   }
   const int diag = (flags & DLS_DIAGONAL) ? 1 : 0;
   const bool vsym = (flags & DLS_VSYM) != 0;
-  const void *fn = pick_kernel(sh.kernel, vsym, d_nodes != nullptr);
+  int wr = 0, wc = 0;
+  bool reg = words_fit_registers(n, vsym, &wr, &wc);
+  if (sh.words == 1) reg = false;
+  if (sh.words == 2 && !reg) return DLS_ERR_BAD_ARG;
+  kp.wr = wr;
+  kp.wc = wc;
+  const void *fn = pick_kernel(sh.kernel, reg, vsym, d_nodes != nullptr, sh.lanes_log2 > 0);
   DevInfo di;
   rc = dev_info(&di);
   if (rc) return rc;
   // static shared memory of the kernels: the 16-entry reduction buffer
   const size_t static_smem = 16 * sizeof(unsigned long long);
-  size_t smem = smem_bytes(order_len, n, depth, order_len - 1, sh.block);
+  size_t smem = smem_bytes(order_len, n, depth, order_len - 1, sh.block, reg);
   const bool default_block = cfg == nullptr || cfg->block_threads == 0;
   while (default_block && smem + static_smem > di.smem_optin && sh.block > 32) {
     sh.block /= 2;
-    smem = smem_bytes(order_len, n, depth, order_len - 1, sh.block);
+    smem = smem_bytes(order_len, n, depth, order_len - 1, sh.block, reg);
   }
   if (smem + static_smem > di.smem_optin) return DLS_ERR_NO_MEMORY;
   e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -40,6 +40,8 @@ SHAPES = [
     dict(donate=-1),
     dict(check_every=1),
     dict(blocks_per_sm=1, block_threads=64),
+    dict(words=1),
+    dict(words=1, lanes_per_prefix=2, block_threads=64),
 ]
 
 
@@ -81,13 +83,56 @@ def test_config2_order7_split10(dls):
     assert int(ref.sum()) == oracle.count(7, D, orders.md_ad_rows(7), orders.identity(7))[0]
 
 
+@pytest.mark.parametrize("n,flags,rows", [(9, D, 4), (10, D, 5), (11, D, 6), (12, D, 7),
+                                          (12, D | V, 6), (10, D | V, 4), (9, 0, 6),
+                                          (10, D, 7)])
+def test_larger_orders_from_sampled_partial_squares(dls, n, flags, rows):
+    """Orders above 8 (row and column words in shared memory, or register
+    fields for symmetric order 10): a few random partial squares with
+    `rows` rows filled, decoded from the same seeded draws by both sides."""
+    import dls_inputs
+    vs = bool(flags & V)
+    order = dls.fill_order(n, flags, first_rows=rows)
+    o_order = orders.md_ad_rows(n, vsym=vs, first_rows=rows)
+    assert [tuple(c) for c in order] == o_order
+    depth = rows * len(orders.identity(n, vs))
+    pre, o_pre = [], []
+    for k in range(6):
+        draws = dls_inputs.draws(1 << 14, seed=n * 100 + rows, stream=k)
+        a, ua = dls.sample_prefix(n, flags, order, depth, draws)
+        b, ub = oracle.sample_prefix(n, flags, o_order, depth, draws)
+        assert ua == ub
+        if b is None:
+            continue
+        assert (a == b).all()
+        pre.append(a)
+        o_pre.append(b)
+    assert pre
+    pre, o_pre = np.array(pre), np.array(o_pre)
+    ref, _ = oracle.count_many(n, flags, o_order, o_pre, threads=THREADS)
+    if rows < n - 3:
+        assert (ref > 0).any()
+    for sh in (dict(), dict(words=1), dict(lanes_per_prefix=8), dict(kernel=dls.KERNEL_PLAIN)):
+        c = _gpu_counts(dls, n, flags, order, pre, dls.Launch(**sh))
+        assert (c == ref).all(), sh
+
+
+def test_register_words_refused_when_they_do_not_fit(dls):
+    order = dls.fill_order(9, D)
+    t = torch.from_numpy(np.arange(9, dtype=np.uint8)[None]).cuda()
+    with pytest.raises(dls.DlsError) as e:
+        dls.count(9, D, order, t, launch=dls.Launch(words=2))
+    assert e.value.code == 3
+
+
 def test_node_counts_match_oracle(dls):
     for n, flags, after in ((6, D, 0), (7, D, 10), (6, D | V, 3), (5, 0, 5)):
         wl = gpu_cases.split(dls, n, flags, after)
         ref_c, ref_n = oracle.count_many(n, flags, wl.oracle_order, wl.oracle_prefixes,
                                          threads=THREADS)
         t = torch.from_numpy(wl.prefixes).cuda()
-        for sh in (dict(), dict(lanes_per_prefix=4), dict(kernel=dls.KERNEL_PLAIN)):
+        for sh in (dict(), dict(lanes_per_prefix=4), dict(kernel=dls.KERNEL_PLAIN),
+                   dict(words=1)):
             nodes = torch.zeros(1, dtype=torch.uint64, device="cuda")
             c = dls.count(n, flags, wl.order, t, nodes=nodes, launch=dls.Launch(**sh))
             torch.cuda.synchronize()

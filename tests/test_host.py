@@ -65,6 +65,30 @@ def test_heuristic_order_is_a_permutation_and_counts_agree(dls, n):
         assert oracle.count(n, D, o, orders.identity(n))[0] == ref
 
 
+@pytest.mark.parametrize("n,flags,keep", [(9, D, 9), (8, D, 28), (8, D, 15), (7, D, 20),
+                                          (10, D | V, 15), (8, D | V, 4), (6, 0, 6), (6, D, 0)])
+def test_order_completion_matches_oracle(dls, n, flags, keep):
+    vs = bool(flags & V)
+    base = dls.fill_order(n, flags)
+    got = [tuple(c) for c in dls.order_complete(n, flags, base, keep, dls.ORDER_HEURISTIC)]
+    ref = orders.heuristic_complete(n, [tuple(c) for c in base[:keep]], bool(flags & D), vs)
+    assert got == ref
+    assert got[:keep] == [tuple(c) for c in base[:keep]]
+    assert sorted(got) == sorted(orders.row_major(n, vsym=vs))
+    got2 = [tuple(c) for c in dls.order_complete(n, flags, base, keep, dls.ORDER_MD_AD_ROWS)]
+    assert sorted(got2) == sorted(got) and got2[:keep] == got[:keep]
+
+
+def test_order_completion_keeps_counts(dls):
+    for n, flags, keep in ((6, D, 10), (7, D, 14), (6, D | V, 6)):
+        vs = bool(flags & V)
+        base = dls.fill_order(n, flags)
+        h = [tuple(c) for c in dls.order_complete(n, flags, base, keep, dls.ORDER_HEURISTIC)]
+        ref = oracle.count(n, flags, orders.md_ad_rows(n, vsym=vs), orders.identity(n, vs))
+        got = oracle.count(n, flags, h, orders.identity(n, vs))
+        assert got[0] == ref[0]
+
+
 @pytest.mark.parametrize("n,flags,extra", [(6, D, 0), (6, D, 5), (6, D, 12), (7, D, 10),
                                            (8, D, 7), (6, D | V, 4), (8, D | V, 6),
                                            (5, 0, 6), (6, D, 30)])
