@@ -241,6 +241,66 @@ int dls_count_host(int n, uint32_t flags, const uint8_t *order,
                    dls_u128 *total_out, const dls_launch_t *cfg,
                    void *stream);
 
+/* ------------------------------------------------------------ serving */
+
+/* A continuous-batching server for counting jobs of mixed order, flags and
+ * prefix (the job answer is Count(prefix), as for dls_count).  Jobs are split
+ * on the host into work items (the prefix split of Section 5.2, extended
+ * until a job has items_per_job items), wait in arrival order, and are
+ * admitted at an epoch boundary when a job slot, enough free chunks of the
+ * device item arena (the memory budget) and queue room are free.  Each
+ * dls_server_step() reads the results of the previous epoch, admits, and
+ * launches one epoch: every lane of a resident grid resumes the search it
+ * saved in device memory, or takes the next queued item of any job, runs
+ * `budget` search iterations and saves what is unfinished.  Search stacks
+ * and per-job counters stay on the device; jobs that arrive while others run
+ * share the GPU with them from the next epoch on.  One server uses one CUDA
+ * stream of its own and is driven from one host thread at a time. */
+typedef struct dls_server dls_server;
+
+typedef struct {
+    int max_jobs;          /* device job slots (default 1024)                */
+    size_t arena_bytes;    /* device memory for queued items (default 64 MiB)*/
+    size_t chunk_bytes;    /* arena allocation unit (default 64 KiB)         */
+    int64_t queue_items;   /* work-queue ring capacity (default 4 Mi)        */
+    int max_order;         /* largest n a job may have (default 10)          */
+    int budget;            /* search iterations per lane per epoch (4096)    */
+    int block_threads;     /* 32..256 (default 128)                          */
+    int blocks_per_sm;     /* 0 = as many as fit                             */
+    int items_per_job;     /* split target per job (default 512)             */
+} dls_server_cfg;
+
+typedef struct {
+    int64_t submitted, admitted, completed, pending, active, epochs;
+    uint64_t squares;      /* sum of the counts of completed jobs            */
+    int64_t lanes;         /* lanes of the resident grid                     */
+    size_t device_bytes;   /* device memory held by the server               */
+    size_t free_arena_bytes;
+} dls_server_stats;
+
+/* Fills *cfg with the defaults above. */
+void dls_server_default_cfg(dls_server_cfg *cfg);
+/* Allocates the server's device memory (cfg NULL = defaults) on the current
+ * device.  Errors: BAD_ARG, NO_MEMORY, CUDA. */
+int dls_server_create(const dls_server_cfg *cfg, dls_server **out);
+/* Queues a job (host arguments, copied; conventions as dls_count with one
+ * prefix of `depth` bytes).  *job_id receives its id.  A job whose prefix is
+ * invalid, or that leaves nothing to search, completes at once.  Errors:
+ * INVALID_N (also n > max_order), BAD_ORDER, BAD_ARG, CAPACITY (the job's
+ * items exceed the whole arena or queue). */
+int dls_server_submit(dls_server *srv, int n, uint32_t flags,
+                      const uint8_t *order, int order_len,
+                      const uint8_t *prefix, int depth, int64_t *job_id);
+/* One epoch (see above).  Blocks only to read the previous epoch's results. */
+int dls_server_step(dls_server *srv);
+/* Moves up to cap completed jobs (ids and exact counts) out of the server;
+ * *n_done receives how many. */
+int dls_server_poll(dls_server *srv, int64_t *ids, uint64_t *counts, int cap,
+                    int *n_done);
+int dls_server_get_stats(dls_server *srv, dls_server_stats *out);
+/* Waits for the running epoch and frees everything. */
+void dls_server_destroy(dls_server *srv);
+
 /* Allocation-free variant of dls_count_host() -- the paper has no
  * counterpart; it exists for callers that cannot let a library call
  * cudaMalloc: programs whose own pool already owns the device memory, and

@@ -87,7 +87,7 @@ def heuristic_complete(n, kept, diagonal=True, vsym=False):
     one unassigned cell in one of its lines (row, column, main diagonal,
     anti-diagonal, looked at in that order), that cell is taken next
     (first-in first-out).  With vsym only left-half cells exist: a row has
-    N/2 of them, a column N, and the diagonals form one line made of the
+    N//2 of them, a column N, and the diagonals form one line made of the
     left cells on either diagonal.  Returns kept + the appended cells."""
     w = n // 2 if vsym else n
     lines = [[(i, j) for j in range(w)] for i in range(n)]
@@ -96,7 +96,9 @@ def heuristic_complete(n, kept, diagonal=True, vsym=False):
         lines.append([(i, i) for i in range(n)])
         lines.append([(i, n - 1 - i) for i in range(n)])
     elif diagonal and vsym:
-        lines.append([(i, i) if i < w else (i, n - 1 - i) for i in range(n)])
+        # left cells of the main diagonal (upper rows) and of the
+        # anti-diagonal (lower rows); an odd order's centre is not a left cell
+        lines.append([(i, i) for i in range(w)] + [(i, n - 1 - i) for i in range(n - w, n)])
     of_cell = {}
     for li, line in enumerate(lines):
         for c in line:

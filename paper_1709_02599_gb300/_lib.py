@@ -46,6 +46,26 @@ class LaunchT(ctypes.Structure):
                 ("words", ctypes.c_int)]
 
 
+class ServerCfg(ctypes.Structure):
+    _fields_ = [("max_jobs", ctypes.c_int),
+                ("arena_bytes", ctypes.c_size_t),
+                ("chunk_bytes", ctypes.c_size_t),
+                ("queue_items", ctypes.c_int64),
+                ("max_order", ctypes.c_int),
+                ("budget", ctypes.c_int),
+                ("block_threads", ctypes.c_int),
+                ("blocks_per_sm", ctypes.c_int),
+                ("items_per_job", ctypes.c_int)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64),
+                ("completed", ctypes.c_int64), ("pending", ctypes.c_int64),
+                ("active", ctypes.c_int64), ("epochs", ctypes.c_int64),
+                ("squares", ctypes.c_uint64), ("lanes", ctypes.c_int64),
+                ("device_bytes", ctypes.c_size_t), ("free_arena_bytes", ctypes.c_size_t)]
+
+
 class DlsError(RuntimeError):
     def __init__(self, code, what):
         self.code = code
@@ -92,6 +112,13 @@ def load():
         "dls_count_host_noalloc": (c_int, [c_int, c_u32, u8p, c_int, vp, c_int, c_i64, vp,
                                            ctypes.POINTER(U128), ctypes.POINTER(LaunchT), vp]),
         "dls_release": (None, []),
+        "dls_server_default_cfg": (None, [ctypes.POINTER(ServerCfg)]),
+        "dls_server_create": (c_int, [ctypes.POINTER(ServerCfg), ctypes.POINTER(vp)]),
+        "dls_server_submit": (c_int, [vp, c_int, c_u32, u8p, c_int, u8p, c_int, i64p]),
+        "dls_server_step": (c_int, [vp]),
+        "dls_server_poll": (c_int, [vp, i64p, u64p, c_int, ctypes.POINTER(c_int)]),
+        "dls_server_get_stats": (c_int, [vp, ctypes.POINTER(ServerStats)]),
+        "dls_server_destroy": (None, [vp]),
         "dls_plan_create": (c_int, [ctypes.POINTER(vp), c_int, c_u32, u8p, c_int, vp,
                                     c_int, c_i64, vp, vp, ctypes.POINTER(LaunchT)]),
         "dls_plan_launch": (c_int, [vp, vp]),

@@ -180,8 +180,13 @@ static void order_heuristic(int n, bool diag, bool vsym,
     lines.push_back(m);
     lines.push_back(a);
   } else if (diag && vsym) {
+    // left cells of the main diagonal (rows above the middle) and of the
+    // anti-diagonal (rows below it); an odd order's centre is not a left cell
     std::vector<std::pair<int, int>> m;
-    for (int i = 0; i < n; ++i) m.push_back(i < w ? std::make_pair(i, i) : std::make_pair(i, n - 1 - i));
+    for (int i = 0; i < n; ++i) {
+      if (i < w) m.push_back({i, i});
+      else if (i >= n - w) m.push_back({i, n - 1 - i});
+    }
     lines.push_back(m);
   }
   for (int l = 0; l < (int)lines.size(); ++l)

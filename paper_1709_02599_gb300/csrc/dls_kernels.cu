@@ -329,7 +329,6 @@ __global__ void __launch_bounds__(512) k_plain(const __grid_constant__ KParams p
   extern __shared__ uint32_t smem[];
   __shared__ unsigned long long red[16];
   const unsigned B = blockDim.x;
-  const int lane = threadIdx.x & 31;
   const uint32_t *tbl;
   uint32_t *stk;
   Lane<REG, VSYM> s;

@@ -1,0 +1,679 @@
+// dls_serve.cu -- continuous-batching server for counting jobs of mixed
+// order, flags and prefix.
+//
+// A job is one count: an order n, flags, a fill order and one prefix; its
+// answer is Count(prefix) as defined in dls.h.  At submission the host splits
+// the job into work items -- the valid extensions of its prefix a few cells
+// deeper (the prefix split of Section 5.2) -- and queues it.  Each call of
+// dls_server_step() is one epoch:
+//   1. results of the previous epoch are read: a job whose items are all
+//      finished is complete, and its job slot and arena chunks are freed;
+//   2. queued jobs are admitted in arrival order while a job slot, enough
+//      free chunks of the device item arena (the memory budget) and queue
+//      room are available; their items are copied to the arena and appended
+//      to the device work queue;
+//   3. one launch of k_serve runs every lane of a resident grid for a fixed
+//      number of search iterations.  A lane resumes the search it saved at
+//      the end of the previous epoch, or takes the next queued item of any
+//      job; when an item is finished its count is added to the job's counter
+//      and the job's remaining-item counter is decremented.  At the end of
+//      the epoch every unfinished search (position, candidate stack, row /
+//      column / diagonal words, partial count) is written back to the lane's
+//      slot in device memory.
+// Jobs that arrive while others are on the GPU therefore start at the next
+// epoch boundary and share the device with them; search stacks and counters
+// stay on the device between epochs.  The search itself is Algorithm 4 as in
+// dls_kernels.cu, with the order, flags and size read per lane from the job
+// table so that lanes of one warp may work on different jobs.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "dls_internal.h"
+
+namespace dls {
+
+constexpr int SV_WORDS = 2 * DLS_MAX_N;   // row words 0..15, column words 16..31
+constexpr int SV_HDR = 10;                // slot header words
+
+struct ServeJob {            // device job descriptor
+  int n;
+  uint32_t flags;
+  int depth;                 // length of the job's item prefixes
+  int order_len;
+  uint8_t ci[DLS_MAX_CELLS];
+  uint8_t cj[DLS_MAX_CELLS];
+};
+
+struct ServeParams {
+  const ServeJob *jobs;
+  unsigned long long *job_count;   // per slot: completions found so far
+  unsigned int *job_left;          // per slot: items not finished
+  const uint8_t *arena;            // item prefixes
+  const uint2 *queue;              // (job slot, arena byte offset)
+  unsigned long long *head;        // items handed out (device counter)
+  unsigned long long tail;         // items queued so far
+  unsigned long long qcap;         // queue ring capacity
+  uint32_t *slots;                 // lane slots, word w of lane g at w * G + g
+  long long G;                     // lanes in the grid
+  int stack_words;                 // stack capacity of a slot
+  int budget;                      // search iterations per lane per epoch
+};
+
+// Cell descriptor for the server: byte offsets of the row word (i) and the
+// column word (16 + j) from the lane's first word, diagonal flags in bits 0
+// and 16 (as in dls_kernels.cu, with a fixed row/column split).
+__device__ __forceinline__ uint32_t sv_describe(const ServeJob &job, int pos,
+                                                unsigned B) {
+  const int i = job.ci[pos], j = job.cj[pos];
+  const bool diag = (job.flags & DLS_DIAGONAL) != 0;
+  const uint32_t m = (diag && i == j) ? 1u : 0u;
+  const uint32_t a = (diag && i + j == job.n - 1) ? 1u : 0u;
+  return ((uint32_t)i * B * 4u) | m | ((((uint32_t)(DLS_MAX_N + j) * B * 4u) | a) << 16);
+}
+
+__device__ __forceinline__ uint32_t &sv_word(char *tb, uint32_t off) {
+  return *reinterpret_cast<uint32_t *>(tb + off);
+}
+
+__device__ __forceinline__ uint32_t sv_cands(char *tb, uint32_t info, uint32_t md,
+                                             uint32_t ad, uint32_t all) {
+  uint32_t f = sv_word(tb, info & 0xfffcu) | sv_word(tb, (info >> 16) & 0xfffcu);
+  f |= (info & 1u) ? md : 0u;
+  f |= (info & 0x10000u) ? ad : 0u;
+  return all & ~f;
+}
+
+// XOR value bits d into the cell's words; vertical symmetry puts n-1-v into
+// the mirror cell (same row; the mirror of a main-diagonal cell is on the
+// anti-diagonal and vice versa).
+__device__ __forceinline__ void sv_toggle(char *tb, uint32_t info, uint32_t d,
+                                          uint32_t &md, uint32_t &ad, int n,
+                                          bool vsym) {
+  const uint32_t dm = vsym ? (__brev(d) >> (32 - n)) : 0u;
+  sv_word(tb, info & 0xfffcu) ^= d ^ dm;
+  sv_word(tb, (info >> 16) & 0xfffcu) ^= d;
+  const bool onmd = (info & 1u) != 0, onad = (info & 0x10000u) != 0;
+  md ^= (onmd ? d : 0u) ^ (onad ? dm : 0u);
+  ad ^= (onad ? d : 0u) ^ (onmd ? dm : 0u);
+}
+
+struct SvLane {
+  int job;          // job slot, -1 = idle
+  int n, depth, last;
+  bool vsym;
+  uint32_t all;
+  int p;
+  uint32_t L, v, info, md, ad;
+  unsigned long long cnt;
+};
+
+__device__ __forceinline__ void sv_job_params(SvLane &s, const ServeJob &job) {
+  s.n = job.n;
+  s.depth = job.depth;
+  s.last = job.order_len - 1;
+  s.vsym = (job.flags & DLS_VSYM) != 0;
+  s.all = (1u << job.n) - 1u;
+  // odd order with vertical symmetry: no left cell may hold (n-1)/2
+  if (s.vsym && (s.n & 1)) s.all &= ~(1u << (s.n / 2));
+}
+
+// Finishes an item: its count goes to the job, one item fewer is left.
+__device__ __forceinline__ void sv_finish(SvLane &s, const ServeParams &P) {
+  if (s.cnt) atomicAdd(P.job_count + s.job, s.cnt);
+  atomicSub(P.job_left + s.job, 1u);
+  s.job = -1;
+}
+
+// Loads an item; returns true if the lane now has a search to run.
+__device__ bool sv_load(SvLane &s, const ServeParams &P, uint2 item, char *tb,
+                        unsigned B) {
+  s.job = (int)item.x;
+  const ServeJob &job = P.jobs[s.job];
+  sv_job_params(s, job);
+  s.md = s.ad = 0u;
+  s.cnt = 0ull;
+  for (int w = 0; w < SV_WORDS; ++w) sv_word(tb, (uint32_t)w * B * 4u) = 0u;
+  const uint8_t *rec = P.arena + item.y;
+  bool ok = true;
+  for (int t = 0; t < s.depth && ok; ++t) {
+    const uint32_t info = sv_describe(job, t, B);
+    const uint32_t val = rec[t];
+    const uint32_t b = (val < (uint32_t)s.n) ? (1u << val) : 0u;
+    ok = (sv_cands(tb, info, s.md, s.ad, s.all) & b) != 0u;
+    if (ok) sv_toggle(tb, info, b, s.md, s.ad, s.n, s.vsym);
+  }
+  if (!ok) {
+    sv_finish(s, P);
+    return false;
+  }
+  if (s.depth == job.order_len) {
+    s.cnt = 1ull;
+    sv_finish(s, P);
+    return false;
+  }
+  s.info = sv_describe(job, s.depth, B);
+  s.L = sv_cands(tb, s.info, s.md, s.ad, s.all);
+  if (s.depth == s.last || s.L == 0u) {
+    s.cnt = (s.depth == s.last) ? (unsigned)__popc(s.L) : 0ull;
+    sv_finish(s, P);
+    return false;
+  }
+  s.p = s.depth;
+  s.v = 0u;
+  return true;
+}
+
+// One search iteration (the step of dls_kernels.cu with per-lane job
+// parameters).  Returns true when the item is finished.
+__device__ __forceinline__ bool sv_step(SvLane &s, const ServeJob &job, char *tb,
+                                        uint32_t *stk, unsigned B) {
+  const uint32_t nv = s.L & (0u - s.L);
+  sv_toggle(tb, s.info, s.v ^ nv, s.md, s.ad, s.n, s.vsym);
+  s.L ^= nv;
+  s.v = nv;
+  if (nv == 0u) {
+    if (--s.p < s.depth) return true;
+    const uint32_t e = stk[(s.p - s.depth) * B];
+    s.L = e & 0xffffu;
+    s.v = e >> 16;
+    s.info = sv_describe(job, s.p, B);
+    return false;
+  }
+  const int q = s.p + 1;
+  const uint32_t info1 = sv_describe(job, q, B);
+  const uint32_t L1 = sv_cands(tb, info1, s.md, s.ad, s.all);
+  if (q == s.last) {
+    s.cnt += (unsigned)__popc(L1);
+    return false;
+  }
+  if (L1 == 0u) return false;
+  stk[(s.p - s.depth) * B] = s.L | (s.v << 16);
+  s.p = q;
+  s.L = L1;
+  s.v = 0u;
+  s.info = info1;
+  return false;
+}
+
+// Items handed out beyond the queued ones are taken back after an epoch
+// (their fetches failed), so the next epoch starts at the first unserved item.
+__global__ void k_serve_clamp(unsigned long long *head, unsigned long long tail) {
+  if (*head > tail) *head = tail;
+}
+
+// Shared memory per lane: SV_WORDS words + stack_words stack entries,
+// thread-minor.
+__global__ void __launch_bounds__(256) k_serve(const __grid_constant__ ServeParams P) {
+  extern __shared__ uint32_t smem[];
+  const unsigned B = blockDim.x;
+  const long long g = (long long)blockIdx.x * B + threadIdx.x;
+  char *tb = reinterpret_cast<char *>(smem + threadIdx.x);
+  uint32_t *stk = smem + SV_WORDS * B + threadIdx.x;
+  uint32_t *slot = P.slots + g;
+  const long long G = P.G;
+
+  SvLane s;
+  s.job = -1;
+  bool busy = slot[0] != 0u;
+  if (busy) {
+    s.job = (int)slot[1 * G];
+    sv_job_params(s, P.jobs[s.job]);
+    s.p = (int)slot[2 * G];
+    s.L = slot[3 * G];
+    s.v = slot[4 * G];
+    s.md = slot[5 * G];
+    s.ad = slot[6 * G];
+    s.cnt = (unsigned long long)slot[7 * G] | ((unsigned long long)slot[8 * G] << 32);
+    for (int w = 0; w < SV_WORDS; ++w) sv_word(tb, (uint32_t)w * B * 4u) = slot[(SV_HDR + w) * G];
+    for (int k = 0; k < s.p - s.depth; ++k) stk[k * B] = slot[(SV_HDR + SV_WORDS + k) * G];
+    s.info = sv_describe(P.jobs[s.job], s.p, B);
+  }
+  bool drained = false;
+  for (int it = 0; it < P.budget; ++it) {
+    if (!busy) {
+      if (drained) break;
+      const unsigned long long idx = atomicAdd(P.head, 1ull);
+      if (idx >= P.tail) {
+        drained = true;
+        break;
+      }
+      busy = sv_load(s, P, P.queue[idx % P.qcap], tb, B);
+      continue;
+    }
+    if (sv_step(s, P.jobs[s.job], tb, stk, B)) {
+      sv_finish(s, P);
+      busy = false;
+    }
+  }
+  slot[0] = busy ? 1u : 0u;
+  if (busy) {
+    slot[1 * G] = (uint32_t)s.job;
+    slot[2 * G] = (uint32_t)s.p;
+    slot[3 * G] = s.L;
+    slot[4 * G] = s.v;
+    slot[5 * G] = s.md;
+    slot[6 * G] = s.ad;
+    slot[7 * G] = (uint32_t)s.cnt;
+    slot[8 * G] = (uint32_t)(s.cnt >> 32);
+    for (int w = 0; w < SV_WORDS; ++w) slot[(SV_HDR + w) * G] = sv_word(tb, (uint32_t)w * B * 4u);
+    for (int k = 0; k < s.p - s.depth; ++k) slot[(SV_HDR + SV_WORDS + k) * G] = stk[k * B];
+  }
+}
+
+}  // namespace dls
+
+using namespace dls;
+
+// ------------------------------------------------------------ host side --
+
+struct HostJob {
+  int64_t id;
+  int slot = -1;
+  int n;
+  uint32_t flags;
+  std::vector<uint8_t> order;   // 2 * order_len
+  int depth;                    // item length
+  std::vector<uint8_t> items;   // n_items * depth
+  int64_t n_items;
+  std::vector<int> chunks;
+};
+
+struct dls_server {
+  dls_server_cfg cfg;
+  int dev = 0;
+  cudaStream_t stream = nullptr;
+  // device
+  ServeJob *d_jobs = nullptr;
+  unsigned long long *d_count = nullptr;
+  unsigned int *d_left = nullptr;
+  uint8_t *d_arena = nullptr;
+  uint2 *d_queue = nullptr;
+  unsigned long long *d_head = nullptr;
+  uint32_t *d_slots = nullptr;
+  long long G = 0;
+  int grid = 0;
+  size_t smem = 0;
+  // host
+  ServeJob *h_job_stage = nullptr;       // pinned, one per slot
+  unsigned long long *h_count = nullptr; // pinned readback
+  unsigned int *h_left = nullptr;
+  uint8_t *h_item_stage = nullptr;       // pinned, arena-sized staging
+  uint2 *h_queue_stage = nullptr;        // pinned, queue-sized staging
+  unsigned long long *h_zero = nullptr;
+  unsigned long long tail = 0;
+  int64_t outstanding = 0;               // queued items of active jobs
+  std::vector<int> free_slots;
+  std::vector<int> free_chunks;
+  std::vector<HostJob *> active;         // by slot
+  std::deque<HostJob *> pending;
+  std::vector<std::pair<int64_t, uint64_t>> done;
+  int64_t next_id = 0;
+  bool in_flight = false;
+  cudaEvent_t ev = nullptr;
+  dls_server_stats stats;
+  std::mutex mu;
+};
+
+static int sv_fail(cudaError_t e) {
+  set_cuda_error(cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? DLS_ERR_NO_MEMORY : DLS_ERR_CUDA;
+}
+
+static void sv_free(dls_server *s) {
+  if (s->ev) cudaEventDestroy(s->ev);
+  if (s->stream) cudaStreamDestroy(s->stream);
+  cudaFree(s->d_jobs);
+  cudaFree(s->d_count);
+  cudaFree(s->d_left);
+  cudaFree(s->d_arena);
+  cudaFree(s->d_queue);
+  cudaFree(s->d_head);
+  cudaFree(s->d_slots);
+  cudaFreeHost(s->h_job_stage);
+  cudaFreeHost(s->h_count);
+  cudaFreeHost(s->h_left);
+  cudaFreeHost(s->h_item_stage);
+  cudaFreeHost(s->h_queue_stage);
+  cudaFreeHost(s->h_zero);
+  for (auto *j : s->active) delete j;
+  for (auto *j : s->pending) delete j;
+  delete s;
+}
+
+extern "C" {
+
+void dls_server_default_cfg(dls_server_cfg *cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->max_jobs = 1024;
+  cfg->arena_bytes = size_t(64) << 20;
+  cfg->chunk_bytes = size_t(64) << 10;
+  cfg->queue_items = int64_t(1) << 22;
+  cfg->max_order = 10;
+  cfg->budget = 4096;
+  cfg->block_threads = 128;
+  cfg->blocks_per_sm = 0;
+  cfg->items_per_job = 512;
+}
+
+int dls_server_create(const dls_server_cfg *cfg_in, dls_server **out) {
+  if (out == nullptr) return DLS_ERR_BAD_ARG;
+  *out = nullptr;
+  dls_server_cfg cfg;
+  dls_server_default_cfg(&cfg);
+  if (cfg_in) cfg = *cfg_in;
+  if (cfg.max_jobs < 1 || cfg.chunk_bytes < 256 || cfg.arena_bytes < cfg.chunk_bytes ||
+      cfg.queue_items < 1 || cfg.max_order < 1 || cfg.max_order > DLS_MAX_N ||
+      cfg.budget < 1 || cfg.block_threads < 32 || cfg.block_threads > 256 ||
+      cfg.block_threads % 32 || cfg.items_per_job < 1 || cfg.blocks_per_sm < 0)
+    return DLS_ERR_BAD_ARG;
+  dls_server *s = new (std::nothrow) dls_server();
+  if (!s) return DLS_ERR_NO_MEMORY;
+  s->cfg = cfg;
+  std::memset(&s->stats, 0, sizeof(s->stats));
+  cudaError_t e = cudaGetDevice(&s->dev);
+  const int stack_words = cfg.max_order * cfg.max_order;
+  const int slot_words = SV_HDR + SV_WORDS + stack_words;
+  const size_t n_chunks = cfg.arena_bytes / cfg.chunk_bytes;
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming);
+  int sms = 0, per_sm = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->dev);
+  s->smem = (size_t)(SV_WORDS + stack_words) * cfg.block_threads * 4u;
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_serve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_serve, cfg.block_threads, s->smem);
+  if (e == cudaSuccess && per_sm < 1) {
+    sv_free(s);
+    return DLS_ERR_NO_MEMORY;
+  }
+  if (e == cudaSuccess) {
+    if (cfg.blocks_per_sm) per_sm = std::min(per_sm, cfg.blocks_per_sm);
+    s->grid = sms * per_sm;
+    s->G = (long long)s->grid * cfg.block_threads;
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_jobs, sizeof(ServeJob) * cfg.max_jobs);
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_count, sizeof(unsigned long long) * cfg.max_jobs);
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_left, sizeof(unsigned int) * cfg.max_jobs);
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_arena, n_chunks * cfg.chunk_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_queue, sizeof(uint2) * cfg.queue_items);
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_head, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_slots, sizeof(uint32_t) * (size_t)slot_words * s->G);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_job_stage, sizeof(ServeJob) * cfg.max_jobs);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_count, sizeof(unsigned long long) * cfg.max_jobs);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_left, sizeof(unsigned int) * cfg.max_jobs);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_item_stage, n_chunks * cfg.chunk_bytes);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_queue_stage, sizeof(uint2) * cfg.queue_items);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_zero, 64);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->d_head, 0, sizeof(unsigned long long), s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->d_slots, 0, sizeof(uint32_t) * s->G, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) {
+    int rc = sv_fail(e);
+    sv_free(s);
+    return rc;
+  }
+  std::memset(s->h_zero, 0, 64);
+  for (int k = cfg.max_jobs - 1; k >= 0; --k) s->free_slots.push_back(k);
+  for (int k = (int)n_chunks - 1; k >= 0; --k) s->free_chunks.push_back(k);
+  s->active.assign(cfg.max_jobs, nullptr);
+  s->stats.lanes = s->G;
+  s->stats.device_bytes = sizeof(ServeJob) * cfg.max_jobs + 12u * cfg.max_jobs +
+                          n_chunks * cfg.chunk_bytes + sizeof(uint2) * cfg.queue_items +
+                          sizeof(uint32_t) * (size_t)slot_words * s->G;
+  *out = s;
+  return DLS_OK;
+}
+
+int dls_server_submit(dls_server *s, int n, uint32_t flags, const uint8_t *order,
+                      int order_len, const uint8_t *prefix, int depth,
+                      int64_t *job_id) {
+  if (s == nullptr || job_id == nullptr) return DLS_ERR_BAD_ARG;
+  OrderInfo info;
+  int rc = validate_order(n, flags, order, order_len, &info);
+  if (rc) return rc;
+  if (n > s->cfg.max_order) return DLS_ERR_INVALID_N;
+  if (depth < 0 || depth > order_len || (depth > 0 && prefix == nullptr)) return DLS_ERR_BAD_ARG;
+  HostJob *j = new (std::nothrow) HostJob();
+  if (!j) return DLS_ERR_NO_MEMORY;
+  j->n = n;
+  j->flags = flags;
+  j->order.assign(order, order + 2 * order_len);
+  // split the prefix a few cells deeper (Section 5.2), at most to two cells
+  // before the end, until there are items_per_job items or more
+  std::vector<uint8_t> cur(prefix, prefix + depth);
+  int d = depth;
+  int64_t m = 1;
+  if (vsym_all_zero(n, flags)) {
+    m = 0;
+    cur.clear();
+  } else {
+    std::vector<uint8_t> next;
+    int64_t need = 0;
+    rc = dls_extend_prefixes(n, flags, order, order_len, cur.data(), d, 1, d, nullptr, 0,
+                             nullptr, &need);
+    if (rc != DLS_OK && rc != DLS_ERR_CAPACITY) {
+      delete j;
+      return rc;
+    }
+    m = need;  // 1 if the prefix is valid, else 0
+    if (m == 0) cur.clear();
+    while (m > 0 && m < s->cfg.items_per_job && d < order_len - 2) {
+      rc = dls_extend_prefixes(n, flags, order, order_len, cur.data(), d, m, d + 1,
+                               nullptr, 0, nullptr, &need);
+      if (rc != DLS_OK && rc != DLS_ERR_CAPACITY) {
+        delete j;
+        return rc;
+      }
+      next.assign((size_t)need * (d + 1), 0);
+      int64_t got = 0;
+      rc = dls_extend_prefixes(n, flags, order, order_len, cur.data(), d, m, d + 1,
+                               next.data(), need, nullptr, &got);
+      if (rc) {
+        delete j;
+        return rc;
+      }
+      cur.swap(next);
+      ++d;
+      m = got;
+    }
+  }
+  j->depth = d;
+  j->n_items = m;
+  j->items.swap(cur);
+  std::lock_guard<std::mutex> g(s->mu);
+  j->id = s->next_id++;
+  *job_id = j->id;
+  s->stats.submitted++;
+  if (m == 0 || d == order_len) {
+    // nothing for the GPU: no valid extension, or complete assignments
+    s->done.push_back({j->id, (uint64_t)(d == order_len ? m : 0)});
+    s->stats.completed++;
+    s->stats.squares += (uint64_t)(d == order_len ? m : 0);
+    delete j;
+    return DLS_OK;
+  }
+  const size_t per_chunk = s->cfg.chunk_bytes / (size_t)d;
+  const size_t chunks = (size_t)((m + (int64_t)per_chunk - 1) / (int64_t)per_chunk);
+  if (chunks > s->cfg.arena_bytes / s->cfg.chunk_bytes || m > s->cfg.queue_items) {
+    s->stats.submitted--;
+    delete j;
+    return DLS_ERR_CAPACITY;
+  }
+  s->pending.push_back(j);
+  return DLS_OK;
+}
+
+// Reads the finished epoch's counters; completes jobs whose items are done.
+static int sv_collect(dls_server *s) {
+  if (!s->in_flight) return DLS_OK;
+  cudaError_t e = cudaEventSynchronize(s->ev);
+  if (e != cudaSuccess) return sv_fail(e);
+  s->in_flight = false;
+  for (int slot = 0; slot < s->cfg.max_jobs; ++slot) {
+    HostJob *j = s->active[slot];
+    if (j == nullptr || s->h_left[slot] != 0u) continue;
+    s->done.push_back({j->id, (uint64_t)s->h_count[slot]});
+    s->stats.completed++;
+    s->stats.squares += s->h_count[slot];
+    s->outstanding -= j->n_items;
+    for (int c : j->chunks) s->free_chunks.push_back(c);
+    s->free_slots.push_back(slot);
+    s->active[slot] = nullptr;
+    delete j;
+  }
+  return DLS_OK;
+}
+
+int dls_server_step(dls_server *s) {
+  if (s == nullptr) return DLS_ERR_BAD_ARG;
+  std::lock_guard<std::mutex> g(s->mu);
+  int rc = sv_collect(s);
+  if (rc) return rc;
+  cudaError_t e;
+  int prev;
+  if (cudaGetDevice(&prev) == cudaSuccess && prev != s->dev) cudaSetDevice(s->dev);
+  // admission, in arrival order, by job slots, arena chunks and queue room
+  size_t qn = 0;
+  unsigned long long q0 = s->tail;
+  while (!s->pending.empty()) {
+    HostJob *j = s->pending.front();
+    const size_t per_chunk = s->cfg.chunk_bytes / (size_t)j->depth;
+    const size_t need = (size_t)((j->n_items + (int64_t)per_chunk - 1) / (int64_t)per_chunk);
+    if (s->free_slots.empty() || s->free_chunks.size() < need ||
+        s->outstanding + j->n_items > s->cfg.queue_items)
+      break;
+    s->pending.pop_front();
+    j->slot = s->free_slots.back();
+    s->free_slots.pop_back();
+    ServeJob &dj = s->h_job_stage[j->slot];
+    std::memset(&dj, 0, sizeof(dj));
+    dj.n = j->n;
+    dj.flags = j->flags;
+    dj.depth = j->depth;
+    dj.order_len = (int)(j->order.size() / 2);
+    for (int t = 0; t < dj.order_len; ++t) {
+      dj.ci[t] = j->order[2 * t];
+      dj.cj[t] = j->order[2 * t + 1];
+    }
+    s->h_count[j->slot] = 0ull;
+    s->h_left[j->slot] = (unsigned int)j->n_items;
+    e = cudaMemcpyAsync(s->d_jobs + j->slot, &dj, sizeof(ServeJob), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(s->d_count + j->slot, s->h_count + j->slot, sizeof(unsigned long long),
+                          cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(s->d_left + j->slot, s->h_left + j->slot, sizeof(unsigned int),
+                          cudaMemcpyHostToDevice, s->stream);
+    int64_t k = 0;
+    for (size_t c = 0; c < need && e == cudaSuccess; ++c) {
+      const int chunk = s->free_chunks.back();
+      s->free_chunks.pop_back();
+      j->chunks.push_back(chunk);
+      const size_t base = (size_t)chunk * s->cfg.chunk_bytes;
+      const int64_t take = std::min<int64_t>((int64_t)per_chunk, j->n_items - k);
+      std::memcpy(s->h_item_stage + base, j->items.data() + (size_t)k * j->depth,
+                  (size_t)take * j->depth);
+      e = cudaMemcpyAsync(s->d_arena + base, s->h_item_stage + base, (size_t)take * j->depth,
+                          cudaMemcpyHostToDevice, s->stream);
+      for (int64_t t = 0; t < take; ++t) {
+        const unsigned long long pos = (q0 + qn) % (unsigned long long)s->cfg.queue_items;
+        s->h_queue_stage[pos] = make_uint2((unsigned)j->slot, (unsigned)(base + (size_t)t * j->depth));
+        ++qn;
+      }
+      k += take;
+    }
+    if (e != cudaSuccess) return sv_fail(e);
+    std::vector<uint8_t>().swap(j->items);
+    s->outstanding += j->n_items;
+    s->active[j->slot] = j;
+    s->stats.admitted++;
+  }
+  // new queue entries (the ring may wrap)
+  if (qn) {
+    const unsigned long long cap = (unsigned long long)s->cfg.queue_items;
+    const unsigned long long a = q0 % cap;
+    const unsigned long long first = std::min<unsigned long long>(qn, cap - a);
+    e = cudaMemcpyAsync(s->d_queue + a, s->h_queue_stage + a, first * sizeof(uint2),
+                        cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess && first < qn)
+      e = cudaMemcpyAsync(s->d_queue, s->h_queue_stage, (qn - first) * sizeof(uint2),
+                          cudaMemcpyHostToDevice, s->stream);
+    if (e != cudaSuccess) return sv_fail(e);
+    s->tail += qn;
+  }
+  bool any = false;
+  for (auto *j : s->active) any = any || (j != nullptr);
+  if (!any) return DLS_OK;
+  // one epoch
+  ServeParams P;
+  P.jobs = s->d_jobs;
+  P.job_count = s->d_count;
+  P.job_left = s->d_left;
+  P.arena = s->d_arena;
+  P.queue = s->d_queue;
+  P.head = s->d_head;
+  P.tail = s->tail;
+  P.qcap = (unsigned long long)s->cfg.queue_items;
+  P.slots = s->d_slots;
+  P.G = s->G;
+  P.stack_words = s->cfg.max_order * s->cfg.max_order;
+  P.budget = s->cfg.budget;
+  k_serve<<<s->grid, s->cfg.block_threads, s->smem, s->stream>>>(P);
+  // lanes that found the queue empty advanced the head past the tail
+  k_serve_clamp<<<1, 1, 0, s->stream>>>(s->d_head, s->tail);
+  e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s->h_count, s->d_count, sizeof(unsigned long long) * s->cfg.max_jobs,
+                        cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s->h_left, s->d_left, sizeof(unsigned int) * s->cfg.max_jobs,
+                        cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(s->ev, s->stream);
+  if (e != cudaSuccess) return sv_fail(e);
+  s->in_flight = true;
+  s->stats.epochs++;
+  return DLS_OK;
+}
+
+int dls_server_poll(dls_server *s, int64_t *ids, uint64_t *counts, int cap, int *n_done) {
+  if (s == nullptr || n_done == nullptr || cap < 0 || (cap > 0 && (!ids || !counts)))
+    return DLS_ERR_BAD_ARG;
+  std::lock_guard<std::mutex> g(s->mu);
+  const int k = (int)std::min<size_t>((size_t)cap, s->done.size());
+  for (int t = 0; t < k; ++t) {
+    ids[t] = s->done[t].first;
+    counts[t] = s->done[t].second;
+  }
+  s->done.erase(s->done.begin(), s->done.begin() + k);
+  *n_done = k;
+  return DLS_OK;
+}
+
+int dls_server_get_stats(dls_server *s, dls_server_stats *out) {
+  if (s == nullptr || out == nullptr) return DLS_ERR_BAD_ARG;
+  std::lock_guard<std::mutex> g(s->mu);
+  *out = s->stats;
+  out->pending = (int64_t)s->pending.size();
+  int64_t act = 0;
+  for (auto *j : s->active) act += (j != nullptr);
+  out->active = act;
+  out->free_arena_bytes = s->free_chunks.size() * s->cfg.chunk_bytes;
+  return DLS_OK;
+}
+
+void dls_server_destroy(dls_server *s) {
+  if (!s) return;
+  if (s->in_flight) cudaEventSynchronize(s->ev);
+  sv_free(s);
+}
+
+}  // extern "C"

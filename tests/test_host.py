@@ -66,7 +66,8 @@ def test_heuristic_order_is_a_permutation_and_counts_agree(dls, n):
 
 
 @pytest.mark.parametrize("n,flags,keep", [(9, D, 9), (8, D, 28), (8, D, 15), (7, D, 20),
-                                          (10, D | V, 15), (8, D | V, 4), (6, 0, 6), (6, D, 0)])
+                                          (10, D | V, 15), (8, D | V, 4), (6, 0, 6), (6, D, 0),
+                                          (7, D | V, 9), (9, D | V, 4)])
 def test_order_completion_matches_oracle(dls, n, flags, keep):
     vs = bool(flags & V)
     base = dls.fill_order(n, flags)
