@@ -68,6 +68,11 @@ def parse():
                     help="split 20 cells past row 0, cells after the split row by row")
     ap.add_argument("--suffix", default="", choices=["", "given", "heuristic"],
                     help="fix the order of the cells after the split")
+    ap.add_argument("--serve-jobs", type=int, default=0,
+                    help="also replay this many jobs of the serving mix (Poisson arrivals "
+                         "at 200/s) and report latency percentiles")
+    ap.add_argument("--serve-limit", type=float, default=120.0,
+                    help="seconds after which the serving replay stops")
     return ap.parse_args()
 
 
@@ -209,6 +214,45 @@ def timed_steps(launch_fn, stream, steps, flush):
     return [a.elapsed_time(b) / 1e3 for a, b in evs]
 
 
+def serving_leg(n_jobs, limit_s, seed=0):
+    """Replays the seeded serving mix in real time against the
+    continuous-batching server; returns the 'serving' object of the line."""
+    from paper_1709_02599_gb300 import serving
+    specs = dls_inputs.serving_jobs(n_jobs, seed=seed)
+    jobs = []
+    for sp in specs:
+        b = serving.build_job(sp["n"], sp["vsym"], sp["rows"], sp["draws"])
+        if b is None:
+            continue
+        flags, order, prefix = b
+        jobs.append(dict(n=sp["n"], flags=flags, order=order, prefix=prefix,
+                         arrival=sp["arrival"], rows=sp["rows"]))
+    srv = serving.Server()
+    # one untimed warm-up job so that the first epoch pays no start-up cost
+    srv.submit(jobs[0]["n"], jobs[0]["flags"], jobs[0]["order"], jobs[0]["prefix"])
+    srv.drain()
+    done, makespan = serving.run_stream(srv, jobs, time_limit_s=limit_s)
+    st = srv.stats()
+    srv.close()
+    lat = np.array([done[k][0] for k in sorted(done)]) * 1e3
+    squares = sum(done[k][1] for k in done)
+    span = jobs[-1]["arrival"] if jobs else 0.0
+    out = {"jobs": len(jobs), "completed": len(done), "unfinished": len(jobs) - len(done),
+           "offered_rate_hz": len(jobs) / span if span > 0 else None,
+           "served_rate_hz": len(done) / makespan if makespan > 0 else None,
+           "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
+           "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
+           "max_ms": float(lat.max()) if len(lat) else None,
+           "squares": int(squares), "squares_per_s": squares / makespan if makespan else None,
+           "makespan_s": makespan, "epochs": st["epochs"], "lanes": st["lanes"],
+           "device_bytes": st["device_bytes"],
+           "mix": "order uniform {6,7,8,9}, diagonal or vertically symmetric, 2..N-3 rows "
+                  "fixed, Poisson 200/s, seed %d" % seed}
+    if out["unfinished"]:
+        out["note"] = "stopped after %.0f s with jobs unfinished" % limit_s
+    return out
+
+
 def reference_arm(args):
     """The oracle, as it stands, on the host cores: each step a bounded sample
     (one diagonal's prefixes) of the same workload."""
@@ -317,9 +361,8 @@ def main():
         t = torch.tensor([step_s], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         step_s = float(t.item())
-        s = torch.tensor([float(squares)], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(s)
-        squares_all = int(s.item())
+        from paper_1709_02599_gb300 import shard
+        squares_all = shard.allreduce_total(squares)
     else:
         squares_all = squares
     value = squares_all / step_s
@@ -397,6 +440,8 @@ def main():
                                           "same split and fill order as the GPU run "
                                           "(%d squares, %.1f s)" % (len(opre), c, dt)}
     plan.close()
+    if rank == 0 and args.serve_jobs > 0:
+        line["serving"] = serving_leg(args.serve_jobs, args.serve_limit)
     if ws > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()

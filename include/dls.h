@@ -267,7 +267,9 @@ typedef struct {
     int budget;            /* search iterations per lane per epoch (4096)    */
     int block_threads;     /* 32..256 (default 128)                          */
     int blocks_per_sm;     /* 0 = as many as fit                             */
-    int items_per_job;     /* split target per job (default 512)             */
+    int items_per_job;     /* split target per job (0 = default: the number
+                              of lanes of the grid, so that one big job can
+                              occupy the whole GPU)                          */
 } dls_server_cfg;
 
 typedef struct {

@@ -360,7 +360,7 @@ void dls_server_default_cfg(dls_server_cfg *cfg) {
   cfg->budget = 4096;
   cfg->block_threads = 128;
   cfg->blocks_per_sm = 0;
-  cfg->items_per_job = 512;
+  cfg->items_per_job = 0;
 }
 
 int dls_server_create(const dls_server_cfg *cfg_in, dls_server **out) {
@@ -372,7 +372,7 @@ int dls_server_create(const dls_server_cfg *cfg_in, dls_server **out) {
   if (cfg.max_jobs < 1 || cfg.chunk_bytes < 256 || cfg.arena_bytes < cfg.chunk_bytes ||
       cfg.queue_items < 1 || cfg.max_order < 1 || cfg.max_order > DLS_MAX_N ||
       cfg.budget < 1 || cfg.block_threads < 32 || cfg.block_threads > 256 ||
-      cfg.block_threads % 32 || cfg.items_per_job < 1 || cfg.blocks_per_sm < 0)
+      cfg.block_threads % 32 || cfg.items_per_job < 0 || cfg.blocks_per_sm < 0)
     return DLS_ERR_BAD_ARG;
   dls_server *s = new (std::nothrow) dls_server();
   if (!s) return DLS_ERR_NO_MEMORY;
@@ -399,6 +399,8 @@ int dls_server_create(const dls_server_cfg *cfg_in, dls_server **out) {
     if (cfg.blocks_per_sm) per_sm = std::min(per_sm, cfg.blocks_per_sm);
     s->grid = sms * per_sm;
     s->G = (long long)s->grid * cfg.block_threads;
+    // by default a job is split until it could occupy every lane
+    if (s->cfg.items_per_job == 0) s->cfg.items_per_job = (int)std::min<long long>(s->G, 1 << 20);
   }
   if (e == cudaSuccess) e = cudaMalloc(&s->d_jobs, sizeof(ServeJob) * cfg.max_jobs);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_count, sizeof(unsigned long long) * cfg.max_jobs);
