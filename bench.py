@@ -68,10 +68,10 @@ def parse():
                     help="split 20 cells past row 0, cells after the split row by row")
     ap.add_argument("--suffix", default="", choices=["", "given", "heuristic"],
                     help="fix the order of the cells after the split")
-    ap.add_argument("--serve-jobs", type=int, default=0,
+    ap.add_argument("--serve-jobs", type=int, default=100,
                     help="also replay this many jobs of the serving mix (Poisson arrivals "
                          "at 200/s) and report latency percentiles")
-    ap.add_argument("--serve-limit", type=float, default=120.0,
+    ap.add_argument("--serve-limit", type=float, default=150.0,
                     help="seconds after which the serving replay stops")
     return ap.parse_args()
 

@@ -86,80 +86,83 @@ __device__ __forceinline__ uint32_t mirror(uint32_t d, int n) {
   return VSYM ? (__brev(d) >> (32 - n)) : 0u;
 }
 
+// A cell descriptor, one per order position, kept in a shared-memory table:
+//   x: where the cell's row word and column word are -- byte offsets from the
+//      lane's first word (bits 0-15, 16-31) in shared memory, or bit shifts
+//      (bits 0-5, 8-13) into the packed registers;
+//   y: diagonal masks -- 0xffff in bits 0-15 if the cell lies on the main
+//      diagonal, 0xffff in bits 16-31 if on the anti-diagonal.
+typedef uint2 Cell;
+
 // The row/column/diagonal words of one lane (Section 3: one word per line,
 // bit v set when value v is used on it).
 //
 // REG = false: row i and column j words in shared memory, word w of thread t
-//   at st[w * blockDim + t] (rows 0..n-1, then columns); a cell descriptor
-//   holds the byte offsets of its row and column word (main-diagonal flag in
-//   bit 0, anti-diagonal flag in bit 16).
+//   at st[w * blockDim + t] (rows 0..n-1, then columns).
 // REG = true: every row word packed into one 64-bit register R (row i at bit
-//   i * wr) and every column word into C (column j at bit j * wc); a cell
-//   descriptor holds the two shifts (bits 0-5 and 8-13) and the diagonal
-//   flags (bits 16, 17).  With vertical symmetry a row field records the
-//   value pairs {v, n-1-v} in use (bit min(v, n-1-v)) -- a row takes each
-//   pair exactly once -- which halves its width.
-// md / ad, the diagonal words, are registers in both.
+//   i * wr) and every column word into C (column j at bit j * wc).  With
+//   vertical symmetry a row field records the value pairs {v, n-1-v} in use
+//   (bit min(v, n-1-v)) -- a row takes each pair exactly once -- which
+//   halves its width.
+// dg holds both diagonal words: the main diagonal in bits 0-15 and the
+// anti-diagonal in bits 16-31, so that one AND with a descriptor's masks
+// selects the diagonals a cell lies on.
 template <bool REG, bool VSYM>
 struct Words {
   unsigned long long R, C;
   char *tb;
-  uint32_t md, ad;
+  uint32_t dg;
 
-  __device__ static uint32_t describe(const KParams &p, int pos, int diag,
-                                      unsigned B) {
+  __device__ static Cell describe(const KParams &p, int pos, int diag, unsigned B) {
     const int i = p.ci[pos], j = p.cj[pos];
-    const uint32_t m = (diag && i == j) ? 1u : 0u;
-    const uint32_t a = (diag && i + j == p.n - 1) ? 1u : 0u;
+    Cell c;
+    c.y = ((diag && i == j) ? 0x0000ffffu : 0u) | ((diag && i + j == p.n - 1) ? 0xffff0000u : 0u);
     if (REG)
-      return (uint32_t)(i * p.wr) | ((uint32_t)(j * p.wc) << 8) | (m << 16) | (a << 17);
-    const uint32_t roff = (uint32_t)i * B * 4u;
-    const uint32_t coff = (uint32_t)(p.n + j) * B * 4u;
-    return roff | m | ((coff | a) << 16);
-  }
-  __device__ static bool on_md(uint32_t info) {
-    return REG ? ((info >> 16) & 1u) != 0 : (info & 1u) != 0;
-  }
-  __device__ static bool on_ad(uint32_t info) {
-    return REG ? ((info >> 17) & 1u) != 0 : ((info >> 16) & 1u) != 0;
+      c.x = (uint32_t)(i * p.wr) | ((uint32_t)(j * p.wc) << 8);
+    else
+      c.x = ((uint32_t)i * B * 4u) | (((uint32_t)(p.n + j) * B * 4u) << 16);
+    return c;
   }
   // Admissible values of the cell: ALL & ~(row | col | md | ad).
-  __device__ uint32_t cands(uint32_t info, const KParams &p) const {
+  __device__ uint32_t cands(Cell c, const KParams &p) const {
     uint32_t f;
     if (REG) {
-      uint32_t r = (uint32_t)(R >> (info & 63u));
+      uint32_t r = (uint32_t)(R >> (c.x & 63u));
       if (VSYM) {
         r &= p.pairmask;
         r |= mirror<true>(r, p.n);
       }
-      f = r | (uint32_t)(C >> ((info >> 8) & 63u));
+      f = r | (uint32_t)(C >> ((c.x >> 8) & 63u));
     } else {
-      f = word_at(tb, info & 0xfffcu) | word_at(tb, (info >> 16) & 0xfffcu);
+      f = word_at(tb, c.x & 0xffffu) | word_at(tb, c.x >> 16);
     }
-    f |= on_md(info) ? md : 0u;
-    f |= on_ad(info) ? ad : 0u;
-    return p.all & ~f;
+    const uint32_t t = dg & c.y;
+    return p.all & ~(f | t | (t >> 16));
   }
   // XOR value bits d (the old value and/or the new one) into the words of the
   // cell; with vertical symmetry the mirror cell (i, n-1-j) takes n-1-v, and
   // the mirror of a main-diagonal cell lies on the anti-diagonal and vice
   // versa.
-  __device__ void toggle(uint32_t info, uint32_t d, const KParams &p) {
+  __device__ void toggle(Cell c, uint32_t d, const KParams &p) {
     const uint32_t dm = mirror<VSYM>(d, p.n);
     if (REG) {
       const uint32_t rd = VSYM ? ((d ^ dm) & p.pairmask) : d;
-      R ^= (unsigned long long)rd << (info & 63u);
-      C ^= (unsigned long long)d << ((info >> 8) & 63u);
+      R ^= (unsigned long long)rd << (c.x & 63u);
+      C ^= (unsigned long long)d << ((c.x >> 8) & 63u);
     } else {
-      word_at(tb, info & 0xfffcu) ^= d ^ dm;
-      word_at(tb, (info >> 16) & 0xfffcu) ^= d;
+      word_at(tb, c.x & 0xffffu) ^= d ^ dm;
+      word_at(tb, c.x >> 16) ^= d;
     }
-    const bool onmd = on_md(info), onad = on_ad(info);
-    md ^= (onmd ? d : 0u) ^ ((VSYM && onad) ? dm : 0u);
-    ad ^= (onad ? d : 0u) ^ ((VSYM && onmd) ? dm : 0u);
+    // d < 2^16, so d * 0x10001 puts d in both halves
+    if (VSYM) {
+      const uint32_t swapped = __byte_perm(c.y, 0u, 0x1032u);
+      dg ^= ((d * 0x10001u) & c.y) ^ ((dm * 0x10001u) & swapped);
+    } else {
+      dg ^= (d * 0x10001u) & c.y;
+    }
   }
   __device__ void clear(const KParams &p, unsigned B) {
-    md = ad = 0u;
+    dg = 0u;
     if (REG) {
       R = C = 0ull;
     } else {
@@ -175,7 +178,7 @@ struct Lane {
   int p;                 // current order position
   uint32_t L;            // untried candidates at p
   uint32_t v;            // value placed at p (one-hot), 0 = none yet
-  uint32_t info;         // cell descriptor of p
+  Cell info;             // cell descriptor of p
   uint32_t splitc;       // nodes met at split_pos so far
   uint32_t sub;          // residue class of split nodes this item keeps
   long long prefix;      // prefix index of the current item
@@ -192,7 +195,7 @@ struct Lane {
 // whether the stack is written or read.
 template <bool REG, bool VSYM, bool NODES, bool SPLIT>
 __device__ __forceinline__ bool dfs_step(Lane<REG, VSYM> &s, const KParams &p,
-                                         uint32_t *stk, const uint32_t *tbl,
+                                         uint32_t *stk, const Cell *tbl,
                                          unsigned B) {
   const uint32_t nv = s.L & (0u - s.L);
   s.w.toggle(s.info, s.v ^ nv, p);
@@ -209,7 +212,7 @@ __device__ __forceinline__ bool dfs_step(Lane<REG, VSYM> &s, const KParams &p,
     s.nodes++;
   }
   const int q = s.p + 1;  // <= last: a lane never stands on the last cell
-  const uint32_t info1 = tbl[q];
+  const Cell info1 = tbl[q];
   const uint32_t L1 = s.w.cands(info1, p);
   const bool live = !pop && !skip;
   const bool leaf = q == p.last;
@@ -220,7 +223,8 @@ __device__ __forceinline__ bool dfs_step(Lane<REG, VSYM> &s, const KParams &p,
   if (down) stk[(s.p - p.depth) * B] = s.L | (s.v << 16);
   const int pp = s.p - 1;
   const bool up = pop && pp >= p.depth;
-  uint32_t e = 0u, infoP = 0u;
+  uint32_t e = 0u;
+  Cell infoP = make_uint2(0u, 0u);
   if (up) {
     e = stk[(pp - p.depth) * B];
     infoP = tbl[pp];
@@ -228,7 +232,8 @@ __device__ __forceinline__ bool dfs_step(Lane<REG, VSYM> &s, const KParams &p,
   s.p = down ? q : (pop ? pp : s.p);
   s.L = down ? L1 : (up ? (e & 0xffffu) : s.L);
   s.v = down ? 0u : (up ? (e >> 16) : s.v);
-  s.info = down ? info1 : (up ? infoP : s.info);
+  s.info.x = down ? info1.x : (up ? infoP.x : s.info.x);
+  s.info.y = down ? info1.y : (up ? infoP.y : s.info.y);
   return pop && !up;
 }
 
@@ -236,7 +241,7 @@ __device__ __forceinline__ bool dfs_step(Lane<REG, VSYM> &s, const KParams &p,
 // finished (invalid prefix, or nothing left to search).
 template <bool REG, bool VSYM, bool NODES>
 __device__ bool load_item(Lane<REG, VSYM> &s, const KParams &p, long long item,
-                          const uint32_t *tbl, unsigned B) {
+                          const Cell *tbl, unsigned B) {
   s.prefix = item >> p.lanes_log2;
   s.sub = (uint32_t)(item & ((1ll << p.lanes_log2) - 1));
   s.cnt = 0ull;
@@ -245,7 +250,7 @@ __device__ bool load_item(Lane<REG, VSYM> &s, const KParams &p, long long item,
   const uint8_t *rec = p.prefixes + (size_t)s.prefix * (size_t)p.depth;
   for (int t = 0; t < p.depth; ++t) {
     const uint32_t val = rec[t];
-    const uint32_t info = tbl[t];
+    const Cell info = tbl[t];
     const uint32_t b = (val < (uint32_t)p.n) ? (1u << val) : 0u;
     if ((s.w.cands(info, p) & b) == 0u) return true;
     s.w.toggle(info, b, p);
@@ -254,7 +259,7 @@ __device__ bool load_item(Lane<REG, VSYM> &s, const KParams &p, long long item,
     s.cnt = (s.sub == 0u) ? 1ull : 0ull;
     return true;
   }
-  const uint32_t info = tbl[p.depth];
+  const Cell info = tbl[p.depth];
   const uint32_t L = s.w.cands(info, p);
   if (p.depth == p.last) {
     if (s.sub == 0u) {
@@ -297,18 +302,18 @@ __device__ void block_reduce_add(unsigned long long v, unsigned long long *dst,
   }
 }
 
-// Shared memory: [table: order_len words, the cell descriptor of each position]
+// Shared memory: [table: one Cell (8 bytes) per order position]
 //                [words: 2n * B, shared-memory variant only]
 //                [stack: (last - depth) * B]
 template <bool REG, bool VSYM>
 __device__ __forceinline__ void setup(const KParams &p, int diag, uint32_t *smem,
-                                      const uint32_t *&tbl, uint32_t *&stk,
+                                      const Cell *&tbl, uint32_t *&stk,
                                       Lane<REG, VSYM> &s) {
   const unsigned B = blockDim.x;
-  uint32_t *t = smem;
+  Cell *t = reinterpret_cast<Cell *>(smem);
   for (int idx = threadIdx.x; idx < p.order_len; idx += B)
     t[idx] = Words<REG, VSYM>::describe(p, idx, diag, B);
-  uint32_t *st = smem + ((p.order_len + 31) & ~31);
+  uint32_t *st = smem + 2 * ((p.order_len + 31) & ~31);
   s.w.tb = reinterpret_cast<char *>(st + threadIdx.x);
   stk = st + (REG ? 0 : 2 * p.n * (int)B) + threadIdx.x;
   tbl = t;
@@ -316,9 +321,10 @@ __device__ __forceinline__ void setup(const KParams &p, int diag, uint32_t *smem
   s.prefix = 0;
   s.sub = 0u;
   s.p = 0;
-  s.L = s.v = s.info = 0u;
+  s.L = s.v = 0u;
+  s.info = make_uint2(0u, 0u);
   s.cnt = 0ull;
-  s.w.md = s.w.ad = 0u;
+  s.w.dg = 0u;
   s.w.R = s.w.C = 0ull;
   __syncthreads();
 }
@@ -329,7 +335,7 @@ __global__ void __launch_bounds__(512) k_plain(const __grid_constant__ KParams p
   extern __shared__ uint32_t smem[];
   __shared__ unsigned long long red[16];
   const unsigned B = blockDim.x;
-  const uint32_t *tbl;
+  const Cell *tbl;
   uint32_t *stk;
   Lane<REG, VSYM> s;
   setup(p, diag, smem, tbl, stk, s);
@@ -364,7 +370,7 @@ __device__ __forceinline__ int nth_set_bit(unsigned m, int r) {
 // pd, which the busy lane gives up.
 template <bool REG, bool VSYM>
 __device__ void donate(Lane<REG, VSYM> &s, bool &busy, const KParams &p,
-                       uint32_t *stk, const uint32_t *tbl, int lane, unsigned B) {
+                       uint32_t *stk, const Cell *tbl, int lane, unsigned B) {
   const unsigned idle = __ballot_sync(FULL, !busy);
   if (idle == 0u || idle == FULL) return;
   const int lo = max(p.depth, p.split_pos + 1);
@@ -406,8 +412,7 @@ __device__ void donate(Lane<REG, VSYM> &s, bool &busy, const KParams &p,
   const uint32_t d_vpd = __shfl_sync(FULL, vpd, partner);
   const int d_p = __shfl_sync(FULL, s.p, partner);
   const uint32_t d_v = __shfl_sync(FULL, s.v, partner);
-  const uint32_t d_md = __shfl_sync(FULL, s.w.md, partner);
-  const uint32_t d_ad = __shfl_sync(FULL, s.w.ad, partner);
+  const uint32_t d_dg = __shfl_sync(FULL, s.w.dg, partner);
   const unsigned long long d_R = __shfl_sync(FULL, s.w.R, partner);
   const unsigned long long d_C = __shfl_sync(FULL, s.w.C, partner);
   const long long d_prefix = __shfl_sync(FULL, s.prefix, partner);
@@ -425,8 +430,7 @@ __device__ void donate(Lane<REG, VSYM> &s, bool &busy, const KParams &p,
     const uint32_t *dstk = stk + dl;
     for (int q = p.depth; q < d_pd; ++q)
       stk[(q - p.depth) * B] = dstk[(q - p.depth) * B] & 0xffff0000u;
-    s.w.md = d_md;
-    s.w.ad = d_ad;
+    s.w.dg = d_dg;
     // undo the donor's placements below pd
     for (int q = d_pd + 1; q <= d_p; ++q) {
       const uint32_t vq = (q < d_p) ? (dstk[(q - p.depth) * B] >> 16) : d_v;
@@ -459,7 +463,7 @@ __global__ void __launch_bounds__(512)
   __shared__ unsigned long long red[16];
   const unsigned B = blockDim.x;
   const int lane = threadIdx.x & 31;
-  const uint32_t *tbl;
+  const Cell *tbl;
   uint32_t *stk;
   Lane<REG, VSYM> s;
   setup(p, diag, smem, tbl, stk, s);
@@ -490,9 +494,12 @@ __global__ void __launch_bounds__(512)
     if (!qdone) {
       // run until some lane finishes its item
       do {
-        if (busy && dfs_step<REG, VSYM, NODES, SPLIT>(s, p, stk, tbl, B)) {
-          busy = false;
-          flush_count(s.prefix, s.cnt, p, lane_total);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          if (busy && dfs_step<REG, VSYM, NODES, SPLIT>(s, p, stk, tbl, B)) {
+            busy = false;
+            flush_count(s.prefix, s.cnt, p, lane_total);
+          }
         }
       } while (__all_sync(FULL, busy));
     } else {
@@ -664,7 +671,7 @@ static bool words_fit_registers(int n, bool vsym, int *wr, int *wc) {
 static size_t smem_bytes(int order_len, int n, int depth, int last, int block,
                          bool reg) {
   const int stack = std::max(0, last - depth);
-  return (size_t)((order_len + 31) & ~31) * 4u + (size_t)((reg ? 0 : 2 * n) + stack) * block * 4u;
+  return (size_t)((order_len + 31) & ~31) * 8u + (size_t)((reg ? 0 : 2 * n) + stack) * block * 4u;
 }
 
 // Validates, fills the parameter block and enqueues the whole pass on
