@@ -1,28 +1,13 @@
-// dls_kernels.cu -- the GPU search (Algorithm 4 of the paper on sm_103a) and
-// the C-ABI entry points that launch it.
+// dls_kernels.cu -- the batch kernels (Algorithm 4 of the paper on sm_103a)
+// and the C-ABI entry points that launch them.
 //
-// One lane runs one depth-first search over the order positions after its
-// prefix.  Its state is the bitmask form of Section 3 -- a word per row and
-// per column holding the values in use, plus the two diagonal words md/ad --
-// and a stack of (remaining candidates, placed value) per position, i.e. the
-// L[i][j] / LS[i][j] pairs of Algorithm 4 kept as an explicit stack instead of
-// nested loops.  Row/column words and the stack live in shared memory in a
-// thread-minor layout (word w of thread t at w * blockDim + t), so a warp's
-// accesses hit 32 distinct banks whatever positions its lanes are at; the
+// The per-lane search (state, step, prefix loading) is in dls_search.cuh.
+// Row/column words and the stack live in shared memory in a thread-minor
+// layout (word w of thread t at w * blockDim + t), so a warp's accesses hit
+// 32 distinct banks whatever positions its lanes are at; or, where they fit,
+// the row and column words are packed into two 64-bit registers.  The
 // diagonal words, the current position's candidates and value stay in
 // registers.
-//
-// One iteration of a lane:
-//   nv = lowest bit of L        (Algorithm 4: LS = L & -L)
-//   d  = v ^ nv                 (take the old value out, put the new one in,
-//                                the two XOR steps of Algorithm 4 fused)
-//   row ^= d (and its mirror for vertically symmetric squares), col ^= d,
-//   md/ad ^= d when the cell lies on them
-//   nv == 0: the loop of this cell is exhausted -> pop to the previous one
-//   else:    candidates of the next cell ALL & ~(row|col|md|ad); at the last
-//            cell add popcount (each admissible value completes a square,
-//            Algorithm 1's innermost loop), an empty set is a dead end, else
-//            push and descend.
 //
 // Kernels:
 //   k_plain      -- one thread per work item, the comparison baseline.
@@ -48,20 +33,14 @@
 #include <vector>
 
 #include "dls_internal.h"
+#include "dls_search.cuh"
 
 namespace dls {
 
-constexpr unsigned FULL = 0xffffffffu;
-
 struct KParams {
-  int n;
-  uint32_t all;          // (1 << n) - 1
-  uint32_t pairmask;     // (1 << n/2) - 1, value pairs of a symmetric row
+  Geo g;                 // order size, admissible values, prefix length, last
+  Split sp;              // item split over lanes
   int order_len;
-  int depth;             // prefix length
-  int last;              // order_len - 1
-  int lanes_log2;        // work items per prefix = 1 << lanes_log2
-  int split_pos;         // order position of the item split (-1 = none)
   int check_mask;        // donation check period - 1
   int donate;
   int count_store;       // 1: counts[p] = cnt (one item per prefix, no donation)
@@ -77,198 +56,33 @@ struct KParams {
   uint8_t cj[DLS_MAX_CELLS];
 };
 
-__device__ __forceinline__ uint32_t &word_at(char *tb, uint32_t off) {
-  return *reinterpret_cast<uint32_t *>(tb + off);
-}
-
-template <bool VSYM>
-__device__ __forceinline__ uint32_t mirror(uint32_t d, int n) {
-  return VSYM ? (__brev(d) >> (32 - n)) : 0u;
-}
-
-// A cell descriptor, one per order position, kept in a shared-memory table:
-//   x: where the cell's row word and column word are -- byte offsets from the
-//      lane's first word (bits 0-15, 16-31) in shared memory, or bit shifts
-//      (bits 0-5, 8-13) into the packed registers;
-//   y: diagonal masks -- 0xffff in bits 0-15 if the cell lies on the main
-//      diagonal, 0xffff in bits 16-31 if on the anti-diagonal.
-typedef uint2 Cell;
-
-// The row/column/diagonal words of one lane (Section 3: one word per line,
-// bit v set when value v is used on it).
-//
-// REG = false: row i and column j words in shared memory, word w of thread t
-//   at st[w * blockDim + t] (rows 0..n-1, then columns).
-// REG = true: every row word packed into one 64-bit register R (row i at bit
-//   i * wr) and every column word into C (column j at bit j * wc).  With
-//   vertical symmetry a row field records the value pairs {v, n-1-v} in use
-//   (bit min(v, n-1-v)) -- a row takes each pair exactly once -- which
-//   halves its width.
-// dg holds both diagonal words: the main diagonal in bits 0-15 and the
-// anti-diagonal in bits 16-31, so that one AND with a descriptor's masks
-// selects the diagonals a cell lies on.
-template <bool REG, bool VSYM>
-struct Words {
-  unsigned long long R, C;
-  char *tb;
-  uint32_t dg;
-
-  __device__ static Cell describe(const KParams &p, int pos, int diag, unsigned B) {
-    const int i = p.ci[pos], j = p.cj[pos];
-    Cell c;
-    c.y = ((diag && i == j) ? 0x0000ffffu : 0u) | ((diag && i + j == p.n - 1) ? 0xffff0000u : 0u);
-    if (REG)
-      c.x = (uint32_t)(i * p.wr) | ((uint32_t)(j * p.wc) << 8);
-    else
-      c.x = ((uint32_t)i * B * 4u) | (((uint32_t)(p.n + j) * B * 4u) << 16);
-    return c;
-  }
-  // Admissible values of the cell: ALL & ~(row | col | md | ad).
-  __device__ uint32_t cands(Cell c, const KParams &p) const {
-    uint32_t f;
-    if (REG) {
-      uint32_t r = (uint32_t)(R >> (c.x & 63u));
-      if (VSYM) {
-        r &= p.pairmask;
-        r |= mirror<true>(r, p.n);
-      }
-      f = r | (uint32_t)(C >> ((c.x >> 8) & 63u));
-    } else {
-      f = word_at(tb, c.x & 0xffffu) | word_at(tb, c.x >> 16);
-    }
-    const uint32_t t = dg & c.y;
-    return p.all & ~(f | t | (t >> 16));
-  }
-  // XOR value bits d (the old value and/or the new one) into the words of the
-  // cell; with vertical symmetry the mirror cell (i, n-1-j) takes n-1-v, and
-  // the mirror of a main-diagonal cell lies on the anti-diagonal and vice
-  // versa.
-  __device__ void toggle(Cell c, uint32_t d, const KParams &p) {
-    const uint32_t dm = mirror<VSYM>(d, p.n);
-    if (REG) {
-      const uint32_t rd = VSYM ? ((d ^ dm) & p.pairmask) : d;
-      R ^= (unsigned long long)rd << (c.x & 63u);
-      C ^= (unsigned long long)d << ((c.x >> 8) & 63u);
-    } else {
-      word_at(tb, c.x & 0xffffu) ^= d ^ dm;
-      word_at(tb, c.x >> 16) ^= d;
-    }
-    // d < 2^16, so d * 0x10001 puts d in both halves
-    if (VSYM) {
-      const uint32_t swapped = __byte_perm(c.y, 0u, 0x1032u);
-      dg ^= ((d * 0x10001u) & c.y) ^ ((dm * 0x10001u) & swapped);
-    } else {
-      dg ^= (d * 0x10001u) & c.y;
-    }
-  }
-  __device__ void clear(const KParams &p, unsigned B) {
-    dg = 0u;
-    if (REG) {
-      R = C = 0ull;
-    } else {
-      for (int w = 0; w < 2 * p.n; ++w) word_at(tb, (uint32_t)w * B * 4u) = 0u;
-    }
-  }
-};
-
-// Per-lane search state.
-template <bool REG, bool VSYM>
-struct Lane {
-  Words<REG, VSYM> w;
-  int p;                 // current order position
-  uint32_t L;            // untried candidates at p
-  uint32_t v;            // value placed at p (one-hot), 0 = none yet
-  Cell info;             // cell descriptor of p
-  uint32_t splitc;       // nodes met at split_pos so far
-  uint32_t sub;          // residue class of split nodes this item keeps
-  long long prefix;      // prefix index of the current item
-  unsigned long long cnt;    // completions found for the current item
-  unsigned long long nodes;  // placements made (node counting variant)
-};
-
-// One search iteration.  Returns true when the lane's item is finished.
-//
-// Written without data-dependent branches so that the lanes of a warp -- each
-// at its own position of its own subtree -- stay converged: every lane
-// computes the candidates of the next cell, and the outcome (descend, dead
-// end, last cell, exhausted level) only selects which registers change and
-// whether the stack is written or read.
-template <bool REG, bool VSYM, bool NODES, bool SPLIT>
-__device__ __forceinline__ bool dfs_step(Lane<REG, VSYM> &s, const KParams &p,
-                                         uint32_t *stk, const Cell *tbl,
-                                         unsigned B) {
-  const uint32_t nv = s.L & (0u - s.L);
-  s.w.toggle(s.info, s.v ^ nv, p);
-  s.L ^= nv;
-  s.v = nv;
-  const bool pop = nv == 0u;
-  bool skip = false;
-  if (SPLIT) {
-    const bool at = (s.p == p.split_pos) && !pop;
-    skip = at && ((s.splitc & ((1u << p.lanes_log2) - 1u)) != s.sub);
-    s.splitc += at ? 1u : 0u;
-    if (NODES && !pop && !skip && (s.p >= p.split_pos || s.sub == 0u)) s.nodes++;
-  } else if (NODES && !pop) {
-    s.nodes++;
-  }
-  const int q = s.p + 1;  // <= last: a lane never stands on the last cell
-  const Cell info1 = tbl[q];
-  const uint32_t L1 = s.w.cands(info1, p);
-  const bool live = !pop && !skip;
-  const bool leaf = q == p.last;
-  const unsigned leaves = (live && leaf) ? (unsigned)__popc(L1) : 0u;
-  s.cnt += leaves;
-  if (NODES) s.nodes += leaves;
-  const bool down = live && !leaf && L1 != 0u;
-  if (down) stk[(s.p - p.depth) * B] = s.L | (s.v << 16);
-  const int pp = s.p - 1;
-  const bool up = pop && pp >= p.depth;
-  uint32_t e = 0u;
-  Cell infoP = make_uint2(0u, 0u);
-  if (up) {
-    e = stk[(pp - p.depth) * B];
-    infoP = tbl[pp];
-  }
-  s.p = down ? q : (pop ? pp : s.p);
-  s.L = down ? L1 : (up ? (e & 0xffffu) : s.L);
-  s.v = down ? 0u : (up ? (e >> 16) : s.v);
-  s.info.x = down ? info1.x : (up ? infoP.x : s.info.x);
-  s.info.y = down ? info1.y : (up ? infoP.y : s.info.y);
-  return pop && !up;
-}
-
 // Load work item `item` into the lane.  Returns true if it is already
 // finished (invalid prefix, or nothing left to search).
 template <bool REG, bool VSYM, bool NODES>
-__device__ bool load_item(Lane<REG, VSYM> &s, const KParams &p, long long item,
+__device__ bool load_item(Lane<REG> &s, const KParams &p, long long item,
                           const Cell *tbl, unsigned B) {
-  s.prefix = item >> p.lanes_log2;
-  s.sub = (uint32_t)(item & ((1ll << p.lanes_log2) - 1));
+  const Geo &g = p.g;
+  s.prefix = item >> p.sp.lanes_log2;
+  s.sub = (uint32_t)(item & ((1ll << p.sp.lanes_log2) - 1));
   s.cnt = 0ull;
   s.splitc = 0u;
-  s.w.clear(p, B);
-  const uint8_t *rec = p.prefixes + (size_t)s.prefix * (size_t)p.depth;
-  for (int t = 0; t < p.depth; ++t) {
-    const uint32_t val = rec[t];
-    const Cell info = tbl[t];
-    const uint32_t b = (val < (uint32_t)p.n) ? (1u << val) : 0u;
-    if ((s.w.cands(info, p) & b) == 0u) return true;
-    s.w.toggle(info, b, p);
-  }
-  if (p.depth == p.order_len) {
+  s.w.clear(2 * g.n, B);
+  if (!place_prefix<REG, VSYM>(s, g, p.prefixes + (size_t)s.prefix * (size_t)g.depth, tbl))
+    return true;
+  if (g.depth == p.order_len) {
     s.cnt = (s.sub == 0u) ? 1ull : 0ull;
     return true;
   }
-  const Cell info = tbl[p.depth];
-  const uint32_t L = s.w.cands(info, p);
-  if (p.depth == p.last) {
+  const Cell info = tbl[g.depth];
+  const uint32_t L = s.w.template cands<VSYM>(info, g);
+  if (g.depth == g.last) {
     if (s.sub == 0u) {
       s.cnt = (unsigned)__popc(L);
       if (NODES) s.nodes += (unsigned)__popc(L);
     }
     return true;
   }
-  s.p = p.depth;
+  s.p = g.depth;
   s.L = L;
   s.v = 0u;
   s.info = info;
@@ -305,17 +119,17 @@ __device__ void block_reduce_add(unsigned long long v, unsigned long long *dst,
 // Shared memory: [table: one Cell (8 bytes) per order position]
 //                [words: 2n * B, shared-memory variant only]
 //                [stack: (last - depth) * B]
-template <bool REG, bool VSYM>
+template <bool REG>
 __device__ __forceinline__ void setup(const KParams &p, int diag, uint32_t *smem,
-                                      const Cell *&tbl, uint32_t *&stk,
-                                      Lane<REG, VSYM> &s) {
+                                      const Cell *&tbl, uint32_t *&stk, Lane<REG> &s) {
   const unsigned B = blockDim.x;
   Cell *t = reinterpret_cast<Cell *>(smem);
   for (int idx = threadIdx.x; idx < p.order_len; idx += B)
-    t[idx] = Words<REG, VSYM>::describe(p, idx, diag, B);
+    t[idx] = REG ? describe_regs(p.ci[idx], p.cj[idx], p.g.n, diag != 0, p.wr, p.wc)
+                 : describe_shared(p.ci[idx], p.cj[idx], p.g.n, diag != 0, B, p.g.n);
   uint32_t *st = smem + 2 * ((p.order_len + 31) & ~31);
   s.w.tb = reinterpret_cast<char *>(st + threadIdx.x);
-  stk = st + (REG ? 0 : 2 * p.n * (int)B) + threadIdx.x;
+  stk = st + (REG ? 0 : 2 * p.g.n * (int)B) + threadIdx.x;
   tbl = t;
   s.nodes = 0ull;
   s.prefix = 0;
@@ -337,8 +151,9 @@ __global__ void __launch_bounds__(512) k_plain(const __grid_constant__ KParams p
   const unsigned B = blockDim.x;
   const Cell *tbl;
   uint32_t *stk;
-  Lane<REG, VSYM> s;
+  Lane<REG> s;
   setup(p, diag, smem, tbl, stk, s);
+  uint32_t *sbase = stk - p.g.depth * (int)B;
 
   unsigned long long lane_total = 0ull;
   const long long item = (long long)blockIdx.x * B + threadIdx.x;
@@ -348,7 +163,7 @@ __global__ void __launch_bounds__(512) k_plain(const __grid_constant__ KParams p
     if (!busy) flush_count(s.prefix, s.cnt, p, lane_total);
   }
   while (__any_sync(FULL, busy)) {
-    if (busy && dfs_step<REG, VSYM, NODES, SPLIT>(s, p, stk, tbl, B)) {
+    if (busy && dfs_step<REG, VSYM, NODES, SPLIT>(s, p.g, p.sp, sbase, tbl, B)) {
       busy = false;
       flush_count(s.prefix, s.cnt, p, lane_total);
     }
@@ -369,16 +184,17 @@ __device__ __forceinline__ int nth_set_bit(unsigned m, int r) {
 // path, undoes its placements below pd and takes the untried candidates of
 // pd, which the busy lane gives up.
 template <bool REG, bool VSYM>
-__device__ void donate(Lane<REG, VSYM> &s, bool &busy, const KParams &p,
-                       uint32_t *stk, const Cell *tbl, int lane, unsigned B) {
+__device__ void donate(Lane<REG> &s, bool &busy, const KParams &p, uint32_t *stk,
+                       const Cell *tbl, int lane, unsigned B) {
+  const Geo &g = p.g;
   const unsigned idle = __ballot_sync(FULL, !busy);
   if (idle == 0u || idle == FULL) return;
-  const int lo = max(p.depth, p.split_pos + 1);
+  const int lo = max(g.depth, p.sp.pos + 1);
   int pd = -1;
   uint32_t Lpd = 0u, vpd = 0u;
   if (busy) {
     for (int q = lo; q < s.p; ++q) {
-      const uint32_t e = stk[(q - p.depth) * B];
+      const uint32_t e = stk[(q - g.depth) * B];
       if (e & 0xffffu) {
         pd = q;
         Lpd = e & 0xffffu;
@@ -425,16 +241,16 @@ __device__ void donate(Lane<REG, VSYM> &s, bool &busy, const KParams &p,
     } else {
       uint32_t *mine = reinterpret_cast<uint32_t *>(s.w.tb);
       const uint32_t *theirs = mine + dl;
-      for (int w = 0; w < 2 * p.n; ++w) mine[w * B] = theirs[w * B];
+      for (int w = 0; w < 2 * g.n; ++w) mine[w * B] = theirs[w * B];
     }
     const uint32_t *dstk = stk + dl;
-    for (int q = p.depth; q < d_pd; ++q)
-      stk[(q - p.depth) * B] = dstk[(q - p.depth) * B] & 0xffff0000u;
+    for (int q = g.depth; q < d_pd; ++q)
+      stk[(q - g.depth) * B] = dstk[(q - g.depth) * B] & 0xffff0000u;
     s.w.dg = d_dg;
     // undo the donor's placements below pd
     for (int q = d_pd + 1; q <= d_p; ++q) {
-      const uint32_t vq = (q < d_p) ? (dstk[(q - p.depth) * B] >> 16) : d_v;
-      if (vq) s.w.toggle(tbl[q], vq, p);
+      const uint32_t vq = (q < d_p) ? (dstk[(q - g.depth) * B] >> 16) : d_v;
+      if (vq) s.w.template toggle<VSYM>(tbl[q], vq, g);
     }
     s.p = d_pd;
     s.L = d_L;
@@ -449,7 +265,7 @@ __device__ void donate(Lane<REG, VSYM> &s, bool &busy, const KParams &p,
   __syncwarp();
   if (giver) {
     if (pd < s.p)
-      stk[(pd - p.depth) * B] &= 0xffff0000u;
+      stk[(pd - g.depth) * B] &= 0xffff0000u;
     else
       s.L = 0u;
   }
@@ -465,8 +281,9 @@ __global__ void __launch_bounds__(512)
   const int lane = threadIdx.x & 31;
   const Cell *tbl;
   uint32_t *stk;
-  Lane<REG, VSYM> s;
+  Lane<REG> s;
   setup(p, diag, smem, tbl, stk, s);
+  uint32_t *sbase = stk - p.g.depth * (int)B;
 
   unsigned long long lane_total = 0ull;
   bool busy = false;
@@ -496,7 +313,7 @@ __global__ void __launch_bounds__(512)
       do {
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
-          if (busy && dfs_step<REG, VSYM, NODES, SPLIT>(s, p, stk, tbl, B)) {
+          if (busy && dfs_step<REG, VSYM, NODES, SPLIT>(s, p.g, p.sp, sbase, tbl, B)) {
             busy = false;
             flush_count(s.prefix, s.cnt, p, lane_total);
           }
@@ -504,7 +321,7 @@ __global__ void __launch_bounds__(512)
       } while (__all_sync(FULL, busy));
     } else {
       for (int it = 0; it <= p.check_mask; ++it) {
-        if (busy && dfs_step<REG, VSYM, NODES, SPLIT>(s, p, stk, tbl, B)) {
+        if (busy && dfs_step<REG, VSYM, NODES, SPLIT>(s, p.g, p.sp, sbase, tbl, B)) {
           busy = false;
           flush_count(s.prefix, s.cnt, p, lane_total);
         }
@@ -711,14 +528,14 @@ static int enqueue_count(int n, uint32_t flags, const uint8_t *order,
 
   KParams kp;
   std::memset(&kp, 0, sizeof(kp));
-  kp.n = n;
-  kp.all = (1u << n) - 1u;
-  kp.pairmask = (1u << (n / 2)) - 1u;
+  kp.g.n = n;
+  kp.g.all = (1u << n) - 1u;
+  kp.g.pairmask = (1u << (n / 2)) - 1u;
+  kp.g.depth = depth;
+  kp.g.last = order_len - 1;
   kp.order_len = order_len;
-  kp.depth = depth;
-  kp.last = order_len - 1;
-  kp.lanes_log2 = sh.lanes_log2;
-  kp.split_pos = sh.split_pos;
+  kp.sp.lanes_log2 = sh.lanes_log2;
+  kp.sp.pos = sh.split_pos;
   kp.check_mask = sh.check_mask;
   kp.donate = sh.donate;
   kp.count_store = store ? 1 : 0;

@@ -36,6 +36,7 @@
 #include <vector>
 
 #include "dls_internal.h"
+#include "dls_search.cuh"
 
 namespace dls {
 
@@ -43,12 +44,11 @@ constexpr int SV_WORDS = 2 * DLS_MAX_N;   // row words 0..15, column words 16..3
 constexpr int SV_HDR = 10;                // slot header words
 
 struct ServeJob {            // device job descriptor
-  int n;
+  Geo g;                     // order size, admissible values, item length, last
   uint32_t flags;
-  int depth;                 // length of the job's item prefixes
   int order_len;
-  uint8_t ci[DLS_MAX_CELLS];
-  uint8_t cj[DLS_MAX_CELLS];
+  Cell cells[DLS_MAX_CELLS]; // descriptor of each order position (shared-memory
+                             // words, column words from word 16)
 };
 
 struct ServeParams {
@@ -62,144 +62,62 @@ struct ServeParams {
   unsigned long long qcap;         // queue ring capacity
   uint32_t *slots;                 // lane slots, word w of lane g at w * G + g
   long long G;                     // lanes in the grid
-  int stack_words;                 // stack capacity of a slot
   int budget;                      // search iterations per lane per epoch
 };
 
-// Cell descriptor for the server: byte offsets of the row word (i) and the
-// column word (16 + j) from the lane's first word, diagonal flags in bits 0
-// and 16 (as in dls_kernels.cu, with a fixed row/column split).
-__device__ __forceinline__ uint32_t sv_describe(const ServeJob &job, int pos,
-                                                unsigned B) {
-  const int i = job.ci[pos], j = job.cj[pos];
-  const bool diag = (job.flags & DLS_DIAGONAL) != 0;
-  const uint32_t m = (diag && i == j) ? 1u : 0u;
-  const uint32_t a = (diag && i + j == job.n - 1) ? 1u : 0u;
-  return ((uint32_t)i * B * 4u) | m | ((((uint32_t)(DLS_MAX_N + j) * B * 4u) | a) << 16);
-}
-
-__device__ __forceinline__ uint32_t &sv_word(char *tb, uint32_t off) {
-  return *reinterpret_cast<uint32_t *>(tb + off);
-}
-
-__device__ __forceinline__ uint32_t sv_cands(char *tb, uint32_t info, uint32_t md,
-                                             uint32_t ad, uint32_t all) {
-  uint32_t f = sv_word(tb, info & 0xfffcu) | sv_word(tb, (info >> 16) & 0xfffcu);
-  f |= (info & 1u) ? md : 0u;
-  f |= (info & 0x10000u) ? ad : 0u;
-  return all & ~f;
-}
-
-// XOR value bits d into the cell's words; vertical symmetry puts n-1-v into
-// the mirror cell (same row; the mirror of a main-diagonal cell is on the
-// anti-diagonal and vice versa).
-__device__ __forceinline__ void sv_toggle(char *tb, uint32_t info, uint32_t d,
-                                          uint32_t &md, uint32_t &ad, int n,
-                                          bool vsym) {
-  const uint32_t dm = vsym ? (__brev(d) >> (32 - n)) : 0u;
-  sv_word(tb, info & 0xfffcu) ^= d ^ dm;
-  sv_word(tb, (info >> 16) & 0xfffcu) ^= d;
-  const bool onmd = (info & 1u) != 0, onad = (info & 0x10000u) != 0;
-  md ^= (onmd ? d : 0u) ^ (onad ? dm : 0u);
-  ad ^= (onad ? d : 0u) ^ (onmd ? dm : 0u);
-}
-
+// A lane of the server: the search state plus its job's shape.
 struct SvLane {
+  Lane<false> s;
   int job;          // job slot, -1 = idle
-  int n, depth, last;
   bool vsym;
-  uint32_t all;
-  int p;
-  uint32_t L, v, info, md, ad;
-  unsigned long long cnt;
+  Geo g;
+  const Cell *tbl;  // the job's descriptor table (global memory)
 };
 
-__device__ __forceinline__ void sv_job_params(SvLane &s, const ServeJob &job) {
-  s.n = job.n;
-  s.depth = job.depth;
-  s.last = job.order_len - 1;
-  s.vsym = (job.flags & DLS_VSYM) != 0;
-  s.all = (1u << job.n) - 1u;
-  // odd order with vertical symmetry: no left cell may hold (n-1)/2
-  if (s.vsym && (s.n & 1)) s.all &= ~(1u << (s.n / 2));
+__device__ __forceinline__ void sv_bind(SvLane &l, const ServeParams &P, int job) {
+  const ServeJob &J = P.jobs[job];
+  l.job = job;
+  l.g = J.g;
+  l.vsym = (J.flags & DLS_VSYM) != 0;
+  l.tbl = J.cells;
 }
 
 // Finishes an item: its count goes to the job, one item fewer is left.
-__device__ __forceinline__ void sv_finish(SvLane &s, const ServeParams &P) {
-  if (s.cnt) atomicAdd(P.job_count + s.job, s.cnt);
-  atomicSub(P.job_left + s.job, 1u);
-  s.job = -1;
+__device__ __forceinline__ void sv_finish(SvLane &l, const ServeParams &P) {
+  if (l.s.cnt) atomicAdd(P.job_count + l.job, l.s.cnt);
+  atomicSub(P.job_left + l.job, 1u);
+  l.job = -1;
 }
 
 // Loads an item; returns true if the lane now has a search to run.
-__device__ bool sv_load(SvLane &s, const ServeParams &P, uint2 item, char *tb,
-                        unsigned B) {
-  s.job = (int)item.x;
-  const ServeJob &job = P.jobs[s.job];
-  sv_job_params(s, job);
-  s.md = s.ad = 0u;
+__device__ bool sv_load(SvLane &l, const ServeParams &P, uint2 item, unsigned B) {
+  sv_bind(l, P, (int)item.x);
+  Lane<false> &s = l.s;
   s.cnt = 0ull;
-  for (int w = 0; w < SV_WORDS; ++w) sv_word(tb, (uint32_t)w * B * 4u) = 0u;
+  s.w.clear(SV_WORDS, B);
   const uint8_t *rec = P.arena + item.y;
-  bool ok = true;
-  for (int t = 0; t < s.depth && ok; ++t) {
-    const uint32_t info = sv_describe(job, t, B);
-    const uint32_t val = rec[t];
-    const uint32_t b = (val < (uint32_t)s.n) ? (1u << val) : 0u;
-    ok = (sv_cands(tb, info, s.md, s.ad, s.all) & b) != 0u;
-    if (ok) sv_toggle(tb, info, b, s.md, s.ad, s.n, s.vsym);
-  }
+  const bool ok = l.vsym ? place_prefix<false, true>(s, l.g, rec, l.tbl)
+                         : place_prefix<false, false>(s, l.g, rec, l.tbl);
   if (!ok) {
-    sv_finish(s, P);
+    sv_finish(l, P);
     return false;
   }
-  if (s.depth == job.order_len) {
+  const int order_len = l.g.last + 1;
+  if (l.g.depth == order_len) {
     s.cnt = 1ull;
-    sv_finish(s, P);
+    sv_finish(l, P);
     return false;
   }
-  s.info = sv_describe(job, s.depth, B);
-  s.L = sv_cands(tb, s.info, s.md, s.ad, s.all);
-  if (s.depth == s.last || s.L == 0u) {
-    s.cnt = (s.depth == s.last) ? (unsigned)__popc(s.L) : 0ull;
-    sv_finish(s, P);
+  s.info = l.tbl[l.g.depth];
+  s.L = l.vsym ? s.w.template cands<true>(s.info, l.g) : s.w.template cands<false>(s.info, l.g);
+  if (l.g.depth == l.g.last || s.L == 0u) {
+    s.cnt = (l.g.depth == l.g.last) ? (unsigned)__popc(s.L) : 0ull;
+    sv_finish(l, P);
     return false;
   }
-  s.p = s.depth;
+  s.p = l.g.depth;
   s.v = 0u;
   return true;
-}
-
-// One search iteration (the step of dls_kernels.cu with per-lane job
-// parameters).  Returns true when the item is finished.
-__device__ __forceinline__ bool sv_step(SvLane &s, const ServeJob &job, char *tb,
-                                        uint32_t *stk, unsigned B) {
-  const uint32_t nv = s.L & (0u - s.L);
-  sv_toggle(tb, s.info, s.v ^ nv, s.md, s.ad, s.n, s.vsym);
-  s.L ^= nv;
-  s.v = nv;
-  if (nv == 0u) {
-    if (--s.p < s.depth) return true;
-    const uint32_t e = stk[(s.p - s.depth) * B];
-    s.L = e & 0xffffu;
-    s.v = e >> 16;
-    s.info = sv_describe(job, s.p, B);
-    return false;
-  }
-  const int q = s.p + 1;
-  const uint32_t info1 = sv_describe(job, q, B);
-  const uint32_t L1 = sv_cands(tb, info1, s.md, s.ad, s.all);
-  if (q == s.last) {
-    s.cnt += (unsigned)__popc(L1);
-    return false;
-  }
-  if (L1 == 0u) return false;
-  stk[(s.p - s.depth) * B] = s.L | (s.v << 16);
-  s.p = q;
-  s.L = L1;
-  s.v = 0u;
-  s.info = info1;
-  return false;
 }
 
 // Items handed out beyond the queued ones are taken back after an epoch
@@ -208,32 +126,33 @@ __global__ void k_serve_clamp(unsigned long long *head, unsigned long long tail)
   if (*head > tail) *head = tail;
 }
 
-// Shared memory per lane: SV_WORDS words + stack_words stack entries,
-// thread-minor.
+// Shared memory per lane: SV_WORDS words + the stack, thread-minor.
 __global__ void __launch_bounds__(256) k_serve(const __grid_constant__ ServeParams P) {
   extern __shared__ uint32_t smem[];
   const unsigned B = blockDim.x;
-  const long long g = (long long)blockIdx.x * B + threadIdx.x;
-  char *tb = reinterpret_cast<char *>(smem + threadIdx.x);
+  const long long gl = (long long)blockIdx.x * B + threadIdx.x;
   uint32_t *stk = smem + SV_WORDS * B + threadIdx.x;
-  uint32_t *slot = P.slots + g;
+  uint32_t *slot = P.slots + gl;
   const long long G = P.G;
+  const Split nosplit = {-1, 0};
 
-  SvLane s;
-  s.job = -1;
+  SvLane l;
+  l.s.w.tb = reinterpret_cast<char *>(smem + threadIdx.x);
+  l.s.w.R = l.s.w.C = 0ull;
+  l.s.nodes = 0ull;
+  l.job = -1;
   bool busy = slot[0] != 0u;
   if (busy) {
-    s.job = (int)slot[1 * G];
-    sv_job_params(s, P.jobs[s.job]);
+    sv_bind(l, P, (int)slot[1 * G]);
+    Lane<false> &s = l.s;
     s.p = (int)slot[2 * G];
     s.L = slot[3 * G];
     s.v = slot[4 * G];
-    s.md = slot[5 * G];
-    s.ad = slot[6 * G];
+    s.w.dg = slot[5 * G];
     s.cnt = (unsigned long long)slot[7 * G] | ((unsigned long long)slot[8 * G] << 32);
-    for (int w = 0; w < SV_WORDS; ++w) sv_word(tb, (uint32_t)w * B * 4u) = slot[(SV_HDR + w) * G];
-    for (int k = 0; k < s.p - s.depth; ++k) stk[k * B] = slot[(SV_HDR + SV_WORDS + k) * G];
-    s.info = sv_describe(P.jobs[s.job], s.p, B);
+    for (int w = 0; w < SV_WORDS; ++w) word_at(s.w.tb, (uint32_t)w * B * 4u) = slot[(SV_HDR + w) * G];
+    for (int k = 0; k < s.p - l.g.depth; ++k) stk[k * B] = slot[(SV_HDR + SV_WORDS + k) * G];
+    s.info = l.tbl[s.p];
   }
   bool drained = false;
   for (int it = 0; it < P.budget; ++it) {
@@ -244,26 +163,29 @@ __global__ void __launch_bounds__(256) k_serve(const __grid_constant__ ServePara
         drained = true;
         break;
       }
-      busy = sv_load(s, P, P.queue[idx % P.qcap], tb, B);
+      busy = sv_load(l, P, P.queue[idx % P.qcap], B);
       continue;
     }
-    if (sv_step(s, P.jobs[s.job], tb, stk, B)) {
-      sv_finish(s, P);
+    uint32_t *sbase = stk - l.g.depth * (int)B;
+    const bool fin = l.vsym ? dfs_step<false, true, false, false>(l.s, l.g, nosplit, sbase, l.tbl, B)
+                            : dfs_step<false, false, false, false>(l.s, l.g, nosplit, sbase, l.tbl, B);
+    if (fin) {
+      sv_finish(l, P);
       busy = false;
     }
   }
   slot[0] = busy ? 1u : 0u;
   if (busy) {
-    slot[1 * G] = (uint32_t)s.job;
+    const Lane<false> &s = l.s;
+    slot[1 * G] = (uint32_t)l.job;
     slot[2 * G] = (uint32_t)s.p;
     slot[3 * G] = s.L;
     slot[4 * G] = s.v;
-    slot[5 * G] = s.md;
-    slot[6 * G] = s.ad;
+    slot[5 * G] = s.w.dg;
     slot[7 * G] = (uint32_t)s.cnt;
     slot[8 * G] = (uint32_t)(s.cnt >> 32);
-    for (int w = 0; w < SV_WORDS; ++w) slot[(SV_HDR + w) * G] = sv_word(tb, (uint32_t)w * B * 4u);
-    for (int k = 0; k < s.p - s.depth; ++k) slot[(SV_HDR + SV_WORDS + k) * G] = stk[k * B];
+    for (int w = 0; w < SV_WORDS; ++w) slot[(SV_HDR + w) * G] = word_at(s.w.tb, (uint32_t)w * B * 4u);
+    for (int k = 0; k < s.p - l.g.depth; ++k) slot[(SV_HDR + SV_WORDS + k) * G] = stk[k * B];
   }
 }
 
@@ -558,14 +480,19 @@ int dls_server_step(dls_server *s) {
     s->free_slots.pop_back();
     ServeJob &dj = s->h_job_stage[j->slot];
     std::memset(&dj, 0, sizeof(dj));
-    dj.n = j->n;
     dj.flags = j->flags;
-    dj.depth = j->depth;
     dj.order_len = (int)(j->order.size() / 2);
-    for (int t = 0; t < dj.order_len; ++t) {
-      dj.ci[t] = j->order[2 * t];
-      dj.cj[t] = j->order[2 * t + 1];
-    }
+    dj.g.n = j->n;
+    dj.g.all = (1u << j->n) - 1u;
+    // odd order with vertical symmetry: no left cell may hold (n-1)/2
+    if ((j->flags & DLS_VSYM) && (j->n & 1)) dj.g.all &= ~(1u << (j->n / 2));
+    dj.g.pairmask = (1u << (j->n / 2)) - 1u;
+    dj.g.depth = j->depth;
+    dj.g.last = dj.order_len - 1;
+    for (int t = 0; t < dj.order_len; ++t)
+      dj.cells[t] = describe_shared(j->order[2 * t], j->order[2 * t + 1], j->n,
+                                    (j->flags & DLS_DIAGONAL) != 0,
+                                    (unsigned)s->cfg.block_threads, DLS_MAX_N);
     s->h_count[j->slot] = 0ull;
     s->h_left[j->slot] = (unsigned int)j->n_items;
     e = cudaMemcpyAsync(s->d_jobs + j->slot, &dj, sizeof(ServeJob), cudaMemcpyHostToDevice, s->stream);
@@ -627,7 +554,6 @@ int dls_server_step(dls_server *s) {
   P.qcap = (unsigned long long)s->cfg.queue_items;
   P.slots = s->d_slots;
   P.G = s->G;
-  P.stack_words = s->cfg.max_order * s->cfg.max_order;
   P.budget = s->cfg.budget;
   k_serve<<<s->grid, s->cfg.block_threads, s->smem, s->stream>>>(P);
   // lanes that found the queue empty advanced the head past the tail
