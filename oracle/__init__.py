@@ -18,6 +18,7 @@ from .core import (  # noqa: F401
     count,
     count_many,
     extend,
+    hourglass_classes,
     sample_prefix,
     multiplier,
 )

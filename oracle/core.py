@@ -58,6 +58,10 @@ def _load():
     lib.oracle_sample_prefix.argtypes = [ctypes.c_int, ctypes.c_uint, u8p, ctypes.c_int,
                                          ctypes.c_int, u32p, ctypes.c_int64, u8p]
     lib.oracle_sample_prefix.restype = ctypes.c_int64
+    lib.oracle_hourglass_classes.argtypes = [ctypes.c_int, ctypes.c_uint, u8p, ctypes.c_int,
+                                             u8p, ctypes.c_int64,
+                                             ctypes.POINTER(ctypes.c_long), ctypes.c_int]
+    lib.oracle_hourglass_classes.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -154,6 +158,25 @@ def sample_prefix(n, flags, order, depth, draws):
     if used < 0:
         return None, -1
     return out[:depth].copy(), int(used)
+
+
+def hourglass_classes(n, flags, order, hourglasses, threads=1):
+    """Class size of each hourglass (rows of ``hourglasses``: values of the
+    first cells of ``order``) if it is canonic, else 0 (Algorithm 5)."""
+    lib = _load()
+    o = _order_array(order)
+    hg = np.ascontiguousarray(np.asarray(hourglasses, dtype=np.uint8))
+    if hg.ndim != 2 or hg.shape[1] > len(o):
+        raise ValueError("hourglasses must be 2-D and no longer than the order")
+    out = np.zeros(len(hg), dtype=np.int_)
+    if len(hg):
+        lib.oracle_hourglass_classes(n, flags, _ptr(o, ctypes.c_uint8), hg.shape[1],
+                                     _ptr(hg, ctypes.c_uint8), len(hg),
+                                     out.ctypes.data_as(ctypes.POINTER(ctypes.c_long)),
+                                     int(threads))
+    if (out < 0).any():
+        raise ValueError("oracle_hourglass_classes: bad arguments")
+    return out
 
 
 def multiplier(n, flags):

@@ -370,3 +370,192 @@ int64_t oracle_sample_prefix(int n, unsigned flags, const uint8_t *order,
     free(s);
     return used;
 }
+
+/* ------------------------------------------------ symmetry breaking --
+ *
+ * Section 4.  An hourglass design has row 0, the last row and both diagonals
+ * filled.  The M-transformations that keep hourglasses (Section 4.2) are
+ * generated by
+ *   - the vertical mirror, column j -> N-1-j (not for vertically symmetric
+ *     squares: there it only renames the symbols, Section 5.4);
+ *   - for any subset S of {0..N/2-1}: swap rows k, N-1-k and columns k,
+ *     N-1-k for every k in S (the second type of Section 4.1);
+ *   - for any permutation s of {1..N/2-1}: row and column k -> s(k) and
+ *     N-1-k -> N-1-s(k) (the third type, with index 0 kept in place so that
+ *     row 0 only ever trades places with the last row).
+ * After a transformation the symbols are renamed so that row 0 reads
+ * 0..N-1 (Section 4.1).  Algorithm 5: an hourglass is canonic when no image
+ * is lexicographically smaller (cells compared in row-major order); its class
+ * size is the number of distinct images. */
+
+typedef struct {
+    int n;
+    int a[OR_MAXN][OR_MAXN];   /* -1 = empty */
+} or_grid;
+
+static void or_apply(const or_grid *src, or_grid *dst, int mirror,
+                     unsigned subset, const int *perm)
+{
+    int n = src->n, h = n / 2;
+    or_grid t1, t2;
+    /* vertical mirror */
+    t1.n = n;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j)
+            t1.a[i][j] = mirror ? src->a[i][n - 1 - j] : src->a[i][j];
+    /* symmetric row+column pair swaps */
+    int sw[OR_MAXN];
+    for (int k = 0; k < n; ++k) sw[k] = k;
+    for (int k = 0; k < h; ++k)
+        if (subset >> k & 1u) {
+            sw[k] = n - 1 - k;
+            sw[n - 1 - k] = k;
+        }
+    t2.n = n;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) t2.a[sw[i]][sw[j]] = t1.a[i][j];
+    /* paired permutation of the left-half indices and their mirrors */
+    int pm[OR_MAXN];
+    for (int k = 0; k < n; ++k) pm[k] = k;
+    for (int k = 0; k < h; ++k) {
+        pm[k] = perm[k];
+        pm[n - 1 - k] = n - 1 - perm[k];
+    }
+    dst->n = n;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) dst->a[pm[i]][pm[j]] = t2.a[i][j];
+    /* rename the symbols so that row 0 reads 0..N-1 */
+    int ren[OR_MAXN];
+    for (int j = 0; j < n; ++j) ren[dst->a[0][j]] = j;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j)
+            if (dst->a[i][j] >= 0) dst->a[i][j] = ren[dst->a[i][j]];
+}
+
+static int or_grid_cmp(const or_grid *x, const or_grid *y)
+{
+    for (int i = 0; i < x->n; ++i)
+        for (int j = 0; j < x->n; ++j)
+            if (x->a[i][j] != y->a[i][j]) return x->a[i][j] < y->a[i][j] ? -1 : 1;
+    return 0;
+}
+
+/* next permutation of p[0..m-1] in lexicographic order; 0 when done */
+static int or_next_perm(int *p, int m)
+{
+    int i = m - 2;
+    while (i >= 0 && p[i] >= p[i + 1]) i--;
+    if (i < 0) return 0;
+    int j = m - 1;
+    while (p[j] <= p[i]) j--;
+    int t = p[i]; p[i] = p[j]; p[j] = t;
+    for (int a = i + 1, b = m - 1; a < b; ++a, --b) {
+        t = p[a]; p[a] = p[b]; p[b] = t;
+    }
+    return 1;
+}
+
+/* Class size of one hourglass if it is canonic, else 0 (Algorithm 5).  The
+ * hourglass is given as the values of the first `len` cells of `order`
+ * (row 0 must be 0..N-1); with vertical symmetry the cells are left-half
+ * cells and their mirrors are filled in.  Orders 2..11.  Returns -1 on bad
+ * arguments. */
+long oracle_hourglass_class(int n, unsigned flags, const uint8_t *order, int len,
+                            const uint8_t *values)
+{
+    if (n < 2 || n > 11 || len < 0 || len > n * n) return -1;
+    int vsym = (flags & OR_VSYM) != 0;
+    or_grid H;
+    H.n = n;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) H.a[i][j] = -1;
+    for (int t = 0; t < len; ++t) {
+        int i = order[2 * t], j = order[2 * t + 1];
+        H.a[i][j] = values[t];
+        if (vsym) H.a[i][n - 1 - j] = n - 1 - values[t];
+    }
+    for (int j = 0; j < n; ++j)
+        if (H.a[0][j] != j) return -1;
+    int h = n / 2;
+    /* at most 2 * 2^5 * 4! = 1536 images for N <= 11 */
+    static __thread or_grid eqc[2 * (1 << 5) * 24];
+    long k = 0;
+    int perm[OR_MAXN];
+    for (int mirror = 0; mirror < (vsym ? 1 : 2); ++mirror) {
+        for (unsigned subset = 0; subset < (1u << h); ++subset) {
+            for (int t = 0; t < h; ++t) perm[t] = t;
+            do {
+                or_grid T;
+                or_apply(&H, &T, mirror, subset, perm);
+                if (or_grid_cmp(&T, &H) < 0) return 0;
+                if (k < (long)(sizeof(eqc) / sizeof(eqc[0]))) eqc[k] = T;
+                k++;
+            } while (or_next_perm(perm + 1, h - 1));
+        }
+    }
+    /* ComputeDistinct: count images not equal to an earlier image */
+    long distinct = 0;
+    for (long x = 0; x < k; ++x) {
+        int seen = 0;
+        for (long y = 0; y < x && !seen; ++y)
+            if (or_grid_cmp(&eqc[x], &eqc[y]) == 0) seen = 1;
+        if (!seen) distinct++;
+    }
+    return distinct;
+}
+
+typedef struct {
+    int n;
+    unsigned flags;
+    const uint8_t *order;
+    int len;
+    const uint8_t *values;
+    int64_t count;
+    long *out;
+    int64_t next;
+    pthread_mutex_t lock;
+} or_canon_job;
+
+static void *or_canon_worker(void *arg)
+{
+    or_canon_job *job = (or_canon_job *)arg;
+    for (;;) {
+        pthread_mutex_lock(&job->lock);
+        int64_t lo = job->next;
+        job->next += 256;
+        pthread_mutex_unlock(&job->lock);
+        if (lo >= job->count) break;
+        int64_t hi = lo + 256 < job->count ? lo + 256 : job->count;
+        for (int64_t q = lo; q < hi; ++q)
+            job->out[q] = oracle_hourglass_class(job->n, job->flags, job->order, job->len,
+                                                 job->values + (size_t)q * job->len);
+    }
+    return NULL;
+}
+
+/* oracle_hourglass_class over many hourglasses on `threads` threads. */
+int oracle_hourglass_classes(int n, unsigned flags, const uint8_t *order, int len,
+                             const uint8_t *values, int64_t count, long *out,
+                             int threads)
+{
+    or_canon_job job;
+    memset(&job, 0, sizeof(job));
+    job.n = n;
+    job.flags = flags;
+    job.order = order;
+    job.len = len;
+    job.values = values;
+    job.count = count;
+    job.out = out;
+    pthread_mutex_init(&job.lock, NULL);
+    if (threads < 1) threads = 1;
+    if (threads > 256) threads = 256;
+    pthread_t tid[256];
+    int started = 0;
+    for (int t = 1; t < threads; ++t)
+        if (pthread_create(&tid[started], NULL, or_canon_worker, &job) == 0) started++;
+    or_canon_worker(&job);
+    for (int t = 0; t < started; ++t) pthread_join(tid[t], NULL);
+    pthread_mutex_destroy(&job.lock);
+    return 0;
+}

@@ -73,6 +73,30 @@ def hourglass(n):
     return out
 
 
+def hourglass_cells(n, vsym=False):
+    """The cells of an hourglass design (Section 4.2) in the order they are
+    filled: row 0, main diagonal, anti-diagonal, last row (left half only
+    with vsym, where a diagonal cell's mirror lies on the other diagonal)."""
+    w = n // 2 if vsym else n
+    seen = set()
+    out = []
+
+    def add(c):
+        if c not in seen and c[1] < w:
+            seen.add(c)
+            out.append(c)
+
+    for j in range(n):
+        add((0, j))
+    for i in range(n):
+        add((i, i))
+    for i in range(n):
+        add((i, n - 1 - i))
+    for j in range(n):
+        add((n - 1, j))
+    return out
+
+
 def identity(n, vsym=False):
     """Values of row 0 fixed to 0..N-1 (left half only when vsym)."""
     return [j for j in _cols(n, vsym)]
