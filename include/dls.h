@@ -80,7 +80,7 @@ typedef enum {
     /* row by row, left to right (the trivial order of Sections 2.1, 5.3) */
     DLS_ORDER_ROW_MAJOR = 1,
     /* row 0, both diagonals, last row, then the rest: the cells of an
-     * hourglass design first (Section 4.2) */
+     * hourglass design first (Section 4.2); left half with DLS_VSYM */
     DLS_ORDER_HOURGLASS = 2,
     /* the greedy most-constrained-cell order of Section 2.3 with its
      * forced-last-cell rule (Fig. 1 for order 9) */
@@ -240,6 +240,26 @@ int dls_count_host(int n, uint32_t flags, const uint8_t *order,
                    int64_t n_prefixes, uint64_t *h_counts,
                    dls_u128 *total_out, const dls_launch_t *cfg,
                    void *stream);
+
+/* ---------------------------------------------------- symmetry breaking */
+
+/* Canonical hourglasses (Section 4.2, Algorithm 5).  An hourglass design has
+ * row 0, the last row and both diagonals filled; `order` lists exactly those
+ * cells (left half with DLS_VSYM) -- e.g. the first cells of
+ * DLS_ORDER_HOURGLASS -- and d_hourglasses (DEVICE, count * len bytes) holds
+ * their values, one hourglass per record.  For each, d_class_size (DEVICE,
+ * count uint32) receives the size of its class under the M-transformations
+ * that keep hourglasses (Section 4.1: vertical mirror -- not with DLS_VSYM,
+ * Section 5.4 --, symmetric row+column pair swaps, paired permutations of
+ * the indices 1..n/2-1) if it is the lexicographically least member after
+ * row 0 is renamed to 0..n-1, else 0.  By Proposition 1 / Corollary 1 the
+ * number of squares with row 0 fixed is the sum over canonical hourglasses
+ * of class size x completions.  DLS_DIAGONAL required; 2 <= n <= 11 (even n
+ * with DLS_VSYM).  Asynchronous on `stream`.  Errors: INVALID_N, BAD_ARG,
+ * BAD_ORDER (cells are not the hourglass cells), CUDA. */
+int dls_hourglass_classes(int n, uint32_t flags, const uint8_t *order, int len,
+                          const uint8_t *d_hourglasses, int64_t count,
+                          uint32_t *d_class_size, void *stream);
 
 /* ------------------------------------------------------------ serving */
 

@@ -87,6 +87,7 @@ def load():
             "g.build()\"` or `python -m paper_1709_02599_gb300.build`" % LIB_PATH)
     lib = ctypes.CDLL(LIB_PATH)
     c_int, c_u32, c_i64 = ctypes.c_int, ctypes.c_uint32, ctypes.c_int64
+    c_int64_t = ctypes.c_int64
     sig = {
         "dls_strerror": (ctypes.c_char_p, [c_int]),
         "dls_last_cuda_error": (ctypes.c_char_p, []),
@@ -111,6 +112,7 @@ def load():
                                    ctypes.POINTER(U128), ctypes.POINTER(LaunchT), vp]),
         "dls_count_host_noalloc": (c_int, [c_int, c_u32, u8p, c_int, vp, c_int, c_i64, vp,
                                            ctypes.POINTER(U128), ctypes.POINTER(LaunchT), vp]),
+        "dls_hourglass_classes": (c_int, [c_int, c_u32, u8p, c_int, vp, c_int64_t, vp, vp]),
         "dls_release": (None, []),
         "dls_server_default_cfg": (None, [ctypes.POINTER(ServerCfg)]),
         "dls_server_create": (c_int, [ctypes.POINTER(ServerCfg), ctypes.POINTER(vp)]),

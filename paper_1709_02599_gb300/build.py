@@ -16,7 +16,8 @@ LIB = os.path.join(OUT, "libdls.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["dls_host.cpp", "dls_kernels.cu", "dls_serve.cu", "dls_noalloc.cu"]
+SOURCES = ["dls_host.cpp", "dls_kernels.cu", "dls_serve.cu", "dls_symmetry.cu",
+           "dls_noalloc.cu"]
 
 
 def nvcc():

@@ -131,10 +131,11 @@ static void order_md_ad_rows(int n, bool vsym, int first_rows,
     for (int j = 0; j < w; ++j) add(i, j);
 }
 
-static void order_hourglass(int n, std::vector<std::pair<int, int>> &out) {
+static void order_hourglass(int n, bool vsym, std::vector<std::pair<int, int>> &out) {
+  const int w = vsym ? n / 2 : n;
   bool used[DLS_MAX_N][DLS_MAX_N] = {};
   auto add = [&](int i, int j) {
-    if (used[i][j]) return;
+    if (j >= w || used[i][j]) return;
     used[i][j] = true;
     out.push_back({i, j});
   };
@@ -279,8 +280,7 @@ int dls_fill_order(int n, uint32_t flags, int kind, int first_rows,
         for (int j = 0; j < (vsym ? n / 2 : n); ++j) cells.push_back({i, j});
       break;
     case DLS_ORDER_HOURGLASS:
-      if (vsym) return DLS_ERR_BAD_ARG;
-      order_hourglass(n, cells);
+      order_hourglass(n, vsym, cells);
       break;
     case DLS_ORDER_HEURISTIC: {
       std::vector<std::pair<int, int>> row0;

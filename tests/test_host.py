@@ -50,6 +50,14 @@ def test_fill_orders_match_oracle(dls, n):
         assert got == orders.md_ad_rows(n, first_rows=k)
 
 
+@pytest.mark.parametrize("n", [4, 6, 8, 10])
+def test_symmetric_hourglass_order(dls, n):
+    got = [tuple(c) for c in dls.fill_order(n, D | V, dls.ORDER_HOURGLASS)]
+    hc = orders.hourglass_cells(n, True)
+    assert got[:len(hc)] == hc
+    assert sorted(got) == sorted(orders.row_major(n, vsym=True))
+
+
 def test_heuristic_order_reproduces_fig1(dls):
     got = [tuple(c) for c in dls.fill_order(9, D, dls.ORDER_HEURISTIC)]
     assert got[:9] == orders.row0(9)
