@@ -46,7 +46,7 @@ def hourglass_classes(n, flags, order, d_hourglasses, stream=None):
     return out
 
 
-def count_symmetry_broken(n, flags=DIAGONAL, launch=None):
+def count_symmetry_broken(n, flags=DIAGONAL, launch=None, min_items=1 << 20):
     """Squares with row 0 fixed to 0..n-1, counted through canonical
     hourglasses.  Returns a dict with the total and the class statistics."""
     import torch
@@ -59,13 +59,24 @@ def count_symmetry_broken(n, flags=DIAGONAL, launch=None):
     d_hg = torch.from_numpy(hg).cuda()
     sizes = hourglass_classes(n, flags, order[:k], d_hg)
     canon = torch.nonzero(sizes > 0).flatten()
-    reps = d_hg[canon].contiguous()
-    counts = dls_count(n, flags, order, reps, launch=launch)
+    sz = sizes[canon].cpu().numpy().astype(np.int64)
+    reps = hg[canon.cpu().numpy()]
+    # split the representatives further (Section 5.2) until there are enough
+    # independent items to keep every lane busy; each item keeps the class
+    # size of its representative
+    depth, items, parent = k, reps, np.arange(len(reps), dtype=np.int64)
+    while len(items) < min_items and depth < len(order) - 2:
+        items, par = extend_prefixes(n, flags, order, items, depth + 1)
+        parent = parent[par]
+        depth += 1
+    counts = dls_count(n, flags, order, torch.from_numpy(items).cuda(), launch=launch)
     torch.cuda.synchronize()
-    sz = sizes[canon].cpu().numpy().astype(np.uint64)
     ct = counts.cpu().numpy()
-    total = sum(int(s) * int(c) for s, c in zip(sz, ct))
+    per_rep = np.zeros(len(reps), dtype=object)
+    for r, c in zip(parent, ct):
+        per_rep[r] += int(c)
+    total = sum(int(s) * int(c) for s, c in zip(sz, per_rep))
     return {"total": total, "hourglasses": int(len(hg)), "classes": int(len(canon)),
             "class_size_sum": int(sizes.sum().item()), "max_class": int(sz.max()) if len(sz) else 0,
-            "squares_counted": int(ct.sum()), "order": order, "hourglass_values": hg,
-            "class_sizes": sizes.cpu().numpy()}
+            "squares_counted": int(ct.sum()), "items": int(len(items)), "split_depth": depth,
+            "order": order, "hourglass_values": hg, "class_sizes": sizes.cpu().numpy()}
