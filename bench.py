@@ -39,8 +39,7 @@ import dls_inputs  # noqa: E402
 
 METRIC = "diagonal Latin squares enumerated/sec on 1 GB300 (exact count) vs plain launch; p99 latency"
 UNIT = "squares/s"
-WORKLOAD = "dls8_diag64"
-N, FLAGS, DIAGS, AFTER_ROW0 = 8, 1, 64, 20
+DIAGS, AFTER_ROW0 = 64, 20
 # integer operations per search node in the bitmask form (see the design
 # notes): isolate + clear the lowest candidate bit (4), mark and unmark the
 # row and column words (4), next cell's forbidden mask and complement (2),
@@ -59,9 +58,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--diagonals", type=int, default=DIAGS,
-                    help="main-diagonal fillings per rank (64 = the benchmark workload; "
-                         "fewer only for profiling captures)")
+    ap.add_argument("--workload", default="dls8_diag64", choices=["dls8_diag64", "vsym10_rows2"])
+    ap.add_argument("--diagonals", type=int, default=0,
+                    help="base prefixes per rank (0 = the workload's own: 64 diagonal "
+                         "fillings / 2000 row prefixes; fewer only for profiling captures)")
     ap.add_argument("--launch", default="", help="json dict of Launch fields (skips the "
                     "launch-shape stage of the autotuner)")
     ap.add_argument("--no-autotune", action="store_true",
@@ -85,36 +85,60 @@ def dist_env():
 
 # ------------------------------------------------------------ workloads --
 
-def product_base(dls, seed, k=DIAGS):
-    """Fill order (row 0, main diagonal, anti-diagonal, rows) and the k drawn
-    main-diagonal fillings (row 0 + main diagonal) the workload starts from."""
-    order = dls.fill_order(N, FLAGS)
-    ident = np.arange(N, dtype=np.uint8)[None]
-    diags, _ = dls.extend_prefixes(N, FLAGS, order, ident, N + (N - 1))
-    picks = dls_inputs.choose(len(diags), k, seed)
-    return order, diags[picks], picks
+class Dls8Diag64:
+    """Order 8, row 0 identity, `units` seed-drawn main-diagonal fillings
+    (row 0 + main diagonal), split 20 cells past row 0 by default."""
+    name, n, flags, units, unit_name = "dls8_diag64", 8, 1, DIAGS, "diagonal fillings"
+    default_depth = 8 + AFTER_ROW0
+    depths = [8 + 14, 8 + 17, 8 + 20, 8 + 23]
+    first_rows = 1
+
+    def base_depth(self):
+        return self.n + (self.n - 1)
+
+    def product_base(self, dls, seed, k):
+        order = dls.fill_order(self.n, self.flags, first_rows=self.first_rows)
+        ident = np.arange(self.n, dtype=np.uint8)[None]
+        allb, _ = dls.extend_prefixes(self.n, self.flags, order, ident, self.base_depth())
+        picks = dls_inputs.choose(len(allb), k, seed)
+        return order, allb[picks]
+
+    def oracle_sample(self, seed, n_units, depth, suffix):
+        """The oracle's own order and prefixes for n_units of the run's base
+        prefixes, split at `depth` (cells after the split in `suffix` order)."""
+        import oracle
+        from oracle import orders
+        vs = bool(self.flags & 2)
+        o_order = orders.md_ad_rows(self.n, vsym=vs, first_rows=self.first_rows)
+        if suffix == "heuristic":
+            o_order = orders.heuristic_complete(self.n, o_order[:depth], True, vs)
+        ident = np.array([orders.identity(self.n, vs)], np.uint8)
+        allb, _ = oracle.extend(self.n, self.flags, o_order, ident, self.base_depth())
+        picks = dls_inputs.choose(len(allb), self.units, seed)
+        sub = picks[dls_inputs.choose(len(picks), n_units, seed + 1000)]
+        pre, _ = oracle.extend(self.n, self.flags, o_order, allb[sub], depth)
+        return o_order, pre
 
 
-def oracle_sample(seed, n_diags, depth=N + AFTER_ROW0, suffix="heuristic"):
-    """The oracle's own order and prefixes for `n_diags` of the run's
-    diagonals, split at `depth`, cells after the split in the given rule."""
-    import oracle
-    from oracle import orders
-    o_order = orders.md_ad_rows(N)
-    if suffix == "heuristic":
-        o_order = orders.heuristic_complete(N, o_order[:depth])
-    ident = np.array([orders.identity(N)], np.uint8)
-    diags, _ = oracle.extend(N, FLAGS, o_order, ident, N + (N - 1))
-    picks = dls_inputs.choose(len(diags), DIAGS, seed)
-    sub = picks[dls_inputs.choose(len(picks), n_diags, seed + 1000)]
-    pre, _ = oracle.extend(N, FLAGS, o_order, diags[sub], depth)
-    return o_order, pre
+class Vsym10Rows2(Dls8Diag64):
+    """Order 10, vertically symmetric, row 0 identity; `units` seed-drawn
+    fillings of rows 1 and 2 out of the 2 153 120 valid ones."""
+    name, n, flags, units, unit_name = "vsym10_rows2", 10, 3, 2000, "rows-1-2 prefixes"
+    default_depth = 19
+    depths = [17, 19, 21, 23]
+    first_rows = 3
+
+    def base_depth(self):
+        return 15
 
 
-def run_oracle(o_order, pre, threads):
+SPECS = {"dls8_diag64": Dls8Diag64(), "vsym10_rows2": Vsym10Rows2()}
+
+
+def run_oracle(spec, o_order, pre, threads):
     import oracle
     t0 = time.perf_counter()
-    counts, nodes = oracle.count_many(N, FLAGS, o_order, pre, threads=threads)
+    counts, nodes = oracle.count_many(spec.n, spec.flags, o_order, pre, threads=threads)
     dt = time.perf_counter() - t0
     return int(counts.sum()), int(nodes.sum()), dt
 
@@ -260,13 +284,14 @@ def reference_arm(args):
     if rank != 0:
         return 0
     threads = os.cpu_count() or 1
-    o_order, pre = oracle_sample(0, 1)
+    spec = SPECS[args.workload]
+    o_order, pre = spec.oracle_sample(0, 1, spec.default_depth, "heuristic")
     for _ in range(args.warmup):
-        run_oracle(o_order, pre, threads)
+        run_oracle(spec, o_order, pre, threads)
     sq = 0
     t = 0.0
     for _ in range(args.steps):
-        c, _, dt = run_oracle(o_order, pre, threads)
+        c, _, dt = run_oracle(spec, o_order, pre, threads)
         sq += c
         t += dt
     value = sq / t
@@ -275,11 +300,13 @@ def reference_arm(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": N, "sample": "1 of the 64 diagonals per step",
+        "config": {"workload": spec.name, "n": spec.n,
+                   "sample": "1 of the %d %s per step" % (spec.units, spec.unit_name),
                    "prefixes_per_step": int(len(pre))},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": "all %d prefixes of 1 seed-chosen diagonal of the 64"
-                                   % len(pre)},
+                         "sample": "all %d prefixes of 1 seed-chosen base prefix of the %d, "
+                                   "cells after the split in the Section 2.3 order"
+                                   % (len(pre), spec.units)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -302,25 +329,28 @@ def main():
     stream = torch.cuda.Stream()
 
     from paper_1709_02599_gb300 import autotune
+    spec = SPECS[args.workload]
+    N, FLAGS = spec.n, spec.flags
+    units = args.diagonals or spec.units
     seed = rank
-    order0, base, picks = product_base(dls, seed, args.diagonals)
+    order0, base = spec.product_base(dls, seed, units)
     fixed = json.loads(args.launch) if args.launch else None
     tuned = None
     if args.no_autotune:
-        depth_sel, suffix_sel, cfg = N + AFTER_ROW0, args.suffix or "given", fixed or {}
+        depth_sel, suffix_sel, cfg = spec.default_depth, args.suffix or "given", fixed or {}
     else:
         t0 = time.perf_counter()
         suffixes = (args.suffix,) if args.suffix else ("given", "heuristic")
         shapes = [{}] if fixed is not None else None
-        best = autotune.tune(N, FLAGS, order0, base, [N + 14, N + 17, N + 20, N + 23],
-                             suffixes=suffixes, shapes=shapes)
+        best = autotune.tune(N, FLAGS, order0, base, spec.depths, suffixes=suffixes,
+                             shapes=shapes)
         depth_sel, suffix_sel = best["depth"], best["suffix"]
         cfg = fixed if fixed is not None else best["launch"]
         tuned = {"trials": len(best["trials"]), "cached": best["cached"],
                  "seconds": round(time.perf_counter() - t0, 2),
-                 "candidates": "split 14/17/20/23 cells past row 0 x suffix order "
-                               "{given, heuristic}, then %d launch shapes" % (
-                                   len(shapes or autotune.SHAPES) - 1)}
+                 "candidates": "split depth %s x order after the split {given, heuristic}, "
+                               "then %d launch shapes" % (spec.depths,
+                                                          len(shapes or autotune.SHAPES) - 1)}
     order, pre, par = autotune.build_problem(N, FLAGS, order0, base, depth_sel, suffix_sel)
     P, depth = pre.shape
     d_pre = torch.from_numpy(pre).to("cuda")
@@ -409,11 +439,11 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * step_s, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": WORKLOAD if args.diagonals == DIAGS else
-                   "%s (profiling case: %d diagonals)" % (WORKLOAD, args.diagonals),
-                   "n": N, "flags": "diagonal", "row0": "identity",
-                   "diagonal_fillings": args.diagonals, "seed": "rank",
-                   "split_after_row0": int(depth_sel - N), "suffix_order": suffix_sel,
+        "config": {"workload": spec.name if units == spec.units else
+                   "%s (profiling case: %d %s)" % (spec.name, units, spec.unit_name),
+                   "n": N, "flags": "diagonal" + (", vertically symmetric" if FLAGS & 2 else ""),
+                   "row0": "identity", spec.unit_name.replace(" ", "_"): units, "seed": "rank",
+                   "split_depth": int(depth_sel), "suffix_order": suffix_sel,
                    "prefixes": int(P), "squares_per_step": squares, "nodes_per_step": nodes,
                    "kernel": "k_persistent (CUDA graph)", "launch": cfg, "autotune": tuned,
                    "l2": "flushed: 256 MiB write between timed steps"},
@@ -432,13 +462,14 @@ def main():
     }
     if rank == 0 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
-        o_order, opre = oracle_sample(seed, 2, depth_sel, suffix_sel)
-        c, _, dt = run_oracle(o_order, opre, threads)
+        o_order, opre = spec.oracle_sample(seed, 2, depth_sel, suffix_sel)
+        c, _, dt = run_oracle(spec, o_order, opre, threads)
         line["cpu_baseline"] = {"value": c / dt, "unit": UNIT, "cores": threads,
                                 "kind": "oracle",
-                                "sample": "all %d prefixes of 2 seed-chosen diagonals of the 64, "
+                                "sample": "all %d prefixes of 2 seed-chosen %s of the %d, "
                                           "same split and fill order as the GPU run "
-                                          "(%d squares, %.1f s)" % (len(opre), c, dt)}
+                                          "(%d squares, %.1f s)" % (len(opre), spec.unit_name,
+                                                                   units, c, dt)}
     plan.close()
     if rank == 0 and args.serve_jobs > 0:
         line["serving"] = serving_leg(args.serve_jobs, args.serve_limit)

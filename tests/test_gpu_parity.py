@@ -169,8 +169,13 @@ def test_config4_vsym10_smallest_against_oracle(dls):
     c2 = _gpu_counts(dls, 10, D | V, wl.order, wl.prefixes, plain=True)
     assert (c2 == c).all()
     idx = np.argsort(c, kind="stable")[:20]
+    # the oracle splits each checked prefix a few cells deeper so that all
+    # host threads stay busy, and sums the parts per prefix
     o_fast = orders.heuristic_complete(10, wl.oracle_order[:wl.depth], True, True)
-    ref, _ = oracle.count_many(10, D | V, o_fast, wl.oracle_prefixes[idx], threads=THREADS)
+    sub, par = oracle.extend(10, D | V, o_fast, wl.oracle_prefixes[idx], wl.depth + 4)
+    part, _ = oracle.count_many(10, D | V, o_fast, sub, threads=THREADS)
+    ref = np.zeros(len(idx), np.uint64)
+    np.add.at(ref, par, part)
     assert (c[idx] == ref).all()
 
 
