@@ -47,6 +47,11 @@ DIAGS, AFTER_ROW0 = 64, 20
 OPS_PER_NODE = 11
 ISSUE_LANES_PER_SM = 4 * 32      # 4 schedulers x 32 lanes, one instruction/clk
 L2_FLUSH_BYTES = 256 << 20
+# DRAM bytes (read + write) per prefix of k_snapshot<0,0> on the order-8
+# workload: one ncu capture of 16 of the 64 diagonals (273 038 prefixes,
+# 9.84 MB read, 0 written while the kernel ran), scaled per prefix; the
+# profile summary under profiles/ gives the command
+TRAFFIC_PER_PREFIX = {("dls8_diag64", "k_snapshot"): 9.843456e6 / 273038}
 
 
 def parse():
@@ -359,6 +364,7 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     launch = dls.Launch(**cfg)
     plan = dls.Plan(N, FLAGS, order, d_pre, counts, total, launch)
+    run = dls.describe_launch(N, FLAGS, order, depth, P, launch)
 
     # node count of the workload (separately compiled counting variant,
     # untimed) and the exact square count
@@ -410,7 +416,7 @@ def main():
             raise RuntimeError("plain launch count differs")
         p_step = sum(pt) / len(pt)
         plain = {"value": squares / p_step, "unit": UNIT, "ms_per_step": 1e3 * p_step,
-                 "kernel": "k_plain", "speedup_of_persistent": p_step / step_s}
+                 "kernel": "k_plain", "speedup_of_batched": p_step / step_s}
         pplan.close()
 
     # end to end through the host-buffer entry point
@@ -445,7 +451,8 @@ def main():
                    "row0": "identity", spec.unit_name.replace(" ", "_"): units, "seed": "rank",
                    "split_depth": int(depth_sel), "suffix_order": suffix_sel,
                    "prefixes": int(P), "squares_per_step": squares, "nodes_per_step": nodes,
-                   "kernel": "k_persistent (CUDA graph)", "launch": cfg, "autotune": tuned,
+                   "kernel": run["kernel"] + " (CUDA graph)", "launch": cfg, "resolved": run,
+                   "autotune": tuned,
                    "l2": "flushed: 256 MiB write between timed steps"},
         "plain": plain,
         "e2e": None if e2e_step is None else {
@@ -453,7 +460,10 @@ def main():
             "unit": UNIT, "h2d_bytes_per_step": int(P * depth),
             "d2h_bytes_per_step": int(P * 8), "entry": "dls_count_host"},
         "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops,
-                     "unit": "Tops/s", "frac": achieved_tops / peak_tops, "traffic": None,
+                     "unit": "Tops/s", "frac": achieved_tops / peak_tops,
+                     "traffic": (TRAFFIC_PER_PREFIX[(spec.name, run["kernel"])] * P
+                                 if (spec.name, run["kernel"]) in TRAFFIC_PER_PREFIX else None),
+                     "algorithmic_bytes": int(P * (depth + 8)),
                      "ops_per_node": OPS_PER_NODE,
                      "peak_from": "%d SMs x 4 schedulers x 32 lanes x %.0f MHz" % (sms, sm_max_mhz)},
         "gpu_launches": args.steps,

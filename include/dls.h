@@ -68,7 +68,9 @@ typedef enum {
     DLS_ERR_TIMEOUT = 6,      /* a bounded wait or budget ran out            */
     DLS_ERR_ABORTED = 7,      /* stopped through dls_server_abort()          */
     DLS_ERR_NO_MEMORY = 8,    /* host or device allocation failed            */
-    DLS_ERR_BAD_STATE = 9     /* object used after release / wrong sequence  */
+    DLS_ERR_BAD_STATE = 9,    /* object used after release / wrong sequence  */
+    DLS_ERR_INTERNAL = 10     /* a kernel met a state its bounds exclude
+                                 (its counts are not to be trusted)          */
 } dls_status;
 
 /* kinds of fill order for dls_fill_order() */
@@ -191,7 +193,44 @@ typedef struct {
                              n <= 10 with DLS_VSYM), else shared memory;
                              1 = shared memory; 2 = registers (BAD_ARG if
                              they do not fit)                                */
+    int stack;            /* persistent only: the search's stack --
+                             1 = one entry per order position (Algorithm 4's
+                             L and LS per cell; backing out of a cell is one
+                             step);
+                             2 = snapshots: an entry (the line words, the
+                             position and its untried candidates) only where
+                             candidates remain after the one placed, so a
+                             dead end returns to the deepest open cell in one
+                             step; register words and one lane per prefix
+                             only (BAD_ARG otherwise); entries per lane =
+                             positions after the prefix whose cell is not
+                             forced by a line with all other cells earlier;
+                             0 = snapshots where they apply (default)        */
 } dls_launch_t;
+
+/* What a dls_count_ex call with this shape runs. */
+typedef enum {
+    DLS_RUN_PERSISTENT = 0, /* persistent grid, one stack entry per position */
+    DLS_RUN_PLAIN = 1,      /* one thread per work item                      */
+    DLS_RUN_SNAPSHOT = 2    /* persistent grid, snapshot stack               */
+} dls_run_kind;
+
+typedef struct {
+    int run;              /* dls_run_kind                                    */
+    int words;            /* 1 = row/column words in shared memory,
+                             2 = in registers                                */
+    int block_threads;
+    int grid_blocks;      /* 0 = nothing to launch                           */
+    int smem_bytes;       /* dynamic shared memory per block                 */
+    int stack_entries;    /* snapshot entries per lane (0 otherwise)         */
+} dls_launch_info;
+
+/* Resolves the kernel and launch shape that dls_count_ex would use for these
+ * arguments (same validation and errors), without enqueueing anything.
+ * Queries the current CUDA device (occupancy).  out: HOST, caller-owned. */
+int dls_describe_launch(int n, uint32_t flags, const uint8_t *order,
+                        int order_len, int depth, int64_t n_prefixes,
+                        const dls_launch_t *cfg, dls_launch_info *out);
 
 /* Count completions of every prefix on the GPU (Algorithm 4 on the device).
  * d_prefixes: DEVICE, n_prefixes * depth bytes (caller-owned).
@@ -234,7 +273,9 @@ int dls_count_ex(int n, uint32_t flags, const uint8_t *order, int order_len,
  * counts -- multiply by dls_multiplier() for whole-square totals).
  * Synchronous: returns after the copies back have landed.  The device
  * buffers come from a per-(device, stream) area that grows on demand and
- * lives until dls_release(). */
+ * lives until dls_release().  Also returns DLS_ERR_INTERNAL if the snapshot
+ * search reported a stack overflow (excluded by its entry bound; the kernel
+ * drops the entry rather than write past its stack). */
 int dls_count_host(int n, uint32_t flags, const uint8_t *order,
                    int order_len, const uint8_t *h_prefixes, int depth,
                    int64_t n_prefixes, uint64_t *h_counts,

@@ -33,11 +33,12 @@ class Launch:
     donate: int = 0
     check_every: int = 0
     words: int = 0
+    stack: int = 0
 
     def c(self):
         return _lib.LaunchT(self.kernel, self.block_threads, self.blocks_per_sm,
                             self.lanes_per_prefix, self.split_pos, self.donate,
-                            self.check_every, self.words)
+                            self.check_every, self.words, self.stack)
 
 
 def lib():
@@ -134,6 +135,23 @@ def _stream_handle(stream):
 
 def _dev_ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def describe_launch(n, flags, order, depth, n_prefixes, launch=None):
+    """The kernel and launch shape dls_count_ex would use (dls_describe_launch):
+    a dict with 'kernel' (k_snapshot / k_persistent / k_plain), 'words'
+    ('registers' or 'shared'), 'block_threads', 'grid_blocks', 'smem_bytes',
+    'stack_entries'."""
+    o, op, ol = _order(order)
+    cfg = (launch or Launch()).c()
+    info = _lib.LaunchInfo()
+    _lib.check(lib().dls_describe_launch(n, flags, op, ol, depth, n_prefixes,
+                                         ctypes.byref(cfg), ctypes.byref(info)),
+               "dls_describe_launch")
+    return {"kernel": _lib.RUN_NAMES[info.run],
+            "words": "registers" if info.words == 2 else "shared",
+            "block_threads": info.block_threads, "grid_blocks": info.grid_blocks,
+            "smem_bytes": info.smem_bytes, "stack_entries": info.stack_entries}
 
 
 def count(n, flags, order, prefixes, counts=None, total=None, nodes=None, launch=None,

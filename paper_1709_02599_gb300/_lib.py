@@ -18,6 +18,11 @@ ORDER_HEURISTIC = 3
 KERNEL_PERSISTENT = 0
 KERNEL_PLAIN = 1
 
+RUN_PERSISTENT = 0
+RUN_PLAIN = 1
+RUN_SNAPSHOT = 2
+RUN_NAMES = {RUN_PERSISTENT: "k_persistent", RUN_PLAIN: "k_plain", RUN_SNAPSHOT: "k_snapshot"}
+
 OK = 0
 ERR_CAPACITY = 4
 
@@ -43,7 +48,17 @@ class LaunchT(ctypes.Structure):
                 ("split_pos", ctypes.c_int),
                 ("donate", ctypes.c_int),
                 ("check_every", ctypes.c_int),
-                ("words", ctypes.c_int)]
+                ("words", ctypes.c_int),
+                ("stack", ctypes.c_int)]
+
+
+class LaunchInfo(ctypes.Structure):
+    _fields_ = [("run", ctypes.c_int),
+                ("words", ctypes.c_int),
+                ("block_threads", ctypes.c_int),
+                ("grid_blocks", ctypes.c_int),
+                ("smem_bytes", ctypes.c_int),
+                ("stack_entries", ctypes.c_int)]
 
 
 class ServerCfg(ctypes.Structure):
@@ -108,6 +123,8 @@ def load():
                                     vp]),
         "dls_count_ex": (c_int, [c_int, c_u32, u8p, c_int, vp, c_int, c_i64, vp, vp, vp,
                                  ctypes.POINTER(LaunchT), vp]),
+        "dls_describe_launch": (c_int, [c_int, c_u32, u8p, c_int, c_int, c_i64,
+                                        ctypes.POINTER(LaunchT), ctypes.POINTER(LaunchInfo)]),
         "dls_count_host": (c_int, [c_int, c_u32, u8p, c_int, vp, c_int, c_i64, vp,
                                    ctypes.POINTER(U128), ctypes.POINTER(LaunchT), vp]),
         "dls_count_host_noalloc": (c_int, [c_int, c_u32, u8p, c_int, vp, c_int, c_i64, vp,

@@ -25,13 +25,14 @@ from . import (Launch, Plan, ORDER_HEURISTIC, ORDER_MD_AD_ROWS, KERNEL_PERSISTEN
 SUFFIXES = {"given": None, "heuristic": ORDER_HEURISTIC}
 SHAPES = [
     {},
-    {"words": 1},
+    {"block_threads": 64},
     {"block_threads": 256},
+    {"check_every": 16},
+    {"stack": 1},
+    {"words": 1},
     {"words": 1, "block_threads": 256},
     {"lanes_per_prefix": 2},
     {"words": 1, "lanes_per_prefix": 2},
-    {"check_every": 16},
-    {"words": 1, "block_threads": 64},
 ]
 _CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 

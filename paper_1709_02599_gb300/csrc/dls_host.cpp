@@ -253,13 +253,14 @@ const char *dls_strerror(int code) {
     case DLS_ERR_ABORTED: return "aborted";
     case DLS_ERR_NO_MEMORY: return "out of memory";
     case DLS_ERR_BAD_STATE: return "object in the wrong state";
+    case DLS_ERR_INTERNAL: return "a kernel exceeded a bound it relies on";
     default: return "unknown status";
   }
 }
 
 const char *dls_last_cuda_error(void) { return g_last_cuda_error.c_str(); }
 
-int dls_version(void) { return (1 << 16) | 0; }
+int dls_version(void) { return (1 << 16) | 1; }
 
 int dls_fill_order(int n, uint32_t flags, int kind, int first_rows,
                    uint8_t *ij_out, int cap, int *len_out) {

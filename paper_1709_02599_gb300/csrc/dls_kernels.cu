@@ -15,6 +15,10 @@
 //                   atomic queue as lanes go idle, and once the queue is empty
 //                   idle lanes take the shallowest untried subtree of a busy
 //                   lane in the same warp (ballot + shuffle + shared memory).
+//   k_snapshot   -- the same grid, queue and donation with the search of
+//                   dls_snapshot.cuh: register words and a stack of state
+//                   snapshots kept only where candidates remain, so that a
+//                   dead end returns to the deepest open cell in one step.
 //   Both keep per-lane totals, reduce them per block in shared memory and add
 //   one 64-bit atomic per block to the global total.
 //
@@ -34,6 +38,7 @@
 
 #include "dls_internal.h"
 #include "dls_search.cuh"
+#include "dls_snapshot.cuh"
 
 namespace dls {
 
@@ -51,7 +56,8 @@ struct KParams {
   unsigned long long *counts;
   unsigned long long *total;
   unsigned long long *nodes;
-  unsigned long long *queue;
+  unsigned long long *queue;  // [0] queue head, [1] stack overflow flag
+  int snap_cap;               // snapshot stack entries per lane
   uint8_t ci[DLS_MAX_CELLS];
   uint8_t cj[DLS_MAX_CELLS];
 };
@@ -67,7 +73,7 @@ __device__ bool load_item(Lane<REG> &s, const KParams &p, long long item,
   s.cnt = 0ull;
   s.splitc = 0u;
   s.w.clear(2 * g.n, B);
-  if (!place_prefix<REG, VSYM>(s, g, p.prefixes + (size_t)s.prefix * (size_t)g.depth, tbl))
+  if (!place_prefix<REG, VSYM>(s.w, g, p.prefixes + (size_t)s.prefix * (size_t)g.depth, tbl))
     return true;
   if (g.depth == p.order_len) {
     s.cnt = (s.sub == 0u) ? 1ull : 0ull;
@@ -333,6 +339,169 @@ __global__ void __launch_bounds__(512)
   if (NODES) block_reduce_add(s.nodes, p.nodes, red);
 }
 
+// ---------------------------------------------------- snapshot search --
+
+// Load work item (= prefix) `item` into a snapshot lane.  Returns true if it
+// is already finished (invalid prefix, or nothing left to search).
+template <bool VSYM, bool NODES>
+__device__ bool snap_load(SnapLane &s, const KParams &p, long long item, const Cell *tbl,
+                          const SnapTable &tb) {
+  const Geo &g = p.g;
+  s.prefix = item;
+  s.cnt = 0ull;
+  s.sp = s.bot = 0;
+  s.w.clear(0, 0u);
+  if (!place_prefix<true, VSYM>(s.w, g, p.prefixes + (size_t)item * (size_t)g.depth, tbl))
+    return true;
+  if (g.depth == p.order_len) {
+    s.cnt = 1ull;
+    return true;
+  }
+  const uint32_t L = s.w.template cands<VSYM>(tbl[g.depth], g);
+  if (g.depth == g.last) {
+    s.cnt = (unsigned)__popc(L);
+    if (NODES) s.nodes += (unsigned)__popc(L);
+    return true;
+  }
+  s.p = g.depth;
+  s.L = L;
+  s.sh = tb.sh[g.depth];
+  s.dm = tb.dm[g.depth];
+  return L == 0u;
+}
+
+// In-warp work donation for snapshot lanes: each idle lane is paired with a
+// busy lane that holds a stack entry; it takes the busy lane's bottom entry
+// (the shallowest open cell: the largest untried subtree) and the busy lane
+// drops it by raising its bottom index.
+template <bool VSYM>
+__device__ void snap_donate(SnapLane &s, bool &busy, const KParams &p, const SnapStack &st,
+                            const SnapTable &tb, int lane, unsigned B) {
+  const unsigned idle = __ballot_sync(FULL, !busy);
+  if (idle == 0u || idle == FULL) return;
+  const unsigned donors = __ballot_sync(FULL, busy && s.sp > s.bot);
+  if (donors == 0u) return;
+  const int pairs = min(__popc(idle), __popc(donors));
+  const unsigned below = (1u << lane) - 1u;
+  int partner = lane;
+  bool receiver = false, giver = false;
+  if (!busy) {
+    const int r = __popc(idle & below);
+    if (r < pairs) {
+      partner = nth_set_bit(donors, r);
+      receiver = true;
+    }
+  } else if ((donors >> lane) & 1u) {
+    giver = __popc(donors & below) < pairs;
+  }
+  const int d_bot = __shfl_sync(FULL, s.bot, partner);
+  const long long d_prefix = __shfl_sync(FULL, s.prefix, partner);
+  if (receiver) {
+    const int off = d_bot * (int)B + (partner - lane);
+    const uint4 a = st.sa[off];
+    const uint32_t wv = st.sw[off];
+    s.w.R = ((unsigned long long)a.y << 32) | a.x;
+    s.w.C = ((unsigned long long)a.w << 32) | a.z;
+    snap_unpack<VSYM>(wv, p.g.n, s.w.dg, s.p, s.L);
+    s.sh = tb.sh[s.p];
+    s.dm = tb.dm[s.p];
+    s.sp = s.bot = 0;
+    s.prefix = d_prefix;
+    s.cnt = 0ull;
+    busy = true;
+  }
+  __syncwarp();
+  if (giver) s.bot++;
+}
+
+// Shared memory: [cell table: 8 bytes per position, rounded to 32 positions]
+//                [position table: 16 + 8 bytes per position, same rounding]
+//                [stack: (cap + 1) * B entries of 16 bytes, then as many of 4]
+template <bool VSYM, bool NODES>
+__global__ void __launch_bounds__(512)
+    k_snapshot(const __grid_constant__ KParams p, int diag) {
+  extern __shared__ uint32_t smem[];
+  __shared__ unsigned long long red[16];
+  const unsigned B = blockDim.x;
+  const int lane = threadIdx.x & 31;
+  const int rows = (p.order_len + 31) & ~31;
+  Cell *t = reinterpret_cast<Cell *>(smem);
+  uint4 *tsh = reinterpret_cast<uint4 *>(smem + 2 * rows);
+  uint2 *tdm = reinterpret_cast<uint2 *>(tsh + rows);
+  for (int idx = threadIdx.x; idx < p.order_len; idx += B) {
+    t[idx] = describe_regs(p.ci[idx], p.cj[idx], p.g.n, diag != 0, p.wr, p.wc);
+    const int nx = min(idx + 1, p.order_len - 1);
+    snap_row(p.g.n, diag != 0, p.wr, p.wc, p.ci[idx], p.cj[idx], p.ci[nx], p.cj[nx], tsh[idx],
+             tdm[idx]);
+  }
+  uint4 *sa0 = reinterpret_cast<uint4 *>(tdm + rows);
+  SnapStack st;
+  st.sa = sa0 + threadIdx.x;
+  st.sw = reinterpret_cast<uint32_t *>(sa0 + (size_t)(p.snap_cap + 1) * B) + threadIdx.x;
+  st.cap = p.snap_cap;
+  const Cell *tbl = t;
+  const SnapTable tb = {tsh, tdm};
+  uint32_t ovf = 0u;
+  SnapLane s;
+  s.w.tb = nullptr;
+  s.w.R = s.w.C = 0ull;
+  s.w.dg = 0u;
+  s.p = 0;
+  s.L = 0u;
+  s.sh = make_uint4(0u, 0u, 0u, 0u);
+  s.dm = make_uint2(0u, 0u);
+  s.sp = s.bot = 0;
+  s.prefix = 0;
+  s.cnt = 0ull;
+  s.nodes = 0ull;
+  __syncthreads();
+
+  unsigned long long lane_total = 0ull;
+  bool busy = false;
+  bool qdone = false;
+  for (;;) {
+    unsigned idle = __ballot_sync(FULL, !busy);
+    while (idle != 0u && !qdone) {
+      const int nidle = __popc(idle);
+      unsigned long long base = 0ull;
+      if (lane == 0) base = atomicAdd(p.queue, (unsigned long long)nidle);
+      base = __shfl_sync(FULL, base, 0);
+      if (!busy) {
+        const long long item = (long long)base + __popc(idle & ((1u << lane) - 1u));
+        if (item < p.n_items) {
+          busy = !snap_load<VSYM, NODES>(s, p, item, tbl, tb);
+          if (!busy) flush_count(s.prefix, s.cnt, p, lane_total);
+        }
+      }
+      if ((long long)(base + (unsigned long long)nidle) >= p.n_items) qdone = true;
+      idle = __ballot_sync(FULL, !busy);
+    }
+    if (idle == FULL) break;  // queue drained and every lane idle
+    if (!qdone) {
+      // every lane is busy here: step until one finishes
+      bool fin;
+      do {
+        fin = snap_step<VSYM, NODES>(s, p.g, st, tb, B, ovf);
+      } while (!__any_sync(FULL, fin));
+      if (fin) {
+        busy = false;
+        flush_count(s.prefix, s.cnt, p, lane_total);
+      }
+    } else {
+      for (int it = 0; it <= p.check_mask; ++it) {
+        if (busy && snap_step<VSYM, NODES>(s, p.g, st, tb, B, ovf)) {
+          busy = false;
+          flush_count(s.prefix, s.cnt, p, lane_total);
+        }
+      }
+      if (p.donate) snap_donate<VSYM>(s, busy, p, st, tb, lane, B);
+    }
+  }
+  if (ovf) *reinterpret_cast<int *>(p.queue + 1) = 1;
+  block_reduce_add(lane_total, p.total, red);
+  if (NODES) block_reduce_add(s.nodes, p.nodes, red);
+}
+
 // ------------------------------------------------------------ host side --
 
 struct Workspace {
@@ -412,6 +581,7 @@ struct Shape {
   int donate;
   int check_mask;
   int words;  // 0 auto, 1 shared memory, 2 registers
+  int stack;  // 0 auto, 1 one entry per position, 2 snapshots
 };
 
 static int resolve_shape(const dls_launch_t *cfg, int depth, int last,
@@ -444,7 +614,43 @@ static int resolve_shape(const dls_launch_t *cfg, int depth, int last,
   sh->check_mask = every - 1;
   sh->words = c.words;
   if (sh->words < 0 || sh->words > 2) return DLS_ERR_BAD_ARG;
+  sh->stack = c.stack;
+  if (sh->stack < 0 || sh->stack > 2) return DLS_ERR_BAD_ARG;
   return DLS_OK;
+}
+
+// Entries a snapshot stack needs: the order positions from depth to the one
+// before the last whose cell can have two or more candidates.  A cell on a
+// line that has all its other cells earlier in the order has at most one
+// (the value the line misses), and entries are only made where a candidate
+// remains after the one placed, at strictly increasing positions of a path.
+// Lines: rows, columns and, with DLS_DIAGONAL, the two diagonals; with
+// DLS_VSYM (left-half cells) a row holds n/2 cells whose last one still has
+// a value pair to choose from, so only the columns (n cells each) and the
+// diagonal line -- the left cell of each row on either diagonal, n cells
+// that fix the n values of the main diagonal -- force a cell.
+static int snapshot_entries(const OrderInfo &info, int n, uint32_t flags, int depth) {
+  const bool diag = (flags & DLS_DIAGONAL) != 0, vsym = (flags & DLS_VSYM) != 0;
+  int rowc[DLS_MAX_N] = {0}, colc[DLS_MAX_N] = {0};
+  int mdc = 0, adc = 0, dline = 0;
+  int cap = 0;
+  for (int t = 0; t + 1 < info.len; ++t) {
+    const int i = info.i[t], j = info.j[t];
+    const bool md = diag && i == j, ad = diag && i + j == n - 1;
+    bool forced;
+    if (vsym)
+      forced = colc[j] == n - 1 || ((md || ad) && dline == n - 1);
+    else
+      forced = rowc[i] == n - 1 || colc[j] == n - 1 || (md && mdc == n - 1) ||
+               (ad && adc == n - 1);
+    if (t >= depth && !forced) ++cap;
+    ++rowc[i];
+    ++colc[j];
+    mdc += md ? 1 : 0;
+    adc += ad ? 1 : 0;
+    dline += (md || ad) ? 1 : 0;
+  }
+  return cap;
 }
 
 template <bool REG, bool VSYM, bool NODES, bool SPLIT>
@@ -469,6 +675,11 @@ static const void *pick_kernel(int kind, bool reg, bool vsym, bool nodes, bool s
   return reg ? pick2<true>(kind, vsym, nodes, split) : pick2<false>(kind, vsym, nodes, split);
 }
 
+static const void *pick_snapshot(bool vsym, bool nodes) {
+  if (vsym) return nodes ? (const void *)k_snapshot<true, true> : (const void *)k_snapshot<true, false>;
+  return nodes ? (const void *)k_snapshot<false, true> : (const void *)k_snapshot<false, false>;
+}
+
 // Do all row words and all column words fit one 64-bit register each?
 // Field widths: 8 bits per row and column for n <= 8; with vertical
 // symmetry n/2 bits per row (value pairs) and n bits per left column.
@@ -491,42 +702,43 @@ static size_t smem_bytes(int order_len, int n, int depth, int last, int block,
   return (size_t)((order_len + 31) & ~31) * 8u + (size_t)((reg ? 0 : 2 * n) + stack) * block * 4u;
 }
 
-// Validates, fills the parameter block and enqueues the whole pass on
-// `stream`: zero the outputs, reset the queue, launch.
-static int enqueue_count(int n, uint32_t flags, const uint8_t *order,
-                         int order_len, const uint8_t *d_prefixes, int depth,
-                         int64_t n_prefixes, uint64_t *d_counts,
-                         uint64_t *d_total, uint64_t *d_nodes,
-                         const dls_launch_t *cfg, cudaStream_t stream,
-                         unsigned long long *scratch = nullptr) {
+// Snapshot kernel: the cell table and the position table (8 + 24 bytes per
+// position), then 20 bytes per entry and lane, one spare entry included.
+static size_t smem_bytes_snapshot(int order_len, int entries, int block) {
+  return (size_t)((order_len + 31) & ~31) * 32u + (size_t)(entries + 1) * block * 20u;
+}
+
+// A resolved launch: the parameter block, the kernel and its shape.
+struct Prepared {
+  KParams kp;
+  const void *fn = nullptr;
+  int run = DLS_RUN_PERSISTENT;  // dls_run_kind
+  int diag = 0;
+  bool reg = false;
+  int block = 0;
+  unsigned grid = 0;  // 0 = nothing to launch
+  size_t smem = 0;
+  bool store = false;
+};
+
+// Validates the arguments and resolves the kernel and its launch shape
+// (no device work).  grid stays 0 when there is nothing to launch (no
+// prefixes, or odd vertically symmetric orders whose counts are all 0).
+static int prepare_launch(int n, uint32_t flags, const uint8_t *order, int order_len,
+                          const uint8_t *d_prefixes, int depth, int64_t n_prefixes,
+                          uint64_t *d_counts, uint64_t *d_total, uint64_t *d_nodes,
+                          const dls_launch_t *cfg, Prepared *pr) {
   OrderInfo info;
   int rc = validate_order(n, flags, order, order_len, &info);
   if (rc) return rc;
   if (depth < 0 || depth > order_len || n_prefixes < 0) return DLS_ERR_BAD_ARG;
-  if (n_prefixes > 0 && d_counts == nullptr && d_total == nullptr) return DLS_ERR_BAD_ARG;
-  if (n_prefixes > 0 && depth > 0 && d_prefixes == nullptr) return DLS_ERR_BAD_ARG;
   Shape sh;
   rc = resolve_shape(cfg, depth, order_len - 1, &sh);
   if (rc) return rc;
-
-  cudaError_t e;
-  if (d_total) {
-    e = cudaMemsetAsync(d_total, 0, sizeof(uint64_t), stream);
-    if (e != cudaSuccess) return cuda_fail(e);
-  }
-  if (d_nodes) {
-    e = cudaMemsetAsync(d_nodes, 0, sizeof(uint64_t), stream);
-    if (e != cudaSuccess) return cuda_fail(e);
-  }
   const bool zero_all = vsym_all_zero(n, flags);
-  const bool store = sh.kernel == DLS_KERNEL_PLAIN && sh.lanes_log2 == 0;
-  if (d_counts && n_prefixes > 0 && (!store || zero_all)) {
-    e = cudaMemsetAsync(d_counts, 0, (size_t)n_prefixes * sizeof(uint64_t), stream);
-    if (e != cudaSuccess) return cuda_fail(e);
-  }
-  if (n_prefixes == 0 || zero_all) return DLS_OK;
+  pr->store = sh.kernel == DLS_KERNEL_PLAIN && sh.lanes_log2 == 0;
 
-  KParams kp;
+  KParams &kp = pr->kp;
   std::memset(&kp, 0, sizeof(kp));
   kp.g.n = n;
   kp.g.all = (1u << n) - 1u;
@@ -538,7 +750,7 @@ static int enqueue_count(int n, uint32_t flags, const uint8_t *order,
   kp.sp.pos = sh.split_pos;
   kp.check_mask = sh.check_mask;
   kp.donate = sh.donate;
-  kp.count_store = store ? 1 : 0;
+  kp.count_store = pr->store ? 1 : 0;
   kp.n_prefixes = n_prefixes;
   kp.n_items = n_prefixes << sh.lanes_log2;
   kp.prefixes = d_prefixes;
@@ -549,7 +761,7 @@ static int enqueue_count(int n, uint32_t flags, const uint8_t *order,
     kp.ci[t] = info.i[t];
     kp.cj[t] = info.j[t];
   }
-  const int diag = (flags & DLS_DIAGONAL) ? 1 : 0;
+  pr->diag = (flags & DLS_DIAGONAL) ? 1 : 0;
   const bool vsym = (flags & DLS_VSYM) != 0;
   int wr = 0, wc = 0;
   bool reg = words_fit_registers(n, vsym, &wr, &wc);
@@ -557,50 +769,108 @@ static int enqueue_count(int n, uint32_t flags, const uint8_t *order,
   if (sh.words == 2 && !reg) return DLS_ERR_BAD_ARG;
   kp.wr = wr;
   kp.wc = wc;
-  const void *fn = pick_kernel(sh.kernel, reg, vsym, d_nodes != nullptr, sh.lanes_log2 > 0);
+  // the snapshot search: persistent grid, register words, one lane per
+  // prefix; order positions must fit its packed entry
+  const bool snap_ok = sh.kernel == DLS_KERNEL_PERSISTENT && reg && sh.lanes_log2 == 0 &&
+                       order_len <= (vsym ? 64 : 256);
+  if (sh.stack == 2 && !snap_ok) return DLS_ERR_BAD_ARG;
+  bool snap = snap_ok && sh.stack != 1;
+  kp.snap_cap = snap ? std::max(1, snapshot_entries(info, n, flags, depth)) : 0;
   DevInfo di;
   rc = dev_info(&di);
   if (rc) return rc;
   // static shared memory of the kernels: the 16-entry reduction buffer
   const size_t static_smem = 16 * sizeof(unsigned long long);
-  size_t smem = smem_bytes(order_len, n, depth, order_len - 1, sh.block, reg);
   const bool default_block = cfg == nullptr || cfg->block_threads == 0;
+  // by default, an explicit block size whose snapshot stacks do not fit
+  // falls back to the per-position stack (a fifth of the bytes per entry)
+  if (snap && sh.stack == 0 && !default_block &&
+      smem_bytes_snapshot(order_len, kp.snap_cap, sh.block) + static_smem > di.smem_optin) {
+    snap = false;
+    kp.snap_cap = 0;
+  }
+  pr->reg = reg;
+  pr->run = snap ? DLS_RUN_SNAPSHOT
+                 : (sh.kernel == DLS_KERNEL_PLAIN ? DLS_RUN_PLAIN : DLS_RUN_PERSISTENT);
+  pr->fn = snap ? pick_snapshot(vsym, d_nodes != nullptr)
+                : pick_kernel(sh.kernel, reg, vsym, d_nodes != nullptr, sh.lanes_log2 > 0);
+  auto smem_for = [&](int block) {
+    return snap ? smem_bytes_snapshot(order_len, kp.snap_cap, block)
+                : smem_bytes(order_len, n, depth, order_len - 1, block, reg);
+  };
+  size_t smem = smem_for(sh.block);
   while (default_block && smem + static_smem > di.smem_optin && sh.block > 32) {
     sh.block /= 2;
-    smem = smem_bytes(order_len, n, depth, order_len - 1, sh.block, reg);
+    smem = smem_for(sh.block);
   }
   if (smem + static_smem > di.smem_optin) return DLS_ERR_NO_MEMORY;
-  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return cuda_fail(e);
-
-  unsigned grid;
+  pr->block = sh.block;
+  pr->smem = smem;
+  pr->grid = 0;
+  if (n_prefixes == 0 || zero_all) return DLS_OK;
   if (sh.kernel == DLS_KERNEL_PLAIN) {
     long long g = (kp.n_items + sh.block - 1) / sh.block;
     if (g > 0x7fffffffll) return DLS_ERR_BAD_ARG;
-    grid = (unsigned)g;
+    pr->grid = (unsigned)g;
   } else {
-    if (scratch == nullptr) {
-      Workspace *ws = nullptr;
-      rc = get_workspace(stream, &ws);
-      if (rc) return rc;
-      scratch = ws->scratch;
-    }
-    kp.queue = scratch;
-    e = cudaMemsetAsync(scratch, 0, sizeof(unsigned long long), stream);
+    cudaError_t e = cudaFuncSetAttribute(pr->fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return cuda_fail(e);
     int per_sm = sh.blocks_per_sm;
     if (per_sm == 0) {
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, sh.block, smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pr->fn, sh.block, smem);
       if (e != cudaSuccess) return cuda_fail(e);
       if (per_sm < 1) return DLS_ERR_NO_MEMORY;
     }
     long long want = (long long)di.sms * per_sm;
     long long need = (kp.n_items + 31) / 32;  // warps with at least one item
     long long blocks_needed = (need * 32 + sh.block - 1) / sh.block;
-    grid = (unsigned)std::max(1ll, std::min(want, blocks_needed));
+    pr->grid = (unsigned)std::max(1ll, std::min(want, blocks_needed));
   }
-  void *args[] = {&kp, (void *)&diag};
-  e = cudaLaunchKernel(fn, dim3(grid), dim3(sh.block), args, smem, stream);
+  return DLS_OK;
+}
+
+// Validates, fills the parameter block and enqueues the whole pass on
+// `stream`: zero the outputs, reset the queue, launch.
+static int enqueue_count(int n, uint32_t flags, const uint8_t *order,
+                         int order_len, const uint8_t *d_prefixes, int depth,
+                         int64_t n_prefixes, uint64_t *d_counts,
+                         uint64_t *d_total, uint64_t *d_nodes,
+                         const dls_launch_t *cfg, cudaStream_t stream,
+                         unsigned long long *scratch = nullptr) {
+  if (n_prefixes > 0 && d_counts == nullptr && d_total == nullptr) return DLS_ERR_BAD_ARG;
+  if (n_prefixes > 0 && depth > 0 && d_prefixes == nullptr) return DLS_ERR_BAD_ARG;
+  Prepared pr;
+  int rc = prepare_launch(n, flags, order, order_len, d_prefixes, depth, n_prefixes, d_counts,
+                          d_total, d_nodes, cfg, &pr);
+  if (rc) return rc;
+  cudaError_t e;
+  if (d_total) {
+    e = cudaMemsetAsync(d_total, 0, sizeof(uint64_t), stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  if (d_nodes) {
+    e = cudaMemsetAsync(d_nodes, 0, sizeof(uint64_t), stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  if (d_counts && n_prefixes > 0 && (!pr.store || pr.grid == 0)) {
+    e = cudaMemsetAsync(d_counts, 0, (size_t)n_prefixes * sizeof(uint64_t), stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  if (pr.grid == 0) return DLS_OK;
+  if (pr.run != DLS_RUN_PLAIN) {
+    if (scratch == nullptr) {
+      Workspace *ws = nullptr;
+      rc = get_workspace(stream, &ws);
+      if (rc) return rc;
+      scratch = ws->scratch;
+    }
+    pr.kp.queue = scratch;
+    e = cudaMemsetAsync(scratch, 0, 2 * sizeof(unsigned long long), stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  void *args[] = {&pr.kp, (void *)&pr.diag};
+  e = cudaLaunchKernel(pr.fn, dim3(pr.grid), dim3(pr.block), args, pr.smem, stream);
   if (e != cudaSuccess) return cuda_fail(e);
   return DLS_OK;
 }
@@ -630,6 +900,23 @@ int dls_count_ex(int n, uint32_t flags, const uint8_t *order, int order_len,
   return enqueue_count(n, flags, order, order_len, d_prefixes, depth, n_prefixes,
                        d_counts, d_total, d_nodes, cfg,
                        reinterpret_cast<cudaStream_t>(stream));
+}
+
+int dls_describe_launch(int n, uint32_t flags, const uint8_t *order, int order_len,
+                        int depth, int64_t n_prefixes, const dls_launch_t *cfg,
+                        dls_launch_info *out) {
+  if (out == nullptr) return DLS_ERR_BAD_ARG;
+  Prepared pr;
+  int rc = prepare_launch(n, flags, order, order_len, nullptr, depth, n_prefixes, nullptr,
+                          nullptr, nullptr, cfg, &pr);
+  if (rc) return rc;
+  out->run = pr.run;
+  out->words = pr.reg ? 2 : 1;
+  out->block_threads = pr.block;
+  out->grid_blocks = (int)pr.grid;
+  out->smem_bytes = (int)pr.smem;
+  out->stack_entries = pr.kp.snap_cap;
+  return DLS_OK;
 }
 
 int dls_count(int n, uint32_t flags, const uint8_t *order, int order_len,
@@ -699,8 +986,12 @@ int dls_count_host(int n, uint32_t flags, const uint8_t *order,
                         cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) return cuda_fail(e);
   }
+  unsigned long long flag = 0ull;
+  e = cudaMemcpyAsync(&flag, ws->scratch + 1, sizeof(flag), cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return cuda_fail(e);
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e);
+  if (flag) return DLS_ERR_INTERNAL;
   if (total_out) {
     dls_u128 t = {0, 0};
     if (h_counts) {

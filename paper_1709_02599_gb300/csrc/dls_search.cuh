@@ -216,14 +216,14 @@ __device__ __forceinline__ bool dfs_step(Lane<REG> &s, const Geo &g, const Split
 // Place the prefix values rec[0..depth-1] into cleared words.  Returns
 // false if a value is out of range or breaks a constraint (count 0).
 template <bool REG, bool VSYM>
-__device__ __forceinline__ bool place_prefix(Lane<REG> &s, const Geo &g, const uint8_t *rec,
+__device__ __forceinline__ bool place_prefix(Words<REG> &w, const Geo &g, const uint8_t *rec,
                                              const Cell *tbl) {
   for (int t = 0; t < g.depth; ++t) {
     const Cell info = tbl[t];
     const uint32_t val = rec[t];
     const uint32_t b = (val < (uint32_t)g.n) ? (1u << val) : 0u;
-    if ((s.w.template cands<VSYM>(info, g) & b) == 0u) return false;
-    s.w.template toggle<VSYM>(info, b, g);
+    if ((w.template cands<VSYM>(info, g) & b) == 0u) return false;
+    w.template toggle<VSYM>(info, b, g);
   }
   return true;
 }

@@ -96,8 +96,8 @@ __device__ bool sv_load(SvLane &l, const ServeParams &P, uint2 item, unsigned B)
   s.cnt = 0ull;
   s.w.clear(SV_WORDS, B);
   const uint8_t *rec = P.arena + item.y;
-  const bool ok = l.vsym ? place_prefix<false, true>(s, l.g, rec, l.tbl)
-                         : place_prefix<false, false>(s, l.g, rec, l.tbl);
+  const bool ok = l.vsym ? place_prefix<false, true>(s.w, l.g, rec, l.tbl)
+                         : place_prefix<false, false>(s.w, l.g, rec, l.tbl);
   if (!ok) {
     sv_finish(l, P);
     return false;

@@ -1,0 +1,206 @@
+// dls_snapshot.cuh -- the per-lane search of Algorithm 4 with a stack of
+// state snapshots (the batch kernel k_snapshot in dls_kernels.cu).
+//
+// Algorithm 4 keeps, per cell, the untried candidates L[i][j] and the value
+// LS[i][j] placed there; backing out of a cell undoes its placement.  On a
+// GPU lane that costs one loop iteration per cell on the way back, and in an
+// order where most cells are forced (one candidate: Section 2.3 completes
+// lines as soon as they miss one cell) most iterations are such pops.
+//
+// This search keeps a stack entry only for a cell that still has untried
+// candidates after the one being placed, and the entry is the whole line
+// state before that placement (row words R, column words C, diagonal words,
+// position, untried candidates).  A dead end or a counted leaf then returns
+// to the deepest such cell in one step and the following iteration places
+// its next candidate.  Every iteration places one value: iterations = search
+// nodes without the last cell.
+//
+// An iteration reads shared memory twice -- the entry it would return to
+// (issued first, used last) and the position-table row of the position it
+// ends at (two cells' field shifts and diagonal masks, used by the next
+// iteration) -- and writes the entry it would push, every time: the reads
+// and the write are unconditional (the write goes to the first free slot,
+// which a push then keeps), so the step has no branch at all and the lanes
+// of a warp never split.
+//
+// A position whose cell lies on a line (row, column or diagonal) that has
+// all its other cells earlier in the order has at most one candidate, so it
+// never makes an entry.  The number of other positions after the prefix
+// bounds the stack (dls_kernels.cu computes it per order): entries are made
+// at strictly increasing positions along a path.
+//
+// Only register-packed words (Words<true>: n <= 8, or even n <= 10 with
+// vertical symmetry).  An entry is 20 bytes: R and C as one 16-byte word and
+// a 32-bit word packing the diagonal words, the position and the untried
+// candidates; a lane has cap + 1 entry slots.
+#pragma once
+
+#include <cstdint>
+
+#include "dls_search.cuh"
+
+namespace dls {
+
+// 32-bit part of an entry.
+//   plain / diagonal (n <= 8): main diagonal bits 0-7, anti-diagonal bits
+//     16-23 (where the diagonal words keep them), position bits 8-15,
+//     untried candidates bits 24-31;
+//   vertically symmetric (n <= 10, order <= 64 cells): main diagonal bits
+//     0-15 (the anti-diagonal word is its mirror: the mirror of a cell on
+//     one diagonal lies on the other), position bits 16-21, untried
+//     candidates bits 22-31.
+template <bool VSYM>
+__device__ __forceinline__ uint32_t snap_pack(uint32_t dg, int p, uint32_t L) {
+  if (VSYM) return (dg & 0xffffu) | ((uint32_t)p << 16) | (L << 22);
+  return (dg & 0x00ff00ffu) | ((uint32_t)p << 8) | (L << 24);
+}
+
+template <bool VSYM>
+__device__ __forceinline__ void snap_unpack(uint32_t w, int n, uint32_t &dg, int &p,
+                                            uint32_t &L) {
+  if (VSYM) {
+    const uint32_t md = w & 0xffffu;
+    dg = md | (mirror<true>(md, n) << 16);
+    p = (int)((w >> 16) & 63u);
+    L = w >> 22;
+  } else {
+    dg = w & 0x00ff00ffu;
+    p = (int)((w >> 8) & 0xffu);
+    L = w >> 24;
+  }
+}
+
+// Position table, one row per order position p: sh = shifts of the row and
+// column fields of the cells at p and p + 1 (rs_p, cs_p, rs_p+1, cs_p+1),
+// dm = their diagonal masks (as Cell::y).  The row of the last position
+// repeats its own cell as the next one.
+struct SnapTable {
+  const uint4 *sh;
+  const uint2 *dm;
+};
+
+__host__ __device__ inline void snap_row(int n, bool diag, int wr, int wc, int i0, int j0,
+                                         int i1, int j1, uint4 &sh, uint2 &dm) {
+  sh = make_uint4((uint32_t)(i0 * wr), (uint32_t)(j0 * wc), (uint32_t)(i1 * wr),
+                  (uint32_t)(j1 * wc));
+  const Cell c0 = describe_regs(i0, j0, n, diag, wr, wc);
+  const Cell c1 = describe_regs(i1, j1, n, diag, wr, wc);
+  dm = make_uint2(c0.y, c1.y);
+}
+
+// Per-lane state.
+struct SnapLane {
+  Words<true> w;             // line words of the current path
+  int p;                     // position whose candidates L are being tried
+  uint32_t L;                // untried candidates at p
+  uint4 sh;                  // table row of p
+  uint2 dm;
+  int sp;                    // entries [bot, sp) are live; entries below
+  int bot;                   // bot were given to other lanes
+  long long prefix;          // prefix index of the current work
+  unsigned long long cnt;    // completions found for the current work
+  unsigned long long nodes;  // placements made (node counting variant)
+};
+
+// Stack of one lane: entry e at sa[e * B] (line words) and sw[e * B]
+// (packed word), thread-minor so that a warp's accesses are conflict-free
+// whatever entries its lanes are at.
+struct SnapStack {
+  uint4 *sa;
+  uint32_t *sw;
+  int cap;                   // entries per lane
+};
+
+// Admissible values of a cell (fields at shifts rs, cs, diagonal mask m).
+template <bool VSYM>
+__device__ __forceinline__ uint32_t snap_cands(const Words<true> &w, uint32_t rs, uint32_t cs,
+                                               uint32_t m, const Geo &g) {
+  uint32_t r = (uint32_t)(w.R >> rs);
+  if (VSYM) {
+    r &= g.pairmask;
+    r |= mirror<true>(r, g.n);
+  }
+  const uint32_t f = r | (uint32_t)(w.C >> cs);
+  const uint32_t t = w.dg & m;
+  return g.all & ~(f | t | (t >> 16));
+}
+
+// Place value bits d at a cell (Words::toggle with explicit shifts).
+template <bool VSYM>
+__device__ __forceinline__ void snap_place(Words<true> &w, uint32_t rs, uint32_t cs, uint32_t m,
+                                           uint32_t d, const Geo &g) {
+  const uint32_t dm = mirror<VSYM>(d, g.n);
+  const uint32_t rd = VSYM ? ((d ^ dm) & g.pairmask) : d;
+  w.R ^= (unsigned long long)rd << rs;
+  w.C ^= (unsigned long long)d << cs;
+  if (VSYM) {
+    const uint32_t swapped = __byte_perm(m, 0u, 0x1032u);
+    w.dg ^= ((d * 0x10001u) & m) ^ ((dm * 0x10001u) & swapped);
+  } else {
+    w.dg ^= (d * 0x10001u) & m;
+  }
+}
+
+// One search iteration.  Returns true when the lane's work is finished.
+//   nv = lowest untried candidate at p (Algorithm 4's L & -L), removed from L
+//   place nv; candidates of the next cell: at the last cell their popcount
+//   is added (each completes a square), none is a dead end
+//   no dead end: if candidates remain at p, the state before placing nv is
+//   pushed as an entry; descend
+//   dead end or leaf: resume at p itself if candidates remain there (no
+//   entry is stored), else at the deepest entry.
+// ovf is set (and the entry dropped; the spare slot cap keeps every write in
+// bounds) if a lane ever needs more entries than cap -- which the bound on
+// cap excludes.
+template <bool VSYM, bool NODES>
+__device__ __forceinline__ bool snap_step(SnapLane &s, const Geo &g, const SnapStack &st,
+                                          const SnapTable &tb, unsigned B, uint32_t &ovf) {
+  const uint32_t nv = s.L & (0u - s.L);
+  const uint32_t Lr = s.L ^ nv;
+  const bool keep = Lr != 0u;
+  const bool has = s.sp > s.bot;
+  // the entry a return would resume (read early and unconditionally -- slot
+  // 0 when the stack is empty; used only on a return)
+  const int rd = max(s.sp - 1, 0);
+  const uint4 ea = st.sa[rd * (int)B];
+  const uint32_t ew = st.sw[rd * (int)B];
+  const int q = s.p + 1;  // <= last: a lane never stands on the last cell
+  const unsigned long long R0 = s.w.R, C0 = s.w.C;
+  const uint32_t dg0 = s.w.dg;
+  snap_place<VSYM>(s.w, s.sh.x, s.sh.y, s.dm.x, nv, g);
+  if (NODES) s.nodes++;
+  const uint32_t L1 = snap_cands<VSYM>(s.w, s.sh.z, s.sh.w, s.dm.y, g);
+  const bool leaf = q == g.last;
+  const unsigned leaves = leaf ? (unsigned)__popc(L1) : 0u;
+  s.cnt += leaves;
+  if (NODES) s.nodes += leaves;
+  const bool dead = leaf || L1 == 0u;
+  const bool push = keep && !dead;
+  const bool pop = dead && !keep && has;
+  const bool back = dead && keep;  // resume at p itself
+  // the new entry is written unconditionally to the first free slot (slot
+  // cap is spare, so a write that is not a push never touches a live one)
+  const int wr = min(s.sp, st.cap);
+  st.sa[wr * (int)B] = make_uint4((uint32_t)R0, (uint32_t)(R0 >> 32), (uint32_t)C0,
+                                  (uint32_t)(C0 >> 32));
+  st.sw[wr * (int)B] = snap_pack<VSYM>(dg0, s.p, Lr);
+  const bool room = s.sp < st.cap;
+  ovf |= (push && !room) ? 1u : 0u;
+  uint32_t edg, eL;
+  int ep;
+  snap_unpack<VSYM>(ew, g.n, edg, ep, eL);
+  const unsigned long long eR = ((unsigned long long)ea.y << 32) | ea.x;
+  const unsigned long long eC = ((unsigned long long)ea.w << 32) | ea.z;
+  s.w.R = back ? R0 : (pop ? eR : s.w.R);
+  s.w.C = back ? C0 : (pop ? eC : s.w.C);
+  s.w.dg = back ? dg0 : (pop ? edg : s.w.dg);
+  s.L = back ? Lr : (pop ? eL : L1);
+  s.p = dead ? (pop ? ep : s.p) : q;
+  s.sp += (push && room) ? 1 : (pop ? -1 : 0);
+  // table row of the new position, for the next iteration
+  s.sh = tb.sh[s.p];
+  s.dm = tb.dm[s.p];
+  return dead && !keep && !has;
+}
+
+}  // namespace dls

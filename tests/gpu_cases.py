@@ -24,11 +24,21 @@ class Workload:
         assert (prefixes == oracle_prefixes).all()
 
 
-def split(dls, n, flags, after_row0, first_rows=1):
-    """Row 0 identity, every valid prefix `after_row0` cells past row 0."""
+def split(dls, n, flags, after_row0, first_rows=1, kind=None):
+    """Row 0 identity, every valid prefix `after_row0` cells past row 0.
+    kind: None = main diagonal, anti-diagonal, rows; dls.ORDER_ROW_MAJOR;
+    dls.ORDER_HEURISTIC (the Section 2.3 order after row 0)."""
     vs = bool(flags & V)
-    order = dls.fill_order(n, flags, first_rows=first_rows)
-    o_order = orders.md_ad_rows(n, vsym=vs, first_rows=first_rows)
+    if kind is None:
+        order = dls.fill_order(n, flags, first_rows=first_rows)
+        o_order = orders.md_ad_rows(n, vsym=vs, first_rows=first_rows)
+    elif kind == dls.ORDER_ROW_MAJOR:
+        order = dls.fill_order(n, flags, kind=kind)
+        o_order = orders.row_major(n, vsym=vs)
+    else:
+        w0 = len(orders.identity(n, vs))
+        order = dls.order_complete(n, flags, dls.fill_order(n, flags)[:w0], w0, kind)
+        o_order = orders.heuristic_complete(n, orders.row0(n, vs), bool(flags & D), vs)
     w = len(orders.identity(n, vs))
     depth = min(len(o_order), w + after_row0)
     base = np.array([orders.identity(n, vs)], np.uint8)

@@ -42,6 +42,8 @@ SHAPES = [
     dict(blocks_per_sm=1, block_threads=64),
     dict(words=1),
     dict(words=1, lanes_per_prefix=2, block_threads=64),
+    dict(stack=1),
+    dict(stack=1, block_threads=64, check_every=1),
 ]
 
 
@@ -117,6 +119,50 @@ def test_larger_orders_from_sampled_partial_squares(dls, n, flags, rows):
         assert (c == ref).all(), sh
 
 
+def test_snapshot_stack_refused_where_it_does_not_apply(dls):
+    """The snapshot search needs register words and one lane per prefix."""
+    t9 = torch.from_numpy(np.arange(9, dtype=np.uint8)[None]).cuda()
+    t8 = torch.from_numpy(np.arange(8, dtype=np.uint8)[None]).cuda()
+    for n, t, sh in ((9, t9, dict(stack=2)), (8, t8, dict(stack=2, words=1)),
+                     (8, t8, dict(stack=2, lanes_per_prefix=2)),
+                     (8, t8, dict(stack=2, kernel=dls.KERNEL_PLAIN)), (8, t8, dict(stack=3))):
+        with pytest.raises(dls.DlsError) as e:
+            dls.count(n, D, dls.fill_order(n, D), t, launch=dls.Launch(**sh))
+        assert e.value.code == 3, (n, sh)
+
+
+def test_describe_launch_names_the_kernel(dls):
+    o8, o9 = dls.fill_order(8, D), dls.fill_order(9, D)
+    d = dls.describe_launch(8, D, o8, 15, 1000)
+    assert d["kernel"] == "k_snapshot" and d["words"] == "registers"
+    assert d["stack_entries"] > 0 and d["grid_blocks"] > 0
+    assert dls.describe_launch(8, D, o8, 15, 1000, dls.Launch(stack=1))["kernel"] == "k_persistent"
+    assert dls.describe_launch(8, D, o8, 15, 1000,
+                               dls.Launch(kernel=dls.KERNEL_PLAIN))["kernel"] == "k_plain"
+    d9 = dls.describe_launch(9, D, o9, 17, 1000)
+    assert d9["kernel"] == "k_persistent" and d9["words"] == "shared"
+    assert dls.describe_launch(8, D, o8, 15, 0)["grid_blocks"] == 0
+    with pytest.raises(dls.DlsError):
+        dls.describe_launch(9, D, o9, 17, 10, dls.Launch(stack=2))
+
+
+def test_snapshot_stack_deep_orders(dls):
+    """Orders whose cells after the prefix are mostly free (row-major order
+    from an empty square, so nothing is forced early): the snapshot stack
+    runs at its bound; the host-buffer entry reports any overflow."""
+    for n, flags, kind, after in ((6, D, dls.ORDER_ROW_MAJOR, 0), (6, 0, dls.ORDER_ROW_MAJOR, 3),
+                                  (7, D, dls.ORDER_ROW_MAJOR, 9), (8, D | V, dls.ORDER_ROW_MAJOR, 2),
+                                  (6, D | V, dls.ORDER_HEURISTIC, 0)):
+        wl = gpu_cases.split(dls, n, flags, after, kind=kind)
+        ref, _ = oracle.count_many(n, flags, wl.oracle_order, wl.oracle_prefixes,
+                                   threads=THREADS)
+        for sh in (dict(stack=2), dict(stack=2, block_threads=32, check_every=1)):
+            c = _gpu_counts(dls, n, flags, wl.order, wl.prefixes, dls.Launch(**sh))
+            assert (c == ref).all(), (n, flags, kind, sh)
+            hc, tot = dls.count_host(n, flags, wl.order, wl.prefixes, launch=dls.Launch(**sh))
+            assert (hc == ref).all() and tot == int(ref.sum())
+
+
 def test_register_words_refused_when_they_do_not_fit(dls):
     order = dls.fill_order(9, D)
     t = torch.from_numpy(np.arange(9, dtype=np.uint8)[None]).cuda()
@@ -132,7 +178,7 @@ def test_node_counts_match_oracle(dls):
                                          threads=THREADS)
         t = torch.from_numpy(wl.prefixes).cuda()
         for sh in (dict(), dict(lanes_per_prefix=4), dict(kernel=dls.KERNEL_PLAIN),
-                   dict(words=1)):
+                   dict(words=1), dict(stack=1)):
             nodes = torch.zeros(1, dtype=torch.uint64, device="cuda")
             c = dls.count(n, flags, wl.order, t, nodes=nodes, launch=dls.Launch(**sh))
             torch.cuda.synchronize()
