@@ -9,7 +9,9 @@ persistent kernel launched from a CUDA graph.  Reported:
 * value     -- squares enumerated per second (exact counts), device-timed
                with CUDA events on the launching stream, L2 flushed between
                steps;
-* plain     -- the same for the one-thread-per-prefix launch;
+* plain     -- the same for the one-thread-per-prefix launch with the same
+               search step (what batching gains), and with the per-position
+               step (plain_per_position_step);
 * e2e       -- through dls_count_host (host buffers, copies inside the timed
                region);
 * roofline  -- integer-issue roofline of the search kernel;
@@ -403,21 +405,27 @@ def main():
         squares_all = squares
     value = squares_all / step_s
 
-    # plain launch on the same workload
-    plain = None
-    if not args.no_plain:
-        pplan = dls.Plan(N, FLAGS, order, d_pre, counts, total,
-                         dls.Launch(kernel=dls.KERNEL_PLAIN, words=cfg.get("words", 0)))
+    # plain one-thread-per-prefix launches on the same workload: with the same
+    # search step (the batching comparison) and with the per-position step
+    def plain_leg(stack):
+        pl = dls.Launch(kernel=dls.KERNEL_PLAIN, words=cfg.get("words", 0), stack=stack)
+        pplan = dls.Plan(N, FLAGS, order, d_pre, counts, total, pl)
         for _ in range(max(args.warmup, 1)):
             pplan.launch(stream)
         torch.cuda.synchronize()
         pt = timed_steps(lambda: pplan.launch(stream), stream, args.steps, flush)
         if int(total.cpu().numpy()[0]) != squares:
             raise RuntimeError("plain launch count differs")
-        p_step = sum(pt) / len(pt)
-        plain = {"value": squares / p_step, "unit": UNIT, "ms_per_step": 1e3 * p_step,
-                 "kernel": "k_plain", "speedup_of_batched": p_step / step_s}
         pplan.close()
+        p_step = sum(pt) / len(pt)
+        return {"value": squares / p_step, "unit": UNIT, "ms_per_step": 1e3 * p_step,
+                "kernel": dls.describe_launch(N, FLAGS, order, depth, P, pl)["kernel"],
+                "speedup_of_batched": p_step / step_s}
+    plain = plain_pp = None
+    if not args.no_plain:
+        plain = plain_leg(0)
+        if plain["kernel"] != "k_plain":
+            plain_pp = plain_leg(1)
 
     # end to end through the host-buffer entry point
     e2e_step = None
@@ -455,6 +463,7 @@ def main():
                    "autotune": tuned,
                    "l2": "flushed: 256 MiB write between timed steps"},
         "plain": plain,
+        "plain_per_position_step": plain_pp,
         "e2e": None if e2e_step is None else {
             "value": squares_all / e2e_step if ws == 1 else squares / e2e_step,
             "unit": UNIT, "h2d_bytes_per_step": int(P * depth),

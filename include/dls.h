@@ -193,7 +193,7 @@ typedef struct {
                              n <= 10 with DLS_VSYM), else shared memory;
                              1 = shared memory; 2 = registers (BAD_ARG if
                              they do not fit)                                */
-    int stack;            /* persistent only: the search's stack --
+    int stack;            /* the search's stack --
                              1 = one entry per order position (Algorithm 4's
                              L and LS per cell; backing out of a cell is one
                              step);
@@ -201,8 +201,9 @@ typedef struct {
                              position and its untried candidates) only where
                              candidates remain after the one placed, so a
                              dead end returns to the deepest open cell in one
-                             step; register words and one lane per prefix
-                             only (BAD_ARG otherwise); entries per lane =
+                             step (persistent and plain kernels alike);
+                             register words and one lane per prefix only
+                             (BAD_ARG otherwise); entries per lane =
                              positions after the prefix whose cell is not
                              forced by a line with all other cells earlier;
                              0 = snapshots where they apply (default)        */
@@ -210,9 +211,12 @@ typedef struct {
 
 /* What a dls_count_ex call with this shape runs. */
 typedef enum {
-    DLS_RUN_PERSISTENT = 0, /* persistent grid, one stack entry per position */
-    DLS_RUN_PLAIN = 1,      /* one thread per work item                      */
-    DLS_RUN_SNAPSHOT = 2    /* persistent grid, snapshot stack               */
+    DLS_RUN_PERSISTENT = 0,     /* persistent grid, one stack entry per
+                                   position                                 */
+    DLS_RUN_PLAIN = 1,          /* one thread per work item, one stack entry
+                                   per position                             */
+    DLS_RUN_SNAPSHOT = 2,       /* persistent grid, snapshot stack          */
+    DLS_RUN_PLAIN_SNAPSHOT = 3  /* one thread per prefix, snapshot stack    */
 } dls_run_kind;
 
 typedef struct {

@@ -139,7 +139,7 @@ def _dev_ptr(t):
 
 def describe_launch(n, flags, order, depth, n_prefixes, launch=None):
     """The kernel and launch shape dls_count_ex would use (dls_describe_launch):
-    a dict with 'kernel' (k_snapshot / k_persistent / k_plain), 'words'
+    a dict with 'kernel' (k_snapshot / k_persistent / k_plain_snap / k_plain), 'words'
     ('registers' or 'shared'), 'block_threads', 'grid_blocks', 'smem_bytes',
     'stack_entries'."""
     o, op, ol = _order(order)

@@ -21,7 +21,9 @@ KERNEL_PLAIN = 1
 RUN_PERSISTENT = 0
 RUN_PLAIN = 1
 RUN_SNAPSHOT = 2
-RUN_NAMES = {RUN_PERSISTENT: "k_persistent", RUN_PLAIN: "k_plain", RUN_SNAPSHOT: "k_snapshot"}
+RUN_PLAIN_SNAPSHOT = 3
+RUN_NAMES = {RUN_PERSISTENT: "k_persistent", RUN_PLAIN: "k_plain", RUN_SNAPSHOT: "k_snapshot",
+             RUN_PLAIN_SNAPSHOT: "k_plain_snap"}
 
 OK = 0
 ERR_CAPACITY = 4

@@ -374,7 +374,7 @@ __device__ bool snap_load(SnapLane &s, const KParams &p, long long item, const C
 // busy lane that holds a stack entry; it takes the busy lane's bottom entry
 // (the shallowest open cell: the largest untried subtree) and the busy lane
 // drops it by raising its bottom index.
-template <bool VSYM>
+template <bool VSYM, bool DG>
 __device__ void snap_donate(SnapLane &s, bool &busy, const KParams &p, const SnapStack &st,
                             const SnapTable &tb, int lane, unsigned B) {
   const unsigned idle = __ballot_sync(FULL, !busy);
@@ -402,7 +402,9 @@ __device__ void snap_donate(SnapLane &s, bool &busy, const KParams &p, const Sna
     const uint32_t wv = st.sw[off];
     s.w.R = ((unsigned long long)a.y << 32) | a.x;
     s.w.C = ((unsigned long long)a.w << 32) | a.z;
-    snap_unpack<VSYM>(wv, p.g.n, s.w.dg, s.p, s.L);
+    uint32_t dg;
+    snap_unpack<VSYM>(wv, p.g.n, dg, s.p, s.L);
+    if (DG) s.w.dg = dg;
     s.sh = tb.sh[s.p];
     s.dm = tb.dm[s.p];
     s.sp = s.bot = 0;
@@ -417,13 +419,10 @@ __device__ void snap_donate(SnapLane &s, bool &busy, const KParams &p, const Sna
 // Shared memory: [cell table: 8 bytes per position, rounded to 32 positions]
 //                [position table: 16 + 8 bytes per position, same rounding]
 //                [stack: (cap + 1) * B entries of 16 bytes, then as many of 4]
-template <bool VSYM, bool NODES>
-__global__ void __launch_bounds__(512)
-    k_snapshot(const __grid_constant__ KParams p, int diag) {
-  extern __shared__ uint32_t smem[];
-  __shared__ unsigned long long red[16];
+__device__ __forceinline__ void snap_setup(const KParams &p, int diag, uint32_t *smem,
+                                           const Cell *&tbl, SnapTable &tb, SnapStack &st,
+                                           SnapLane &s) {
   const unsigned B = blockDim.x;
-  const int lane = threadIdx.x & 31;
   const int rows = (p.order_len + 31) & ~31;
   Cell *t = reinterpret_cast<Cell *>(smem);
   uint4 *tsh = reinterpret_cast<uint4 *>(smem + 2 * rows);
@@ -435,14 +434,12 @@ __global__ void __launch_bounds__(512)
              tdm[idx]);
   }
   uint4 *sa0 = reinterpret_cast<uint4 *>(tdm + rows);
-  SnapStack st;
   st.sa = sa0 + threadIdx.x;
   st.sw = reinterpret_cast<uint32_t *>(sa0 + (size_t)(p.snap_cap + 1) * B) + threadIdx.x;
   st.cap = p.snap_cap;
-  const Cell *tbl = t;
-  const SnapTable tb = {tsh, tdm};
-  uint32_t ovf = 0u;
-  SnapLane s;
+  tbl = t;
+  tb.sh = tsh;
+  tb.dm = tdm;
   s.w.tb = nullptr;
   s.w.R = s.w.C = 0ull;
   s.w.dg = 0u;
@@ -455,6 +452,54 @@ __global__ void __launch_bounds__(512)
   s.cnt = 0ull;
   s.nodes = 0ull;
   __syncthreads();
+}
+
+// The plain launch with the snapshot search: one thread per prefix, no
+// queue, no donation (the baseline the batched kernel is measured against,
+// with the same search step).
+template <bool VSYM, bool NODES, bool DG>
+__global__ void __launch_bounds__(512)
+    k_plain_snap(const __grid_constant__ KParams p, int diag) {
+  extern __shared__ uint32_t smem[];
+  __shared__ unsigned long long red[16];
+  const unsigned B = blockDim.x;
+  const Cell *tbl;
+  SnapTable tb;
+  SnapStack st;
+  SnapLane s;
+  snap_setup(p, diag, smem, tbl, tb, st, s);
+  uint32_t ovf = 0u;
+  unsigned long long lane_total = 0ull;
+  const long long item = (long long)blockIdx.x * B + threadIdx.x;
+  bool busy = false;
+  if (item < p.n_items) {
+    busy = !snap_load<VSYM, NODES>(s, p, item, tbl, tb);
+    if (!busy) flush_count(s.prefix, s.cnt, p, lane_total);
+  }
+  while (__any_sync(FULL, busy)) {
+    if (busy && snap_step<VSYM, NODES, DG>(s, p.g, st, tb, B, ovf)) {
+      busy = false;
+      flush_count(s.prefix, s.cnt, p, lane_total);
+    }
+  }
+  if (ovf) *reinterpret_cast<int *>(p.queue + 1) = 1;
+  block_reduce_add(lane_total, p.total, red);
+  if (NODES) block_reduce_add(s.nodes, p.nodes, red);
+}
+
+template <bool VSYM, bool NODES, bool DG>
+__global__ void __launch_bounds__(512)
+    k_snapshot(const __grid_constant__ KParams p, int diag) {
+  extern __shared__ uint32_t smem[];
+  __shared__ unsigned long long red[16];
+  const unsigned B = blockDim.x;
+  const int lane = threadIdx.x & 31;
+  const Cell *tbl;
+  SnapTable tb;
+  SnapStack st;
+  SnapLane s;
+  snap_setup(p, diag, smem, tbl, tb, st, s);
+  uint32_t ovf = 0u;
 
   unsigned long long lane_total = 0ull;
   bool busy = false;
@@ -481,7 +526,7 @@ __global__ void __launch_bounds__(512)
       // every lane is busy here: step until one finishes
       bool fin;
       do {
-        fin = snap_step<VSYM, NODES>(s, p.g, st, tb, B, ovf);
+        fin = snap_step<VSYM, NODES, DG>(s, p.g, st, tb, B, ovf);
       } while (!__any_sync(FULL, fin));
       if (fin) {
         busy = false;
@@ -489,12 +534,12 @@ __global__ void __launch_bounds__(512)
       }
     } else {
       for (int it = 0; it <= p.check_mask; ++it) {
-        if (busy && snap_step<VSYM, NODES>(s, p.g, st, tb, B, ovf)) {
+        if (busy && snap_step<VSYM, NODES, DG>(s, p.g, st, tb, B, ovf)) {
           busy = false;
           flush_count(s.prefix, s.cnt, p, lane_total);
         }
       }
-      if (p.donate) snap_donate<VSYM>(s, busy, p, st, tb, lane, B);
+      if (p.donate) snap_donate<VSYM, DG>(s, busy, p, st, tb, lane, B);
     }
   }
   if (ovf) *reinterpret_cast<int *>(p.queue + 1) = 1;
@@ -675,9 +720,30 @@ static const void *pick_kernel(int kind, bool reg, bool vsym, bool nodes, bool s
   return reg ? pick2<true>(kind, vsym, nodes, split) : pick2<false>(kind, vsym, nodes, split);
 }
 
-static const void *pick_snapshot(bool vsym, bool nodes) {
-  if (vsym) return nodes ? (const void *)k_snapshot<true, true> : (const void *)k_snapshot<true, false>;
-  return nodes ? (const void *)k_snapshot<false, true> : (const void *)k_snapshot<false, false>;
+template <bool VSYM, bool NODES, bool DG>
+static const void *snapshot_ptr(bool plain) {
+  return plain ? (const void *)k_plain_snap<VSYM, NODES, DG>
+               : (const void *)k_snapshot<VSYM, NODES, DG>;
+}
+
+template <bool VSYM>
+static const void *pick_snapshot2(bool plain, bool nodes, bool dg) {
+  if (dg) return nodes ? snapshot_ptr<VSYM, true, true>(plain)
+                       : snapshot_ptr<VSYM, false, true>(plain);
+  return nodes ? snapshot_ptr<VSYM, true, false>(plain) : snapshot_ptr<VSYM, false, false>(plain);
+}
+
+// dg: some cell at or after the prefix depth lies on a diagonal (the
+// diagonal words change during the search)
+static const void *pick_snapshot(bool plain, bool vsym, bool nodes, bool dg) {
+  return vsym ? pick_snapshot2<true>(plain, nodes, dg) : pick_snapshot2<false>(plain, nodes, dg);
+}
+
+static bool diagonal_cells_after(const OrderInfo &info, int n, uint32_t flags, int depth) {
+  if (!(flags & DLS_DIAGONAL)) return false;
+  for (int t = depth; t < info.len; ++t)
+    if (info.i[t] == info.j[t] || info.i[t] + info.j[t] == n - 1) return true;
+  return false;
 }
 
 // Do all row words and all column words fit one 64-bit register each?
@@ -769,10 +835,9 @@ static int prepare_launch(int n, uint32_t flags, const uint8_t *order, int order
   if (sh.words == 2 && !reg) return DLS_ERR_BAD_ARG;
   kp.wr = wr;
   kp.wc = wc;
-  // the snapshot search: persistent grid, register words, one lane per
-  // prefix; order positions must fit its packed entry
-  const bool snap_ok = sh.kernel == DLS_KERNEL_PERSISTENT && reg && sh.lanes_log2 == 0 &&
-                       order_len <= (vsym ? 64 : 256);
+  // the snapshot search: register words, one lane per prefix; order
+  // positions must fit its packed entry
+  const bool snap_ok = reg && sh.lanes_log2 == 0 && order_len <= (vsym ? 64 : 256);
   if (sh.stack == 2 && !snap_ok) return DLS_ERR_BAD_ARG;
   bool snap = snap_ok && sh.stack != 1;
   kp.snap_cap = snap ? std::max(1, snapshot_entries(info, n, flags, depth)) : 0;
@@ -790,9 +855,11 @@ static int prepare_launch(int n, uint32_t flags, const uint8_t *order, int order
     kp.snap_cap = 0;
   }
   pr->reg = reg;
-  pr->run = snap ? DLS_RUN_SNAPSHOT
-                 : (sh.kernel == DLS_KERNEL_PLAIN ? DLS_RUN_PLAIN : DLS_RUN_PERSISTENT);
-  pr->fn = snap ? pick_snapshot(vsym, d_nodes != nullptr)
+  const bool plain = sh.kernel == DLS_KERNEL_PLAIN;
+  pr->run = snap ? (plain ? DLS_RUN_PLAIN_SNAPSHOT : DLS_RUN_SNAPSHOT)
+                 : (plain ? DLS_RUN_PLAIN : DLS_RUN_PERSISTENT);
+  pr->fn = snap ? pick_snapshot(plain, vsym, d_nodes != nullptr,
+                                diagonal_cells_after(info, n, flags, depth))
                 : pick_kernel(sh.kernel, reg, vsym, d_nodes != nullptr, sh.lanes_log2 > 0);
   auto smem_for = [&](int block) {
     return snap ? smem_bytes_snapshot(order_len, kp.snap_cap, block)
@@ -808,14 +875,14 @@ static int prepare_launch(int n, uint32_t flags, const uint8_t *order, int order
   pr->smem = smem;
   pr->grid = 0;
   if (n_prefixes == 0 || zero_all) return DLS_OK;
+  cudaError_t e = cudaFuncSetAttribute(pr->fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return cuda_fail(e);
   if (sh.kernel == DLS_KERNEL_PLAIN) {
     long long g = (kp.n_items + sh.block - 1) / sh.block;
     if (g > 0x7fffffffll) return DLS_ERR_BAD_ARG;
     pr->grid = (unsigned)g;
   } else {
-    cudaError_t e = cudaFuncSetAttribute(pr->fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return cuda_fail(e);
     int per_sm = sh.blocks_per_sm;
     if (per_sm == 0) {
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pr->fn, sh.block, smem);
@@ -858,7 +925,7 @@ static int enqueue_count(int n, uint32_t flags, const uint8_t *order,
     if (e != cudaSuccess) return cuda_fail(e);
   }
   if (pr.grid == 0) return DLS_OK;
-  if (pr.run != DLS_RUN_PLAIN) {
+  if (pr.run != DLS_RUN_PLAIN) {  // queue head and / or overflow flag
     if (scratch == nullptr) {
       Workspace *ws = nullptr;
       rc = get_workspace(stream, &ws);
@@ -978,6 +1045,8 @@ int dls_count_host(int n, uint32_t flags, const uint8_t *order,
     if (e != cudaSuccess) return cuda_fail(e);
   }
   uint64_t *d_counts = reinterpret_cast<uint64_t *>(ws->d2h);
+  e = cudaMemsetAsync(ws->scratch + 1, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return cuda_fail(e);
   rc = enqueue_count(n, flags, order, order_len, ws->h2d, depth, n_prefixes,
                      d_counts, nullptr, nullptr, cfg, st);
   if (rc) return rc;

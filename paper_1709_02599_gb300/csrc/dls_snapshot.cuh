@@ -112,7 +112,9 @@ struct SnapStack {
 };
 
 // Admissible values of a cell (fields at shifts rs, cs, diagonal mask m).
-template <bool VSYM>
+// DG = false: no cell searched lies on a diagonal, the diagonal words are
+// left out.
+template <bool VSYM, bool DG>
 __device__ __forceinline__ uint32_t snap_cands(const Words<true> &w, uint32_t rs, uint32_t cs,
                                                uint32_t m, const Geo &g) {
   uint32_t r = (uint32_t)(w.R >> rs);
@@ -121,18 +123,20 @@ __device__ __forceinline__ uint32_t snap_cands(const Words<true> &w, uint32_t rs
     r |= mirror<true>(r, g.n);
   }
   const uint32_t f = r | (uint32_t)(w.C >> cs);
+  if (!DG) return g.all & ~f;
   const uint32_t t = w.dg & m;
   return g.all & ~(f | t | (t >> 16));
 }
 
 // Place value bits d at a cell (Words::toggle with explicit shifts).
-template <bool VSYM>
+template <bool VSYM, bool DG>
 __device__ __forceinline__ void snap_place(Words<true> &w, uint32_t rs, uint32_t cs, uint32_t m,
                                            uint32_t d, const Geo &g) {
   const uint32_t dm = mirror<VSYM>(d, g.n);
   const uint32_t rd = VSYM ? ((d ^ dm) & g.pairmask) : d;
   w.R ^= (unsigned long long)rd << rs;
   w.C ^= (unsigned long long)d << cs;
+  if (!DG) return;
   if (VSYM) {
     const uint32_t swapped = __byte_perm(m, 0u, 0x1032u);
     w.dg ^= ((d * 0x10001u) & m) ^ ((dm * 0x10001u) & swapped);
@@ -152,7 +156,7 @@ __device__ __forceinline__ void snap_place(Words<true> &w, uint32_t rs, uint32_t
 // ovf is set (and the entry dropped; the spare slot cap keeps every write in
 // bounds) if a lane ever needs more entries than cap -- which the bound on
 // cap excludes.
-template <bool VSYM, bool NODES>
+template <bool VSYM, bool NODES, bool DG>
 __device__ __forceinline__ bool snap_step(SnapLane &s, const Geo &g, const SnapStack &st,
                                           const SnapTable &tb, unsigned B, uint32_t &ovf) {
   const uint32_t nv = s.L & (0u - s.L);
@@ -167,9 +171,9 @@ __device__ __forceinline__ bool snap_step(SnapLane &s, const Geo &g, const SnapS
   const int q = s.p + 1;  // <= last: a lane never stands on the last cell
   const unsigned long long R0 = s.w.R, C0 = s.w.C;
   const uint32_t dg0 = s.w.dg;
-  snap_place<VSYM>(s.w, s.sh.x, s.sh.y, s.dm.x, nv, g);
+  snap_place<VSYM, DG>(s.w, s.sh.x, s.sh.y, s.dm.x, nv, g);
   if (NODES) s.nodes++;
-  const uint32_t L1 = snap_cands<VSYM>(s.w, s.sh.z, s.sh.w, s.dm.y, g);
+  const uint32_t L1 = snap_cands<VSYM, DG>(s.w, s.sh.z, s.sh.w, s.dm.y, g);
   const bool leaf = q == g.last;
   const unsigned leaves = leaf ? (unsigned)__popc(L1) : 0u;
   s.cnt += leaves;
@@ -183,7 +187,7 @@ __device__ __forceinline__ bool snap_step(SnapLane &s, const Geo &g, const SnapS
   const int wr = min(s.sp, st.cap);
   st.sa[wr * (int)B] = make_uint4((uint32_t)R0, (uint32_t)(R0 >> 32), (uint32_t)C0,
                                   (uint32_t)(C0 >> 32));
-  st.sw[wr * (int)B] = snap_pack<VSYM>(dg0, s.p, Lr);
+  st.sw[wr * (int)B] = snap_pack<VSYM>(DG ? dg0 : 0u, s.p, Lr);
   const bool room = s.sp < st.cap;
   ovf |= (push && !room) ? 1u : 0u;
   uint32_t edg, eL;
@@ -193,7 +197,7 @@ __device__ __forceinline__ bool snap_step(SnapLane &s, const Geo &g, const SnapS
   const unsigned long long eC = ((unsigned long long)ea.w << 32) | ea.z;
   s.w.R = back ? R0 : (pop ? eR : s.w.R);
   s.w.C = back ? C0 : (pop ? eC : s.w.C);
-  s.w.dg = back ? dg0 : (pop ? edg : s.w.dg);
+  if (DG) s.w.dg = back ? dg0 : (pop ? edg : s.w.dg);
   s.L = back ? Lr : (pop ? eL : L1);
   s.p = dead ? (pop ? ep : s.p) : q;
   s.sp += (push && room) ? 1 : (pop ? -1 : 0);

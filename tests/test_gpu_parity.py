@@ -61,8 +61,10 @@ def test_config1_order6_single_subproblem(dls, golden):
 
 @pytest.mark.parametrize("n,flags,after", [(4, D, 0), (5, D, 3), (5, 0, 4), (6, D, 5),
                                            (6, D, 9), (6, D | V, 2), (6, 0, 8), (7, D, 4),
-                                           (8, D | V, 6), (7, D, 14)])
+                                           (8, D | V, 6), (7, D, 14), (6, D, 12)])
 def test_small_workloads_all_shapes(dls, n, flags, after):
+    # (7, D, 14) and (6, D, 12) hold both diagonals in the prefix: the
+    # snapshot search runs without diagonal words there
     wl = gpu_cases.split(dls, n, flags, after)
     ref, _ = oracle.count_many(n, flags, wl.oracle_order, wl.oracle_prefixes, threads=THREADS)
     for sh in SHAPES:
@@ -71,6 +73,7 @@ def test_small_workloads_all_shapes(dls, n, flags, after):
         c = _gpu_counts(dls, n, flags, wl.order, wl.prefixes,
                         dls.Launch(kernel=dls.KERNEL_PLAIN, **sh))
         assert (c == ref).all(), ("plain", sh)
+
 
 
 def test_config2_order7_split10(dls):
@@ -125,7 +128,8 @@ def test_snapshot_stack_refused_where_it_does_not_apply(dls):
     t8 = torch.from_numpy(np.arange(8, dtype=np.uint8)[None]).cuda()
     for n, t, sh in ((9, t9, dict(stack=2)), (8, t8, dict(stack=2, words=1)),
                      (8, t8, dict(stack=2, lanes_per_prefix=2)),
-                     (8, t8, dict(stack=2, kernel=dls.KERNEL_PLAIN)), (8, t8, dict(stack=3))):
+                     (8, t8, dict(stack=2, kernel=dls.KERNEL_PLAIN, lanes_per_prefix=4)),
+                     (8, t8, dict(stack=3))):
         with pytest.raises(dls.DlsError) as e:
             dls.count(n, D, dls.fill_order(n, D), t, launch=dls.Launch(**sh))
         assert e.value.code == 3, (n, sh)
@@ -138,7 +142,9 @@ def test_describe_launch_names_the_kernel(dls):
     assert d["stack_entries"] > 0 and d["grid_blocks"] > 0
     assert dls.describe_launch(8, D, o8, 15, 1000, dls.Launch(stack=1))["kernel"] == "k_persistent"
     assert dls.describe_launch(8, D, o8, 15, 1000,
-                               dls.Launch(kernel=dls.KERNEL_PLAIN))["kernel"] == "k_plain"
+                               dls.Launch(kernel=dls.KERNEL_PLAIN))["kernel"] == "k_plain_snap"
+    assert dls.describe_launch(8, D, o8, 15, 1000,
+                               dls.Launch(kernel=dls.KERNEL_PLAIN, stack=1))["kernel"] == "k_plain"
     d9 = dls.describe_launch(9, D, o9, 17, 1000)
     assert d9["kernel"] == "k_persistent" and d9["words"] == "shared"
     assert dls.describe_launch(8, D, o8, 15, 0)["grid_blocks"] == 0
@@ -156,7 +162,8 @@ def test_snapshot_stack_deep_orders(dls):
         wl = gpu_cases.split(dls, n, flags, after, kind=kind)
         ref, _ = oracle.count_many(n, flags, wl.oracle_order, wl.oracle_prefixes,
                                    threads=THREADS)
-        for sh in (dict(stack=2), dict(stack=2, block_threads=32, check_every=1)):
+        for sh in (dict(stack=2), dict(stack=2, block_threads=32, check_every=1),
+                   dict(stack=2, kernel=dls.KERNEL_PLAIN)):
             c = _gpu_counts(dls, n, flags, wl.order, wl.prefixes, dls.Launch(**sh))
             assert (c == ref).all(), (n, flags, kind, sh)
             hc, tot = dls.count_host(n, flags, wl.order, wl.prefixes, launch=dls.Launch(**sh))
