@@ -315,16 +315,15 @@ __global__ void __launch_bounds__(512)
     }
     if (idle == FULL) break;  // queue drained and every lane idle
     if (!qdone) {
-      // run until some lane finishes its item
+      // every lane is busy here: step until one finishes its item
+      bool fin;
       do {
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          if (busy && dfs_step<REG, VSYM, NODES, SPLIT>(s, p.g, p.sp, sbase, tbl, B)) {
-            busy = false;
-            flush_count(s.prefix, s.cnt, p, lane_total);
-          }
-        }
-      } while (__all_sync(FULL, busy));
+        fin = dfs_step<REG, VSYM, NODES, SPLIT>(s, p.g, p.sp, sbase, tbl, B);
+      } while (!__any_sync(FULL, fin));
+      if (fin) {
+        busy = false;
+        flush_count(s.prefix, s.cnt, p, lane_total);
+      }
     } else {
       for (int it = 0; it <= p.check_mask; ++it) {
         if (busy && dfs_step<REG, VSYM, NODES, SPLIT>(s, p.g, p.sp, sbase, tbl, B)) {

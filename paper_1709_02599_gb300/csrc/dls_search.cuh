@@ -26,6 +26,8 @@ struct Geo {
   uint32_t pairmask;  // (1 << n/2) - 1: value pairs of a symmetric row
   int depth;          // prefix length = first position with a stack entry
   int last;           // order length - 1
+  uint32_t vsmask;    // all ones with vertical symmetry, else 0 (read only by
+                      // the step that takes the flag at run time)
 };
 
 // Work-item split of a prefix over several lanes (SPLIT kernels only).
@@ -127,6 +129,17 @@ struct Words {
       dg ^= (d * 0x10001u) & c.y;
     }
   }
+  // toggle() with vertical symmetry decided at run time by g.vsmask (one
+  // step body for lanes of a warp that serve different jobs); shared-memory
+  // words only.  With dm = 0 the symmetric update reduces to the plain one.
+  __device__ __forceinline__ void toggle_rt(Cell c, uint32_t d, const Geo &g) {
+    static_assert(!REG, "runtime symmetry flag: shared-memory words only");
+    const uint32_t dm = (__brev(d) >> (32 - g.n)) & g.vsmask;
+    word_at(tb, c.x & 0xffffu) ^= d ^ dm;
+    word_at(tb, c.x >> 16) ^= d;
+    const uint32_t swapped = __byte_perm(c.y, 0u, 0x1032u);
+    dg ^= ((d * 0x10001u) & c.y) ^ ((dm * 0x10001u) & swapped);
+  }
   __device__ __forceinline__ void clear(int words, unsigned B) {
     dg = 0u;
     if (REG) {
@@ -164,16 +177,21 @@ struct Lane {
 //            loop), an empty set is a dead end, else push and descend.
 // Written without data-dependent branches so that the lanes of a warp -- each
 // at its own position of its own subtree -- stay converged: every lane
-// computes the candidates of the next cell, and the outcome only selects
-// which registers change and whether the stack is written or read.
+// computes the candidates of the next cell, writes the stack slot of its
+// position and reads the one below it, and the outcome only selects which
+// registers change.
 //
 // sbase is the lane's stack base moved back by depth entries, so that the
 // entry of position k is sbase[k * B] (k >= depth).
-template <bool REG, bool VSYM, bool NODES, bool SPLIT>
+// RTV: vertical symmetry from g.vsmask at run time (VSYM is then ignored).
+template <bool REG, bool VSYM, bool NODES, bool SPLIT, bool RTV = false>
 __device__ __forceinline__ bool dfs_step(Lane<REG> &s, const Geo &g, const Split &sp,
                                          uint32_t *sbase, const Cell *tbl, unsigned B) {
   const uint32_t nv = s.L & (0u - s.L);
-  s.w.template toggle<VSYM>(s.info, s.v ^ nv, g);
+  if constexpr (RTV)
+    s.w.toggle_rt(s.info, s.v ^ nv, g);
+  else
+    s.w.template toggle<VSYM>(s.info, s.v ^ nv, g);
   s.L ^= nv;
   s.v = nv;
   const bool pop = nv == 0u;
@@ -195,16 +213,16 @@ __device__ __forceinline__ bool dfs_step(Lane<REG> &s, const Geo &g, const Split
   s.cnt += leaves;
   if (NODES) s.nodes += leaves;
   const bool down = live && !leaf && L1 != 0u;
-  // entry = untried candidates (bits 0-15) | placed value (bits 16-31)
-  if (down) sbase[s.p * (int)B] = __byte_perm(s.L, s.v, 0x5410u);
+  // entry = untried candidates (bits 0-15) | placed value (bits 16-31);
+  // written unconditionally: the slot of the current position is live only
+  // once the lane descends below it, which is when this write matters
+  sbase[s.p * (int)B] = __byte_perm(s.L, s.v, 0x5410u);
   const int pp = s.p - 1;
   const bool up = pop && pp >= g.depth;
-  uint32_t e = 0u;
-  Cell infoP = make_uint2(0u, 0u);
-  if (up) {
-    e = sbase[pp * (int)B];
-    infoP = tbl[pp];
-  }
+  // read unconditionally (used only when popping; clamped into the stack)
+  const int pr = max(pp, g.depth);
+  const uint32_t e = sbase[pr * (int)B];
+  const Cell infoP = tbl[pr];
   s.p = down ? q : (pop ? pp : s.p);
   s.L = down ? L1 : (up ? (e & 0xffffu) : s.L);
   s.v = down ? 0u : (up ? (e >> 16) : s.v);

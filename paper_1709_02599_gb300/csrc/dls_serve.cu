@@ -154,21 +154,41 @@ __global__ void __launch_bounds__(256) k_serve(const __grid_constant__ ServePara
     for (int k = 0; k < s.p - l.g.depth; ++k) stk[k * B] = slot[(SV_HDR + SV_WORDS + k) * G];
     s.info = l.tbl[s.p];
   }
+  // The epoch: idle lanes of a warp take queued items together (one atomic
+  // per warp); while every lane of the warp is busy it steps until one
+  // finishes; once the queue is drained the remaining searches step on.
+  // Lanes may serve different jobs: one step body decides vertical symmetry
+  // from the job at run time, so the warp never splits on it.
+  const int lane = threadIdx.x & 31;
   bool drained = false;
-  for (int it = 0; it < P.budget; ++it) {
-    if (!busy) {
-      if (drained) break;
-      const unsigned long long idx = atomicAdd(P.head, 1ull);
-      if (idx >= P.tail) {
-        drained = true;
-        break;
+  int it = 0;
+  while (it < P.budget) {
+    unsigned idle = __ballot_sync(FULL, !busy);
+    if (idle != 0u && !drained) {
+      const int nidle = __popc(idle);
+      unsigned long long base = 0ull;
+      if (lane == 0) base = atomicAdd(P.head, (unsigned long long)nidle);
+      base = __shfl_sync(FULL, base, 0);
+      if (!busy) {
+        const unsigned long long idx = base + (unsigned)__popc(idle & ((1u << lane) - 1u));
+        if (idx < P.tail) busy = sv_load(l, P, P.queue[idx % P.qcap], B);
       }
-      busy = sv_load(l, P, P.queue[idx % P.qcap], B);
+      if (base + (unsigned long long)nidle >= P.tail) drained = true;
+      ++it;
       continue;
     }
+    if (idle == FULL) break;  // drained and nothing left to search
     uint32_t *sbase = stk - l.g.depth * (int)B;
-    const bool fin = l.vsym ? dfs_step<false, true, false, false>(l.s, l.g, nosplit, sbase, l.tbl, B)
-                            : dfs_step<false, false, false, false>(l.s, l.g, nosplit, sbase, l.tbl, B);
+    bool fin = false;
+    if (idle == 0u) {
+      do {
+        fin = dfs_step<false, false, false, false, true>(l.s, l.g, nosplit, sbase, l.tbl, B);
+        ++it;
+      } while (!__any_sync(FULL, fin) && it < P.budget);
+    } else {
+      if (busy) fin = dfs_step<false, false, false, false, true>(l.s, l.g, nosplit, sbase, l.tbl, B);
+      ++it;
+    }
     if (fin) {
       sv_finish(l, P);
       busy = false;
@@ -487,6 +507,7 @@ int dls_server_step(dls_server *s) {
     // odd order with vertical symmetry: no left cell may hold (n-1)/2
     if ((j->flags & DLS_VSYM) && (j->n & 1)) dj.g.all &= ~(1u << (j->n / 2));
     dj.g.pairmask = (1u << (j->n / 2)) - 1u;
+    dj.g.vsmask = (j->flags & DLS_VSYM) ? 0xffffffffu : 0u;
     dj.g.depth = j->depth;
     dj.g.last = dj.order_len - 1;
     for (int t = 0; t < dj.order_len; ++t)
