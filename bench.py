@@ -49,11 +49,13 @@ DIAGS, AFTER_ROW0 = 64, 20
 OPS_PER_NODE = 11
 ISSUE_LANES_PER_SM = 4 * 32      # 4 schedulers x 32 lanes, one instruction/clk
 L2_FLUSH_BYTES = 256 << 20
-# DRAM bytes (read + write) per prefix of k_snapshot<0,0> on the order-8
-# workload: one ncu capture of 16 of the 64 diagonals (273 038 prefixes,
-# 9.84 MB read, 0 written while the kernel ran), scaled per prefix; the
-# profile summary under profiles/ gives the command
-TRAFFIC_PER_PREFIX = {("dls8_diag64", "k_snapshot"): 9.843456e6 / 273038}
+# DRAM bytes (read + write) per prefix of k_snapshot on the order-8 workload,
+# per split depth: ncu captures of 16 of the 64 diagonals (depth 28: 273 038
+# prefixes, 9.844 MB read; depth 25: 149 590 prefixes, 5.255 MB read; 0
+# written while the kernel ran), scaled per prefix; the profile summary under
+# profiles/ gives the commands
+TRAFFIC_PER_PREFIX = {("dls8_diag64", "k_snapshot", 28): 9.844224e6 / 273038,
+                      ("dls8_diag64", "k_snapshot", 25): 5.254656e6 / 149590}
 
 
 def parse():
@@ -75,6 +77,8 @@ def parse():
                     help="split 20 cells past row 0, cells after the split row by row")
     ap.add_argument("--suffix", default="", choices=["", "given", "heuristic"],
                     help="fix the order of the cells after the split")
+    ap.add_argument("--depth", type=int, default=0,
+                    help="fix the split depth (cells from the start of the order)")
     ap.add_argument("--serve-jobs", type=int, default=100,
                     help="also replay this many jobs of the serving mix (Poisson arrivals "
                          "at 200/s) and report latency percentiles")
@@ -344,13 +348,14 @@ def main():
     fixed = json.loads(args.launch) if args.launch else None
     tuned = None
     if args.no_autotune:
-        depth_sel, suffix_sel, cfg = spec.default_depth, args.suffix or "given", fixed or {}
+        depth_sel = args.depth or spec.default_depth
+        suffix_sel, cfg = args.suffix or "given", fixed or {}
     else:
         t0 = time.perf_counter()
         suffixes = (args.suffix,) if args.suffix else ("given", "heuristic")
         shapes = [{}] if fixed is not None else None
-        best = autotune.tune(N, FLAGS, order0, base, spec.depths, suffixes=suffixes,
-                             shapes=shapes)
+        best = autotune.tune(N, FLAGS, order0, base, [args.depth] if args.depth else spec.depths,
+                             suffixes=suffixes, shapes=shapes)
         depth_sel, suffix_sel = best["depth"], best["suffix"]
         cfg = fixed if fixed is not None else best["launch"]
         tuned = {"trials": len(best["trials"]), "cached": best["cached"],
@@ -470,8 +475,9 @@ def main():
             "d2h_bytes_per_step": int(P * 8), "entry": "dls_count_host"},
         "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops,
                      "unit": "Tops/s", "frac": achieved_tops / peak_tops,
-                     "traffic": (TRAFFIC_PER_PREFIX[(spec.name, run["kernel"])] * P
-                                 if (spec.name, run["kernel"]) in TRAFFIC_PER_PREFIX else None),
+                     "traffic": (TRAFFIC_PER_PREFIX[(spec.name, run["kernel"], depth)] * P
+                                 if (spec.name, run["kernel"], depth) in TRAFFIC_PER_PREFIX
+                                 else None),
                      "algorithmic_bytes": int(P * (depth + 8)),
                      "ops_per_node": OPS_PER_NODE,
                      "peak_from": "%d SMs x 4 schedulers x 32 lanes x %.0f MHz" % (sms, sm_max_mhz)},

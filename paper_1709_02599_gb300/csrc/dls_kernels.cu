@@ -396,7 +396,7 @@ __device__ void snap_donate(SnapLane &s, bool &busy, const KParams &p, const Sna
   const int d_bot = __shfl_sync(FULL, s.bot, partner);
   const long long d_prefix = __shfl_sync(FULL, s.prefix, partner);
   if (receiver) {
-    const int off = d_bot * (int)B + (partner - lane);
+    const int off = (d_bot + 1) * (int)B + (partner - lane);
     const uint4 a = st.sa[off];
     const uint32_t wv = st.sw[off];
     s.w.R = ((unsigned long long)a.y << 32) | a.x;
@@ -417,7 +417,7 @@ __device__ void snap_donate(SnapLane &s, bool &busy, const KParams &p, const Sna
 
 // Shared memory: [cell table: 8 bytes per position, rounded to 32 positions]
 //                [position table: 16 + 8 bytes per position, same rounding]
-//                [stack: (cap + 1) * B entries of 16 bytes, then as many of 4]
+//                [stack: (cap + 2) * B entries of 16 bytes, then as many of 4]
 __device__ __forceinline__ void snap_setup(const KParams &p, int diag, uint32_t *smem,
                                            const Cell *&tbl, SnapTable &tb, SnapStack &st,
                                            SnapLane &s) {
@@ -434,7 +434,7 @@ __device__ __forceinline__ void snap_setup(const KParams &p, int diag, uint32_t 
   }
   uint4 *sa0 = reinterpret_cast<uint4 *>(tdm + rows);
   st.sa = sa0 + threadIdx.x;
-  st.sw = reinterpret_cast<uint32_t *>(sa0 + (size_t)(p.snap_cap + 1) * B) + threadIdx.x;
+  st.sw = reinterpret_cast<uint32_t *>(sa0 + (size_t)(p.snap_cap + 2) * B) + threadIdx.x;
   st.cap = p.snap_cap;
   tbl = t;
   tb.sh = tsh;
@@ -768,9 +768,9 @@ static size_t smem_bytes(int order_len, int n, int depth, int last, int block,
 }
 
 // Snapshot kernel: the cell table and the position table (8 + 24 bytes per
-// position), then 20 bytes per entry and lane, one spare entry included.
+// position), then 20 bytes per entry slot and lane (cap + 2 slots).
 static size_t smem_bytes_snapshot(int order_len, int entries, int block) {
-  return (size_t)((order_len + 31) & ~31) * 32u + (size_t)(entries + 1) * block * 20u;
+  return (size_t)((order_len + 31) & ~31) * 32u + (size_t)(entries + 2) * block * 20u;
 }
 
 // A resolved launch: the parameter block, the kernel and its shape.

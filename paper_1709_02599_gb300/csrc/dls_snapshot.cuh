@@ -15,13 +15,14 @@
 // its next candidate.  Every iteration places one value: iterations = search
 // nodes without the last cell.
 //
-// An iteration reads shared memory twice -- the entry it would return to
-// (issued first, used last) and the position-table row of the position it
-// ends at (two cells' field shifts and diagonal masks, used by the next
-// iteration) -- and writes the entry it would push, every time: the reads
-// and the write are unconditional (the write goes to the first free slot,
-// which a push then keeps), so the step has no branch at all and the lanes
-// of a warp never split.
+// An iteration writes the entry it would push (the state before its
+// placement) to the first free slot and reads back the entry a dead end
+// would resume -- that one, or the deepest live one -- plus the
+// position-table row of the position it ends at (two cells' field shifts and
+// diagonal masks, used by the next iteration).  Both accesses happen every
+// time (a push keeps the slot, anything else leaves it free), so the step
+// has no branch at all and the lanes of a warp never split; and a dead end
+// takes its whole state from the one entry read, one select per register.
 //
 // A position whose cell lies on a line (row, column or diagonal) that has
 // all its other cells earlier in the order has at most one candidate, so it
@@ -32,7 +33,9 @@
 // Only register-packed words (Words<true>: n <= 8, or even n <= 10 with
 // vertical symmetry).  An entry is 20 bytes: R and C as one 16-byte word and
 // a 32-bit word packing the diagonal words, the position and the untried
-// candidates; a lane has cap + 1 entry slots.
+// candidates; a lane has cap + 2 entry slots (entry e in slot e + 1; slot 0
+// is read when the stack is empty and never holds a live entry; slot cap + 1
+// takes the writes a push does not keep once the stack is full).
 #pragma once
 
 #include <cstdint>
@@ -151,11 +154,11 @@ __device__ __forceinline__ void snap_place(Words<true> &w, uint32_t rs, uint32_t
 //   is added (each completes a square), none is a dead end
 //   no dead end: if candidates remain at p, the state before placing nv is
 //   pushed as an entry; descend
-//   dead end or leaf: resume at p itself if candidates remain there (no
-//   entry is stored), else at the deepest entry.
-// ovf is set (and the entry dropped; the spare slot cap keeps every write in
-// bounds) if a lane ever needs more entries than cap -- which the bound on
-// cap excludes.
+//   dead end or leaf: resume at p itself if candidates remain there (that
+//   state is the entry just written, read back), else at the deepest entry.
+// ovf is set (and the stack index held at cap, so every access stays in the
+// lane's cap + 2 slots) if a lane ever needs more entries than cap -- which
+// the bound on cap excludes.
 template <bool VSYM, bool NODES, bool DG>
 __device__ __forceinline__ bool snap_step(SnapLane &s, const Geo &g, const SnapStack &st,
                                           const SnapTable &tb, unsigned B, uint32_t &ovf) {
@@ -163,11 +166,6 @@ __device__ __forceinline__ bool snap_step(SnapLane &s, const Geo &g, const SnapS
   const uint32_t Lr = s.L ^ nv;
   const bool keep = Lr != 0u;
   const bool has = s.sp > s.bot;
-  // the entry a return would resume (read early and unconditionally -- slot
-  // 0 when the stack is empty; used only on a return)
-  const int rd = max(s.sp - 1, 0);
-  const uint4 ea = st.sa[rd * (int)B];
-  const uint32_t ew = st.sw[rd * (int)B];
   const int q = s.p + 1;  // <= last: a lane never stands on the last cell
   const unsigned long long R0 = s.w.R, C0 = s.w.C;
   const uint32_t dg0 = s.w.dg;
@@ -179,28 +177,32 @@ __device__ __forceinline__ bool snap_step(SnapLane &s, const Geo &g, const SnapS
   s.cnt += leaves;
   if (NODES) s.nodes += leaves;
   const bool dead = leaf || L1 == 0u;
+  // entry e lives in slot e + 1 (slot 0 is never live, slot cap + 1 is
+  // spare): the state before placing nv is written to the first free slot
+  // every iteration; a push keeps it
+  st.sa[(s.sp + 1) * (int)B] = make_uint4((uint32_t)R0, (uint32_t)(R0 >> 32), (uint32_t)C0,
+                                          (uint32_t)(C0 >> 32));
+  st.sw[(s.sp + 1) * (int)B] = snap_pack<VSYM>(DG ? dg0 : 0u, s.p, Lr);
+  // a dead end resumes the entry just written if candidates remain at p,
+  // else the deepest live one (read back after the write; used only on a
+  // dead end)
+  const int rd = keep ? s.sp + 1 : s.sp;
+  const uint4 ea = st.sa[rd * (int)B];
+  const uint32_t ew = st.sw[rd * (int)B];
   const bool push = keep && !dead;
   const bool pop = dead && !keep && has;
-  const bool back = dead && keep;  // resume at p itself
-  // the new entry is written unconditionally to the first free slot (slot
-  // cap is spare, so a write that is not a push never touches a live one)
-  const int wr = min(s.sp, st.cap);
-  st.sa[wr * (int)B] = make_uint4((uint32_t)R0, (uint32_t)(R0 >> 32), (uint32_t)C0,
-                                  (uint32_t)(C0 >> 32));
-  st.sw[wr * (int)B] = snap_pack<VSYM>(DG ? dg0 : 0u, s.p, Lr);
-  const bool room = s.sp < st.cap;
-  ovf |= (push && !room) ? 1u : 0u;
+  ovf |= (push && s.sp >= st.cap) ? 1u : 0u;
   uint32_t edg, eL;
   int ep;
   snap_unpack<VSYM>(ew, g.n, edg, ep, eL);
   const unsigned long long eR = ((unsigned long long)ea.y << 32) | ea.x;
   const unsigned long long eC = ((unsigned long long)ea.w << 32) | ea.z;
-  s.w.R = back ? R0 : (pop ? eR : s.w.R);
-  s.w.C = back ? C0 : (pop ? eC : s.w.C);
-  if (DG) s.w.dg = back ? dg0 : (pop ? edg : s.w.dg);
-  s.L = back ? Lr : (pop ? eL : L1);
-  s.p = dead ? (pop ? ep : s.p) : q;
-  s.sp += (push && room) ? 1 : (pop ? -1 : 0);
+  s.w.R = dead ? eR : s.w.R;
+  s.w.C = dead ? eC : s.w.C;
+  if (DG) s.w.dg = dead ? edg : s.w.dg;
+  s.L = dead ? eL : L1;
+  s.p = dead ? ep : q;
+  s.sp = min(s.sp + (push ? 1 : 0) - (pop ? 1 : 0), st.cap);
   // table row of the new position, for the next iteration
   s.sh = tb.sh[s.p];
   s.dm = tb.dm[s.p];
