@@ -15,6 +15,9 @@ Workload recipes (sizes follow the paper's experiments, Sections 5.1-5.4):
   cells past row 0 (both diagonals and the rest of row 1).
 * ``vsym10_rows2``: order 10, vertically symmetric; ``choose(n_prefixes,
   2000, seed=0)`` picks 2000 of the valid fillings of rows 1 and 2.
+* Monte Carlo (Section 5.3): ``ranks(N^k, m, seed)`` -- m uniform ranks of
+  k-cell partial squares, each side selecting the partial square of a rank
+  itself.
 * serving: ``serving_jobs(n, seed)`` -- Poisson arrivals at 200 req/s, order
   uniform in {6, 7, 8, 9}, flag uniform in {diagonal, vertically symmetric},
   k uniform in {2, ..., N-3} fixed rows, and 4096 uint32 draws per job from
@@ -44,6 +47,11 @@ def choose(population, k, seed=0):
 def draws(count, seed, stream=0):
     """``count`` uniform uint32 numbers."""
     return rng(seed, stream).integers(0, 2**32, size=int(count), dtype=np.uint32)
+
+
+def ranks(total, count, seed, stream=3):
+    """``count`` uniform integers in [0, total) (Monte Carlo sample ranks)."""
+    return rng(seed, stream).integers(0, int(total), size=int(count), dtype=np.int64)
 
 
 def poisson_arrivals(rate_hz, n_jobs, seed=0):

@@ -260,6 +260,25 @@ def test_paper_partial_count_n10_k30(dls, golden):
     assert (c[idx] == ref).all()
 
 
+@pytest.mark.slow
+def test_paper_partial_count_n10_k32(dls, golden):
+    # Section 5.3: 12 611 543 636 160 partial diagonal Latin squares of order
+    # 10 with the first 32 cells in row-major order filled and row 0 fixed;
+    # split after 18 cells (~1e6 prefixes)
+    n = 10
+    order = dls.fill_order(n, D, dls.ORDER_ROW_MAJOR)[:32]
+    base = np.arange(n, dtype=np.uint8)[None]
+    pre, _ = dls.extend_prefixes(n, D, order, base, 18)
+    o_pre, _ = oracle.extend(n, D, orders.row_major(n)[:32], base, 18)
+    assert (pre == o_pre).all()
+    c = _gpu_counts(dls, n, D, order, pre)
+    assert int(c.sum(dtype=np.uint64)) == golden["n10_k32"]
+    # a few prefixes against the oracle
+    idx = np.arange(0, len(pre), len(pre) // 8)[:8]
+    ref, _ = oracle.count_many(n, D, orders.row_major(n)[:32], o_pre[idx], threads=THREADS)
+    assert (c[idx] == ref).all() and (ref > 0).any()
+
+
 def test_paper_hourglass8_on_gpu(dls, golden):
     # Section 4.2: 22 192 248 hourglass designs of order 8
     n = 8
