@@ -214,6 +214,45 @@ def test_config3_order8_diag64_sampled_against_oracle(dls):
     assert (c3 == c).all()
 
 
+def test_bench_configuration_against_oracle(dls):
+    """The order-8 workload exactly as the benchmark times it: split 28 cells
+    into the order (row 0, both diagonals, the rest of row 1), the Section
+    2.3 order after the split, counted through a CUDA-graph plan with the
+    default launch and the 64-thread blocks the autotuner picks; the prefixes
+    of 4 seed-chosen diagonals of the 64 against the oracle (its own order
+    and prefixes)."""
+    import dls_inputs
+    from paper_1709_02599_gb300 import autotune
+    n, depth = 8, 28
+    order0 = dls.fill_order(n, D)
+    ident = np.arange(n, dtype=np.uint8)[None]
+    diags, _ = dls.extend_prefixes(n, D, order0, ident, n + (n - 1))
+    picks = dls_inputs.choose(len(diags), 64, 0)         # the benchmark's seed-0 draw
+    order, pre, par = autotune.build_problem(n, D, order0, diags[picks], depth, "heuristic")
+    o_order = orders.heuristic_complete(n, orders.md_ad_rows(n)[:depth])
+    assert [tuple(map(int, x)) for x in order] == o_order
+    o_diags, _ = oracle.extend(n, D, orders.md_ad_rows(n), np.array([orders.identity(n)],
+                                                                        np.uint8), n + (n - 1))
+    o_pre, o_par = oracle.extend(n, D, o_order, o_diags[picks], depth)
+    assert (o_pre == pre).all() and (o_par == par).all()
+    sel = np.isin(par, dls_inputs.choose(64, 4, seed=2))
+    ref, _ = oracle.count_many(n, D, o_order, o_pre[sel], threads=THREADS)
+    assert int(ref.sum()) > 0
+    d_pre = torch.from_numpy(pre).cuda()
+    for launch in (dict(), dict(block_threads=64)):
+        counts = torch.empty(len(pre), dtype=torch.uint64, device="cuda")
+        total = torch.empty(1, dtype=torch.uint64, device="cuda")
+        plan = dls.Plan(n, D, order, d_pre, counts, total, dls.Launch(**launch))
+        plan.launch()
+        torch.cuda.synchronize()
+        c = counts.cpu().numpy()
+        plan.close()
+        assert dls.describe_launch(n, D, order, depth, len(pre),
+                                   dls.Launch(**launch))["kernel"] == "k_snapshot"
+        assert int(total.cpu().numpy()[0]) == int(c.sum(dtype=np.uint64))
+        assert (c[sel] == ref).all(), launch
+
+
 @pytest.mark.slow
 def test_config4_vsym10_smallest_against_oracle(dls):
     wl = gpu_cases.vsym10_rows2(dls)
