@@ -75,7 +75,7 @@ def parse():
                     "launch-shape stage of the autotuner)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="split 20 cells past row 0, cells after the split row by row")
-    ap.add_argument("--suffix", default="", choices=["", "given", "heuristic"],
+    ap.add_argument("--suffix", default="", choices=["", "given", "heuristic", "heuristic_sq"],
                     help="fix the order of the cells after the split")
     ap.add_argument("--depth", type=int, default=0,
                     help="fix the split depth (cells from the start of the order)")
@@ -121,8 +121,9 @@ class Dls8Diag64:
         from oracle import orders
         vs = bool(self.flags & 2)
         o_order = orders.md_ad_rows(self.n, vsym=vs, first_rows=self.first_rows)
-        if suffix == "heuristic":
-            o_order = orders.heuristic_complete(self.n, o_order[:depth], True, vs)
+        if suffix in ("heuristic", "heuristic_sq"):
+            o_order = orders.heuristic_complete(self.n, o_order[:depth], True, vs,
+                                                squares=suffix == "heuristic_sq")
         ident = np.array([orders.identity(self.n, vs)], np.uint8)
         allb, _ = oracle.extend(self.n, self.flags, o_order, ident, self.base_depth())
         picks = dls_inputs.choose(len(allb), self.units, seed)
@@ -352,7 +353,7 @@ def main():
         suffix_sel, cfg = args.suffix or "given", fixed or {}
     else:
         t0 = time.perf_counter()
-        suffixes = (args.suffix,) if args.suffix else ("given", "heuristic")
+        suffixes = (args.suffix,) if args.suffix else ("given", "heuristic", "heuristic_sq")
         shapes = [{}] if fixed is not None else None
         best = autotune.tune(N, FLAGS, order0, base, [args.depth] if args.depth else spec.depths,
                              suffixes=suffixes, shapes=shapes)
@@ -360,7 +361,8 @@ def main():
         cfg = fixed if fixed is not None else best["launch"]
         tuned = {"trials": len(best["trials"]), "cached": best["cached"],
                  "seconds": round(time.perf_counter() - t0, 2),
-                 "candidates": "split depth %s x order after the split {given, heuristic}, "
+                 "candidates": "split depth %s x order after the split {given, heuristic, "
+                               "heuristic_sq}, "
                                "then %d launch shapes" % (spec.depths,
                                                           len(shapes or autotune.SHAPES) - 1)}
     order, pre, par = autotune.build_problem(N, FLAGS, order0, base, depth_sel, suffix_sel)

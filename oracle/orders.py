@@ -102,7 +102,7 @@ def identity(n, vsym=False):
     return [j for j in _cols(n, vsym)]
 
 
-def heuristic_complete(n, kept, diagonal=True, vsym=False):
+def heuristic_complete(n, kept, diagonal=True, vsym=False, squares=False):
     """Section 2.3: starting from the `kept` cells (row 0 for a whole
     order), repeatedly take the unassigned cell with the largest
     V = r_i + c_j + md(i,j) + ad(i,j) -- the numbers of assigned cells in its
@@ -112,7 +112,9 @@ def heuristic_complete(n, kept, diagonal=True, vsym=False):
     anti-diagonal, looked at in that order), that cell is taken next
     (first-in first-out).  With vsym only left-half cells exist: a row has
     N//2 of them, a column N, and the diagonals form one line made of the
-    left cells on either diagonal.  Returns kept + the appended cells."""
+    left cells on either diagonal.  squares=True: V is the sum of the squares
+    of those numbers instead (a variant the paper does not have).  Returns
+    kept + the appended cells."""
     w = n // 2 if vsym else n
     lines = [[(i, j) for j in range(w)] for i in range(n)]
     lines += [[(i, j) for i in range(n)] for j in range(w)]
@@ -156,7 +158,8 @@ def heuristic_complete(n, kept, diagonal=True, vsym=False):
                 for j in range(w):
                     if (i, j) in assigned:
                         continue
-                    v = sum(sum(1 for x in lines[li] if x in assigned) for li in of_cell[(i, j)])
+                    counts = [sum(1 for x in lines[li] if x in assigned) for li in of_cell[(i, j)]]
+                    v = sum(c * c for c in counts) if squares else sum(counts)
                     if v > best:
                         best, cell = v, (i, j)
         assign(cell, True)

@@ -18,7 +18,8 @@ import numpy as np
 
 from . import _lib
 from ._lib import (DIAGONAL, VSYM, DLS_MAX_N, ORDER_MD_AD_ROWS, ORDER_ROW_MAJOR,  # noqa: F401
-                   ORDER_HOURGLASS, ORDER_HEURISTIC, KERNEL_PERSISTENT, KERNEL_PLAIN,
+                   ORDER_HOURGLASS, ORDER_HEURISTIC, ORDER_HEURISTIC_SQ, KERNEL_PERSISTENT,
+                   KERNEL_PLAIN,
                    DlsError)
 
 

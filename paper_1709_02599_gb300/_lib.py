@@ -14,6 +14,7 @@ ORDER_MD_AD_ROWS = 0
 ORDER_ROW_MAJOR = 1
 ORDER_HOURGLASS = 2
 ORDER_HEURISTIC = 3
+ORDER_HEURISTIC_SQ = 4
 
 KERNEL_PERSISTENT = 0
 KERNEL_PLAIN = 1

@@ -19,10 +19,11 @@ import time
 
 import numpy as np
 
-from . import (Launch, Plan, ORDER_HEURISTIC, ORDER_MD_AD_ROWS, KERNEL_PERSISTENT,
+from . import (Launch, Plan, ORDER_HEURISTIC, ORDER_HEURISTIC_SQ, ORDER_MD_AD_ROWS,
+               KERNEL_PERSISTENT,
                extend_prefixes, order_complete)
 
-SUFFIXES = {"given": None, "heuristic": ORDER_HEURISTIC}
+SUFFIXES = {"given": None, "heuristic": ORDER_HEURISTIC, "heuristic_sq": ORDER_HEURISTIC_SQ}
 SHAPES = [
     {},
     {"block_threads": 64},
@@ -96,7 +97,7 @@ def time_plan(n, flags, order, d_pre, launch, reps=2):
     return best, tot
 
 
-def tune(n, flags, order, base, depths, suffixes=("given", "heuristic"), shapes=None,
+def tune(n, flags, order, base, depths, suffixes=("given", "heuristic", "heuristic_sq"), shapes=None,
          reps=2, use_cache=True, log=None):
     """Two stages: (split depth, suffix) with the default launch shape, then
     the launch shape for the best of those.  Returns a dict with the chosen

@@ -158,9 +158,13 @@ static void order_hourglass(int n, bool vsym, std::vector<std::pair<int, int>> &
 // With vsym the cells are the left half: a row has n/2 of them, a column n,
 // and the two diagonals become one line (the left cells on the main diagonal
 // and those on the anti-diagonal, whose mirrors complete the main diagonal).
+// squares = true is this library's variant (DLS_ORDER_HEURISTIC_SQ): V is
+// the sum of the squares of those counts, which prefers a cell on one nearly
+// complete line to a cell on several half-filled ones; everything else is
+// the same.
 static void order_heuristic(int n, bool diag, bool vsym,
                             const std::vector<std::pair<int, int>> &kept,
-                            std::vector<std::pair<int, int>> &out) {
+                            std::vector<std::pair<int, int>> &out, bool squares = false) {
   const int w = vsym ? n / 2 : n;
   std::vector<std::vector<std::pair<int, int>>> lines;
   std::vector<std::vector<int>> of_cell(n * w);
@@ -224,7 +228,7 @@ static void order_heuristic(int n, bool diag, bool vsym,
         for (int j = 0; j < w; ++j) {
           if (asg[i * w + j]) continue;
           int v = 0;
-          for (int l : of_cell[i * w + j]) v += filled[l];
+          for (int l : of_cell[i * w + j]) v += squares ? filled[l] * filled[l] : filled[l];
           if (v > best) {
             best = v;
             cell = {i, j};
@@ -283,10 +287,11 @@ int dls_fill_order(int n, uint32_t flags, int kind, int first_rows,
     case DLS_ORDER_HOURGLASS:
       order_hourglass(n, vsym, cells);
       break;
-    case DLS_ORDER_HEURISTIC: {
+    case DLS_ORDER_HEURISTIC:
+    case DLS_ORDER_HEURISTIC_SQ: {
       std::vector<std::pair<int, int>> row0;
       for (int j = 0; j < (vsym ? n / 2 : n); ++j) row0.push_back({0, j});
-      order_heuristic(n, diag, vsym, row0, cells);
+      order_heuristic(n, diag, vsym, row0, cells, kind == DLS_ORDER_HEURISTIC_SQ);
       break;
     }
     default:
@@ -314,8 +319,8 @@ int dls_order_complete(int n, uint32_t flags, const uint8_t *order, int keep,
   const int w = vsym ? n / 2 : n;
   std::vector<std::pair<int, int>> kept, cells;
   for (int t = 0; t < keep; ++t) kept.push_back({info.i[t], info.j[t]});
-  if (kind == DLS_ORDER_HEURISTIC) {
-    order_heuristic(n, diag, vsym, kept, cells);
+  if (kind == DLS_ORDER_HEURISTIC || kind == DLS_ORDER_HEURISTIC_SQ) {
+    order_heuristic(n, diag, vsym, kept, cells, kind == DLS_ORDER_HEURISTIC_SQ);
   } else if (kind == DLS_ORDER_MD_AD_ROWS || kind == DLS_ORDER_ROW_MAJOR) {
     bool used[DLS_MAX_N][DLS_MAX_N] = {};
     for (auto &c : kept) {

@@ -214,10 +214,12 @@ def test_config3_order8_diag64_sampled_against_oracle(dls):
     assert (c3 == c).all()
 
 
-def test_bench_configuration_against_oracle(dls):
+@pytest.mark.parametrize("suffix", ["heuristic", "heuristic_sq"])
+def test_bench_configuration_against_oracle(dls, suffix):
     """The order-8 workload exactly as the benchmark times it: split 28 cells
     into the order (row 0, both diagonals, the rest of row 1), the Section
-    2.3 order after the split, counted through a CUDA-graph plan with the
+    2.3 order (or its squared-count variant) after the split, counted
+    through a CUDA-graph plan with the
     default launch and the 64-thread blocks the autotuner picks; the prefixes
     of 4 seed-chosen diagonals of the 64 against the oracle (its own order
     and prefixes)."""
@@ -228,8 +230,9 @@ def test_bench_configuration_against_oracle(dls):
     ident = np.arange(n, dtype=np.uint8)[None]
     diags, _ = dls.extend_prefixes(n, D, order0, ident, n + (n - 1))
     picks = dls_inputs.choose(len(diags), 64, 0)         # the benchmark's seed-0 draw
-    order, pre, par = autotune.build_problem(n, D, order0, diags[picks], depth, "heuristic")
-    o_order = orders.heuristic_complete(n, orders.md_ad_rows(n)[:depth])
+    order, pre, par = autotune.build_problem(n, D, order0, diags[picks], depth, suffix)
+    o_order = orders.heuristic_complete(n, orders.md_ad_rows(n)[:depth],
+                                        squares=suffix == "heuristic_sq")
     assert [tuple(map(int, x)) for x in order] == o_order
     o_diags, _ = oracle.extend(n, D, orders.md_ad_rows(n), np.array([orders.identity(n)],
                                                                         np.uint8), n + (n - 1))

@@ -82,6 +82,10 @@ def test_order_completion_matches_oracle(dls, n, flags, keep):
     got = [tuple(c) for c in dls.order_complete(n, flags, base, keep, dls.ORDER_HEURISTIC)]
     ref = orders.heuristic_complete(n, [tuple(c) for c in base[:keep]], bool(flags & D), vs)
     assert got == ref
+    sq = [tuple(c) for c in dls.order_complete(n, flags, base, keep, dls.ORDER_HEURISTIC_SQ)]
+    assert sq == orders.heuristic_complete(n, [tuple(c) for c in base[:keep]], bool(flags & D),
+                                           vs, squares=True)
+    assert sorted(sq) == sorted(got) and sq[:keep] == got[:keep]
     assert got[:keep] == [tuple(c) for c in base[:keep]]
     assert sorted(got) == sorted(orders.row_major(n, vsym=vs))
     got2 = [tuple(c) for c in dls.order_complete(n, flags, base, keep, dls.ORDER_MD_AD_ROWS)]
@@ -92,10 +96,29 @@ def test_order_completion_keeps_counts(dls):
     for n, flags, keep in ((6, D, 10), (7, D, 14), (6, D | V, 6)):
         vs = bool(flags & V)
         base = dls.fill_order(n, flags)
-        h = [tuple(c) for c in dls.order_complete(n, flags, base, keep, dls.ORDER_HEURISTIC)]
         ref = oracle.count(n, flags, orders.md_ad_rows(n, vsym=vs), orders.identity(n, vs))
-        got = oracle.count(n, flags, h, orders.identity(n, vs))
-        assert got[0] == ref[0]
+        for kind in (dls.ORDER_HEURISTIC, dls.ORDER_HEURISTIC_SQ):
+            h = [tuple(c) for c in dls.order_complete(n, flags, base, keep, kind)]
+            got = oracle.count(n, flags, h, orders.identity(n, vs))
+            assert got[0] == ref[0]
+
+
+def test_squared_heuristic_searches_less_on_the_order8_split(dls):
+    # the squared-count variant of the Section 2.3 rule, after the order-8
+    # split of the benchmark (row 0, both diagonals, the rest of row 1):
+    # same count, fewer search nodes (oracle node counts on a few prefixes)
+    n, keep = 8, 28
+    base = dls.fill_order(n, D)
+    o_base = orders.md_ad_rows(n)
+    pre, _ = oracle.extend(n, D, o_base, np.array([orders.identity(n)], np.uint8), keep)
+    pre = pre[::max(1, len(pre) // 40)][:40]
+    h = orders.heuristic_complete(n, o_base[:keep])
+    q = orders.heuristic_complete(n, o_base[:keep], squares=True)
+    assert q == [tuple(c) for c in dls.order_complete(n, D, base, keep, dls.ORDER_HEURISTIC_SQ)]
+    ch, nh = oracle.count_many(n, D, h, pre, threads=4)
+    cq, nq = oracle.count_many(n, D, q, pre, threads=4)
+    assert (ch == cq).all() and ch.sum() > 0
+    assert nq.sum() < nh.sum()
 
 
 @pytest.mark.parametrize("n,flags,extra", [(6, D, 0), (6, D, 5), (6, D, 12), (7, D, 10),
