@@ -250,9 +250,10 @@ def timed_steps(launch_fn, stream, steps, flush):
     return [a.elapsed_time(b) / 1e3 for a, b in evs]
 
 
-def serving_leg(n_jobs, limit_s, seed=0):
+def serving_leg(n_jobs, limit_s, seed=0, **cfg):
     """Replays the seeded serving mix in real time against the
-    continuous-batching server; returns the 'serving' object of the line."""
+    continuous-batching server (dls_server_cfg fields in cfg); returns the
+    'serving' object of the line."""
     from paper_1709_02599_gb300 import serving
     specs = dls_inputs.serving_jobs(n_jobs, seed=seed)
     jobs = []
@@ -263,7 +264,7 @@ def serving_leg(n_jobs, limit_s, seed=0):
         flags, order, prefix = b
         jobs.append(dict(n=sp["n"], flags=flags, order=order, prefix=prefix,
                          arrival=sp["arrival"], rows=sp["rows"]))
-    srv = serving.Server()
+    srv = serving.Server(**cfg)
     # one untimed warm-up job so that the first epoch pays no start-up cost
     srv.submit(jobs[0]["n"], jobs[0]["flags"], jobs[0]["order"], jobs[0]["prefix"])
     srv.drain()

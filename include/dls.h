@@ -318,13 +318,18 @@ int dls_hourglass_classes(int n, uint32_t flags, const uint8_t *order, int len,
 /* A continuous-batching server for counting jobs of mixed order, flags and
  * prefix (the job answer is Count(prefix), as for dls_count).  Jobs are split
  * on the host into work items (the prefix split of Section 5.2, extended
- * until a job has items_per_job items), wait in arrival order, and are
- * admitted at an epoch boundary when a job slot, enough free chunks of the
- * device item arena (the memory budget) and queue room are free.  Each
- * dls_server_step() reads the results of the previous epoch, admits, and
- * launches one epoch: every lane of a resident grid resumes the search it
- * saved in device memory, or takes the next queued item of any job, runs
- * `budget` search iterations and saves what is unfinished.  Search stacks
+ * until a job has one item per lane, or more for a big job -- see
+ * item_nodes), wait in arrival order, and are
+ * admitted at an epoch boundary when a job slot and enough free chunks of the
+ * device item arena (the memory budget) are free; an admitted job's items
+ * are copied to the arena.  Each dls_server_step() reads the results of the
+ * previous epoch, admits, feeds the device work queue -- items for the idle
+ * lanes plus a backlog, in equal shares from every admitted job with items
+ * left, so a new job is served within an epoch or two even while a big one
+ * still has most of its items to go -- and launches one epoch: every lane of
+ * a resident grid resumes the search it saved in device memory, or takes the
+ * next queued item, runs `budget` search iterations and saves what is
+ * unfinished.  Search stacks
  * and per-job counters stay on the device; jobs that arrive while others run
  * share the GPU with them from the next epoch on.  One server uses one CUDA
  * stream of its own and is driven from one host thread at a time. */
@@ -332,16 +337,25 @@ typedef struct dls_server dls_server;
 
 typedef struct {
     int max_jobs;          /* device job slots (default 1024)                */
-    size_t arena_bytes;    /* device memory for queued items (default 64 MiB)*/
+    size_t arena_bytes;    /* device memory for the items of admitted jobs
+                              (default 256 MiB)                              */
     size_t chunk_bytes;    /* arena allocation unit (default 64 KiB)         */
     int64_t queue_items;   /* work-queue ring capacity (default 4 Mi)        */
     int max_order;         /* largest n a job may have (default 10)          */
     int budget;            /* search iterations per lane per epoch (4096)    */
     int block_threads;     /* 32..256 (default 128)                          */
     int blocks_per_sm;     /* 0 = as many as fit                             */
-    int items_per_job;     /* split target per job (0 = default: the number
-                              of lanes of the grid, so that one big job can
-                              occupy the whole GPU)                          */
+    int items_per_job;     /* most items a job is split into (0 = default:
+                              16 per lane of the grid, at most 4 Mi)         */
+    int min_backlog;       /* queue items kept beyond the idle lanes (default
+                              1024; twice the items taken in the last epoch
+                              when that is more)                             */
+    int64_t item_nodes;    /* search nodes aimed at per item (default 2^17):
+                              a job is split into one item per lane, or into
+                              its estimated nodes / item_nodes items if that
+                              is more (at most items_per_job), the estimate
+                              being Knuth's random-descent estimate of the
+                              size of its search tree (256 descents)         */
 } dls_server_cfg;
 
 typedef struct {
@@ -355,13 +369,16 @@ typedef struct {
 /* Fills *cfg with the defaults above. */
 void dls_server_default_cfg(dls_server_cfg *cfg);
 /* Allocates the server's device memory (cfg NULL = defaults) on the current
- * device.  Errors: BAD_ARG, NO_MEMORY, CUDA. */
+ * device and starts its worker threads (at most 4).  Errors: BAD_ARG,
+ * NO_MEMORY, CUDA. */
 int dls_server_create(const dls_server_cfg *cfg, dls_server **out);
 /* Queues a job (host arguments, copied; conventions as dls_count with one
- * prefix of `depth` bytes).  *job_id receives its id.  A job whose prefix is
- * invalid, or that leaves nothing to search, completes at once.  Errors:
- * INVALID_N (also n > max_order), BAD_ORDER, BAD_ARG, CAPACITY (the job's
- * items exceed the whole arena or queue). */
+ * prefix of `depth` bytes) and returns at once: *job_id receives its id, and
+ * the job is split into work items on one of the server's worker threads
+ * (never beyond half the arena, so every job can be admitted) before it
+ * waits for admission.  A job whose prefix is invalid, or that leaves
+ * nothing to search, completes without the GPU.  Errors: INVALID_N (also
+ * n > max_order), BAD_ORDER, BAD_ARG, NO_MEMORY. */
 int dls_server_submit(dls_server *srv, int n, uint32_t flags,
                       const uint8_t *order, int order_len,
                       const uint8_t *prefix, int depth, int64_t *job_id);

@@ -73,7 +73,9 @@ class ServerCfg(ctypes.Structure):
                 ("budget", ctypes.c_int),
                 ("block_threads", ctypes.c_int),
                 ("blocks_per_sm", ctypes.c_int),
-                ("items_per_job", ctypes.c_int)]
+                ("items_per_job", ctypes.c_int),
+                ("min_backlog", ctypes.c_int),
+                ("item_nodes", ctypes.c_int64)]
 
 
 class ServerStats(ctypes.Structure):

@@ -29,10 +29,12 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <condition_variable>
 #include <cstring>
 #include <deque>
 #include <map>
 #include <mutex>
+#include <thread>
 #include <vector>
 
 #include "dls_internal.h"
@@ -224,6 +226,8 @@ struct HostJob {
   int depth;                    // item length
   std::vector<uint8_t> items;   // n_items * depth
   int64_t n_items;
+  int64_t fed = 0;              // items appended to the device queue so far
+  size_t per_chunk = 0;         // items per arena chunk
   std::vector<int> chunks;
 };
 
@@ -249,8 +253,11 @@ struct dls_server {
   uint8_t *h_item_stage = nullptr;       // pinned, arena-sized staging
   uint2 *h_queue_stage = nullptr;        // pinned, queue-sized staging
   unsigned long long *h_zero = nullptr;
+  unsigned long long *h_head = nullptr;  // pinned readback of the queue head
   unsigned long long tail = 0;
-  int64_t outstanding = 0;               // queued items of active jobs
+  unsigned long long head_known = 0;     // queue head after the last epoch
+  unsigned long long taken_last = 0;     // items handed out in the last epoch
+  int64_t finished_done = 0;             // items of completed jobs
   std::vector<int> free_slots;
   std::vector<int> free_chunks;
   std::vector<HostJob *> active;         // by slot
@@ -261,7 +268,135 @@ struct dls_server {
   cudaEvent_t ev = nullptr;
   dls_server_stats stats;
   std::mutex mu;
+  // submitted jobs are split on worker threads, off the caller's path
+  std::deque<HostJob *> to_split;
+  int64_t splitting = 0;                 // submitted, not yet pending or done
+  std::condition_variable cv;
+  bool stopping = false;
+  std::vector<std::thread> workers;
 };
+
+// splitmix64 (Steele, Lea, Flood 2014): the server's counter-based generator
+// for the random probes below, keyed by (job id, probe, position).
+static uint64_t splitmix64(uint64_t x) {
+  x += 0x9e3779b97f4a7c15ull;
+  x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+  x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+  return x ^ (x >> 31);
+}
+
+// Knuth's estimate of the size of the search below a prefix (D. E. Knuth,
+// "Estimating the efficiency of backtrack programs", 1975): a random descent
+// along the order takes, at each cell, the product of the numbers of
+// admissible values met so far as its estimate of the nodes at that depth
+// and adds them up, stopping at a dead end or the last cell; the mean over
+// descents is an unbiased estimate of the number of search nodes.  (The
+// same estimate of the completions alone is nearly always 0 here: most
+// descents end at a dead end.)  Used only to choose how finely a job is
+// split -- the counts never depend on it.
+static double estimate_nodes(const OrderInfo &info, const uint8_t *prefix, int depth,
+                             uint64_t key, int probes) {
+  HostState base;
+  base.init(info);
+  for (int t = 0; t < depth; ++t)
+    if (!base.place(t, prefix[t])) return 0.0;
+  double sum = 0.0;
+  for (int pr = 0; pr < probes; ++pr) {
+    HostState s = base;
+    double w = 1.0;
+    for (int t = depth; t < info.len; ++t) {
+      const uint32_t c = s.candidates(t);
+      const int k = __builtin_popcount(c);
+      w *= (double)k;
+      sum += w;
+      if (k == 0 || t == info.len - 1) break;
+      const uint64_t r = splitmix64(key ^ splitmix64(((uint64_t)pr << 32) | (uint64_t)t));
+      uint32_t v = c;
+      for (int q = (int)(r % (uint64_t)k); q > 0; --q) v &= v - 1u;
+      s.toggle(t, v & (0u - v));
+    }
+  }
+  return sum / probes;
+}
+
+// Splits a submitted job into work items (worker thread, no lock held but
+// at the end): the prefix is extended a few cells deeper (Section 5.2), at
+// most to two cells before the end, until there are enough items -- one per
+// lane, or more for a big job: its estimated search nodes / item_nodes, at
+// most items_per_job -- so that no item of a big job is long, while small
+// jobs are not cut finer than the grid needs; and never beyond half the
+// item arena, so that every job can be admitted.  Then the job waits for
+// admission (or completes at once if nothing is left for the GPU).
+static void sv_split(dls_server *s, HostJob *j) {
+  const int n = j->n;
+  const uint32_t flags = j->flags;
+  const int order_len = (int)(j->order.size() / 2);
+  const uint8_t *order = j->order.data();
+  OrderInfo info;
+  int rc = validate_order(n, flags, order, order_len, &info);
+  std::vector<uint8_t> cur;
+  cur.swap(j->items);
+  int d = j->depth;
+  int64_t m = 0;
+  if (rc == DLS_OK && !vsym_all_zero(n, flags)) {
+    int64_t need = 0;
+    rc = dls_extend_prefixes(n, flags, order, order_len, cur.data(), d, 1, d, nullptr, 0,
+                             nullptr, &need);
+    m = (rc == DLS_OK || rc == DLS_ERR_CAPACITY) ? need : 0;  // 1 if the prefix is valid
+    int64_t target = std::min<int64_t>(s->G, s->cfg.items_per_job);
+    if (m > 0) {
+      const double est = estimate_nodes(info, cur.data(), d, splitmix64((uint64_t)j->id), 256);
+      const double want = est / (double)s->cfg.item_nodes;
+      if (want > (double)target)
+        target = (int64_t)std::min<double>(want, (double)s->cfg.items_per_job);
+    }
+    std::vector<uint8_t> next;
+    while (m > 0 && m < target && d < order_len - 2) {
+      rc = dls_extend_prefixes(n, flags, order, order_len, cur.data(), d, m, d + 1,
+                               nullptr, 0, nullptr, &need);
+      if ((rc != DLS_OK && rc != DLS_ERR_CAPACITY) ||
+          (double)need * (d + 1) > 0.5 * (double)s->cfg.arena_bytes)
+        break;
+      next.assign((size_t)need * (d + 1), 0);
+      int64_t got = 0;
+      rc = dls_extend_prefixes(n, flags, order, order_len, cur.data(), d, m, d + 1,
+                               next.data(), need, nullptr, &got);
+      if (rc) break;
+      cur.swap(next);
+      ++d;
+      m = got;
+    }
+  }
+  if (m == 0) cur.clear();
+  j->depth = d;
+  j->n_items = m;
+  j->items.swap(cur);
+  std::lock_guard<std::mutex> g(s->mu);
+  s->splitting--;
+  if (m == 0 || d == order_len) {
+    // nothing for the GPU: no valid extension, or complete assignments
+    s->done.push_back({j->id, (uint64_t)(d == order_len ? m : 0)});
+    s->stats.completed++;
+    s->stats.squares += (uint64_t)(d == order_len ? m : 0);
+    delete j;
+    return;
+  }
+  s->pending.push_back(j);
+}
+
+static void sv_worker(dls_server *s) {
+  for (;;) {
+    HostJob *j = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      s->cv.wait(lk, [&] { return s->stopping || !s->to_split.empty(); });
+      if (s->stopping) return;
+      j = s->to_split.front();
+      s->to_split.pop_front();
+    }
+    sv_split(s, j);
+  }
+}
 
 static int sv_fail(cudaError_t e) {
   set_cuda_error(cudaGetErrorString(e));
@@ -269,6 +404,13 @@ static int sv_fail(cudaError_t e) {
 }
 
 static void sv_free(dls_server *s) {
+  {
+    std::lock_guard<std::mutex> g(s->mu);
+    s->stopping = true;
+  }
+  s->cv.notify_all();
+  for (auto &t : s->workers) t.join();
+  for (auto *j : s->to_split) delete j;
   if (s->ev) cudaEventDestroy(s->ev);
   if (s->stream) cudaStreamDestroy(s->stream);
   cudaFree(s->d_jobs);
@@ -284,6 +426,7 @@ static void sv_free(dls_server *s) {
   cudaFreeHost(s->h_item_stage);
   cudaFreeHost(s->h_queue_stage);
   cudaFreeHost(s->h_zero);
+  cudaFreeHost(s->h_head);
   for (auto *j : s->active) delete j;
   for (auto *j : s->pending) delete j;
   delete s;
@@ -295,7 +438,7 @@ void dls_server_default_cfg(dls_server_cfg *cfg) {
   if (!cfg) return;
   std::memset(cfg, 0, sizeof(*cfg));
   cfg->max_jobs = 1024;
-  cfg->arena_bytes = size_t(64) << 20;
+  cfg->arena_bytes = size_t(256) << 20;
   cfg->chunk_bytes = size_t(64) << 10;
   cfg->queue_items = int64_t(1) << 22;
   cfg->max_order = 10;
@@ -303,6 +446,8 @@ void dls_server_default_cfg(dls_server_cfg *cfg) {
   cfg->block_threads = 128;
   cfg->blocks_per_sm = 0;
   cfg->items_per_job = 0;
+  cfg->min_backlog = 1024;
+  cfg->item_nodes = int64_t(1) << 17;
 }
 
 int dls_server_create(const dls_server_cfg *cfg_in, dls_server **out) {
@@ -314,7 +459,8 @@ int dls_server_create(const dls_server_cfg *cfg_in, dls_server **out) {
   if (cfg.max_jobs < 1 || cfg.chunk_bytes < 256 || cfg.arena_bytes < cfg.chunk_bytes ||
       cfg.queue_items < 1 || cfg.max_order < 1 || cfg.max_order > DLS_MAX_N ||
       cfg.budget < 1 || cfg.block_threads < 32 || cfg.block_threads > 256 ||
-      cfg.block_threads % 32 || cfg.items_per_job < 0 || cfg.blocks_per_sm < 0)
+      cfg.block_threads % 32 || cfg.items_per_job < 0 || cfg.blocks_per_sm < 0 ||
+      cfg.min_backlog < 1 || cfg.item_nodes < 1)
     return DLS_ERR_BAD_ARG;
   dls_server *s = new (std::nothrow) dls_server();
   if (!s) return DLS_ERR_NO_MEMORY;
@@ -341,8 +487,10 @@ int dls_server_create(const dls_server_cfg *cfg_in, dls_server **out) {
     if (cfg.blocks_per_sm) per_sm = std::min(per_sm, cfg.blocks_per_sm);
     s->grid = sms * per_sm;
     s->G = (long long)s->grid * cfg.block_threads;
-    // by default a job is split until it could occupy every lane
-    if (s->cfg.items_per_job == 0) s->cfg.items_per_job = (int)std::min<long long>(s->G, 1 << 20);
+    // by default a job may be split into up to 16 items per lane: a big
+    // job's slowest item, which bounds its latency, is then a small part of it
+    if (s->cfg.items_per_job == 0)
+      s->cfg.items_per_job = (int)std::min<long long>(16 * s->G, 1 << 22);
   }
   if (e == cudaSuccess) e = cudaMalloc(&s->d_jobs, sizeof(ServeJob) * cfg.max_jobs);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_count, sizeof(unsigned long long) * cfg.max_jobs);
@@ -357,6 +505,7 @@ int dls_server_create(const dls_server_cfg *cfg_in, dls_server **out) {
   if (e == cudaSuccess) e = cudaMallocHost(&s->h_item_stage, n_chunks * cfg.chunk_bytes);
   if (e == cudaSuccess) e = cudaMallocHost(&s->h_queue_stage, sizeof(uint2) * cfg.queue_items);
   if (e == cudaSuccess) e = cudaMallocHost(&s->h_zero, 64);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_head, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemsetAsync(s->d_head, 0, sizeof(unsigned long long), s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->d_slots, 0, sizeof(uint32_t) * s->G, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
@@ -366,9 +515,13 @@ int dls_server_create(const dls_server_cfg *cfg_in, dls_server **out) {
     return rc;
   }
   std::memset(s->h_zero, 0, 64);
+  *s->h_head = 0ull;
   for (int k = cfg.max_jobs - 1; k >= 0; --k) s->free_slots.push_back(k);
   for (int k = (int)n_chunks - 1; k >= 0; --k) s->free_chunks.push_back(k);
   s->active.assign(cfg.max_jobs, nullptr);
+  const unsigned hw = std::thread::hardware_concurrency();
+  const int n_workers = (int)std::max(1u, std::min(4u, hw ? hw / 2 : 1u));
+  for (int w = 0; w < n_workers; ++w) s->workers.emplace_back(sv_worker, s);
   s->stats.lanes = s->G;
   s->stats.device_bytes = sizeof(ServeJob) * cfg.max_jobs + 12u * cfg.max_jobs +
                           n_chunks * cfg.chunk_bytes + sizeof(uint2) * cfg.queue_items +
@@ -391,68 +544,17 @@ int dls_server_submit(dls_server *s, int n, uint32_t flags, const uint8_t *order
   j->n = n;
   j->flags = flags;
   j->order.assign(order, order + 2 * order_len);
-  // split the prefix a few cells deeper (Section 5.2), at most to two cells
-  // before the end, until there are items_per_job items or more
-  std::vector<uint8_t> cur(prefix, prefix + depth);
-  int d = depth;
-  int64_t m = 1;
-  if (vsym_all_zero(n, flags)) {
-    m = 0;
-    cur.clear();
-  } else {
-    std::vector<uint8_t> next;
-    int64_t need = 0;
-    rc = dls_extend_prefixes(n, flags, order, order_len, cur.data(), d, 1, d, nullptr, 0,
-                             nullptr, &need);
-    if (rc != DLS_OK && rc != DLS_ERR_CAPACITY) {
-      delete j;
-      return rc;
-    }
-    m = need;  // 1 if the prefix is valid, else 0
-    if (m == 0) cur.clear();
-    while (m > 0 && m < s->cfg.items_per_job && d < order_len - 2) {
-      rc = dls_extend_prefixes(n, flags, order, order_len, cur.data(), d, m, d + 1,
-                               nullptr, 0, nullptr, &need);
-      if (rc != DLS_OK && rc != DLS_ERR_CAPACITY) {
-        delete j;
-        return rc;
-      }
-      next.assign((size_t)need * (d + 1), 0);
-      int64_t got = 0;
-      rc = dls_extend_prefixes(n, flags, order, order_len, cur.data(), d, m, d + 1,
-                               next.data(), need, nullptr, &got);
-      if (rc) {
-        delete j;
-        return rc;
-      }
-      cur.swap(next);
-      ++d;
-      m = got;
-    }
+  j->items.assign(prefix, prefix + depth);  // the prefix, until it is split
+  j->depth = depth;
+  {
+    std::lock_guard<std::mutex> g(s->mu);
+    j->id = s->next_id++;
+    *job_id = j->id;
+    s->stats.submitted++;
+    s->to_split.push_back(j);
+    s->splitting++;
   }
-  j->depth = d;
-  j->n_items = m;
-  j->items.swap(cur);
-  std::lock_guard<std::mutex> g(s->mu);
-  j->id = s->next_id++;
-  *job_id = j->id;
-  s->stats.submitted++;
-  if (m == 0 || d == order_len) {
-    // nothing for the GPU: no valid extension, or complete assignments
-    s->done.push_back({j->id, (uint64_t)(d == order_len ? m : 0)});
-    s->stats.completed++;
-    s->stats.squares += (uint64_t)(d == order_len ? m : 0);
-    delete j;
-    return DLS_OK;
-  }
-  const size_t per_chunk = s->cfg.chunk_bytes / (size_t)d;
-  const size_t chunks = (size_t)((m + (int64_t)per_chunk - 1) / (int64_t)per_chunk);
-  if (chunks > s->cfg.arena_bytes / s->cfg.chunk_bytes || m > s->cfg.queue_items) {
-    s->stats.submitted--;
-    delete j;
-    return DLS_ERR_CAPACITY;
-  }
-  s->pending.push_back(j);
+  s->cv.notify_one();
   return DLS_OK;
 }
 
@@ -462,13 +564,15 @@ static int sv_collect(dls_server *s) {
   cudaError_t e = cudaEventSynchronize(s->ev);
   if (e != cudaSuccess) return sv_fail(e);
   s->in_flight = false;
+  s->taken_last = *s->h_head - s->head_known;
+  s->head_known = *s->h_head;
   for (int slot = 0; slot < s->cfg.max_jobs; ++slot) {
     HostJob *j = s->active[slot];
     if (j == nullptr || s->h_left[slot] != 0u) continue;
     s->done.push_back({j->id, (uint64_t)s->h_count[slot]});
     s->stats.completed++;
     s->stats.squares += s->h_count[slot];
-    s->outstanding -= j->n_items;
+    s->finished_done += j->n_items;
     for (int c : j->chunks) s->free_chunks.push_back(c);
     s->free_slots.push_back(slot);
     s->active[slot] = nullptr;
@@ -492,9 +596,7 @@ int dls_server_step(dls_server *s) {
     HostJob *j = s->pending.front();
     const size_t per_chunk = s->cfg.chunk_bytes / (size_t)j->depth;
     const size_t need = (size_t)((j->n_items + (int64_t)per_chunk - 1) / (int64_t)per_chunk);
-    if (s->free_slots.empty() || s->free_chunks.size() < need ||
-        s->outstanding + j->n_items > s->cfg.queue_items)
-      break;
+    if (s->free_slots.empty() || s->free_chunks.size() < need) break;
     s->pending.pop_front();
     j->slot = s->free_slots.back();
     s->free_slots.pop_back();
@@ -534,18 +636,56 @@ int dls_server_step(dls_server *s) {
                   (size_t)take * j->depth);
       e = cudaMemcpyAsync(s->d_arena + base, s->h_item_stage + base, (size_t)take * j->depth,
                           cudaMemcpyHostToDevice, s->stream);
-      for (int64_t t = 0; t < take; ++t) {
-        const unsigned long long pos = (q0 + qn) % (unsigned long long)s->cfg.queue_items;
-        s->h_queue_stage[pos] = make_uint2((unsigned)j->slot, (unsigned)(base + (size_t)t * j->depth));
-        ++qn;
-      }
       k += take;
     }
     if (e != cudaSuccess) return sv_fail(e);
     std::vector<uint8_t>().swap(j->items);
-    s->outstanding += j->n_items;
+    j->per_chunk = per_chunk;
+    j->fed = 0;
     s->active[j->slot] = j;
     s->stats.admitted++;
+  }
+  // feed the device queue: enough items for the lanes that are idle plus a
+  // margin for those that free up during the epoch (twice the items taken
+  // in the last epoch, at least min_backlog), in equal shares from every
+  // active job with items left -- so a job admitted now is served within an
+  // epoch or two even while a big job still has most of its items left
+  {
+    int64_t finished = s->finished_done;
+    std::vector<HostJob *> feed;
+    for (int slot = 0; slot < s->cfg.max_jobs; ++slot) {
+      HostJob *j = s->active[slot];
+      if (j == nullptr) continue;
+      finished += j->n_items - (int64_t)s->h_left[slot];
+      if (j->fed < j->n_items) feed.push_back(j);
+    }
+    const long long busy = (long long)s->head_known - (long long)finished;
+    const long long idle = std::max(0ll, (long long)s->G - std::max(0ll, busy));
+    const long long backlog = (long long)(s->tail - s->head_known);
+    const long long margin = std::max<long long>(s->cfg.min_backlog, 2 * (long long)s->taken_last);
+    const long long room = (long long)s->cfg.queue_items - backlog;
+    long long want = std::min(room, idle + margin - backlog);
+    while (want > 0 && !feed.empty()) {
+      const long long share = std::max(1ll, want / (long long)feed.size());
+      std::vector<HostJob *> left;
+      for (HostJob *j : feed) {
+        const long long take = std::min({share, want, (long long)(j->n_items - j->fed)});
+        for (long long t = 0; t < take; ++t) {
+          const int64_t item = j->fed + t;
+          const size_t base = (size_t)j->chunks[(size_t)(item / (int64_t)j->per_chunk)] *
+                                  s->cfg.chunk_bytes +
+                              (size_t)(item % (int64_t)j->per_chunk) * j->depth;
+          const unsigned long long pos = (q0 + qn) % (unsigned long long)s->cfg.queue_items;
+          s->h_queue_stage[pos] = make_uint2((unsigned)j->slot, (unsigned)base);
+          ++qn;
+        }
+        j->fed += take;
+        want -= take;
+        if (j->fed < j->n_items) left.push_back(j);
+        if (want <= 0) break;
+      }
+      feed.swap(left);
+    }
   }
   // new queue entries (the ring may wrap)
   if (qn) {
@@ -586,6 +726,9 @@ int dls_server_step(dls_server *s) {
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(s->h_left, s->d_left, sizeof(unsigned int) * s->cfg.max_jobs,
                         cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s->h_head, s->d_head, sizeof(unsigned long long),
+                        cudaMemcpyDeviceToHost, s->stream);
   if (e == cudaSuccess) e = cudaEventRecord(s->ev, s->stream);
   if (e != cudaSuccess) return sv_fail(e);
   s->in_flight = true;
@@ -611,7 +754,7 @@ int dls_server_get_stats(dls_server *s, dls_server_stats *out) {
   if (s == nullptr || out == nullptr) return DLS_ERR_BAD_ARG;
   std::lock_guard<std::mutex> g(s->mu);
   *out = s->stats;
-  out->pending = (int64_t)s->pending.size();
+  out->pending = (int64_t)s->pending.size() + s->splitting;
   int64_t act = 0;
   for (auto *j : s->active) act += (j != nullptr);
   out->active = act;
