@@ -21,8 +21,8 @@ def test_autotune_small_problem(dls, tmp_path, monkeypatch):
     base = base[::5]
     best = autotune.tune(n, D, order, base, [n + 8, n + 10], shapes=autotune.SHAPES[:3])
     assert not best["cached"]
-    assert best["depth"] in (n + 8, n + 10) and best["suffix"] in ("given", "heuristic")
-    assert len(best["trials"]) == 4 + 2
+    assert best["depth"] in (n + 8, n + 10) and best["suffix"] in autotune.SUFFIXES
+    assert len(best["trials"]) == 2 * len(autotune.SUFFIXES) + 2
     # the chosen setting gives the oracle's per-prefix counts
     o, pre, _ = autotune.build_problem(n, D, order, base, best["depth"], best["suffix"])
     c = dls.count(n, D, o, torch.from_numpy(pre).cuda(), launch=dls.Launch(**best["launch"]))
