@@ -298,7 +298,7 @@ def reference_arm(args):
         return 0
     threads = os.cpu_count() or 1
     spec = SPECS[args.workload]
-    o_order, pre = spec.oracle_sample(0, 1, spec.default_depth, "heuristic")
+    o_order, pre = spec.oracle_sample(0, 1, spec.default_depth, "heuristic_sq")
     for _ in range(args.warmup):
         run_oracle(spec, o_order, pre, threads)
     sq = 0
@@ -318,7 +318,8 @@ def reference_arm(args):
                    "prefixes_per_step": int(len(pre))},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": "all %d prefixes of 1 seed-chosen base prefix of the %d, "
-                                   "cells after the split in the Section 2.3 order"
+                                   "cells after the split in the squared-count Section 2.3 "
+                                   "order"
                                    % (len(pre), spec.units)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
