@@ -324,9 +324,10 @@ int dls_hourglass_classes(int n, uint32_t flags, const uint8_t *order, int len,
  * device item arena (the memory budget) are free; an admitted job's items
  * are copied to the arena.  Each dls_server_step() reads the results of the
  * previous epoch, admits, feeds the device work queue -- items for the idle
- * lanes plus a backlog, in equal shares from every admitted job with items
- * left, so a new job is served within an epoch or two even while a big one
- * still has most of its items to go -- and launches one epoch: every lane of
+ * lanes plus a backlog, first from the admitted job with the least estimated
+ * work not yet fed (shortest remaining work first), so a new job is served
+ * within an epoch or two even while a big one still has most of its items to
+ * go -- and launches one epoch: every lane of
  * a resident grid resumes the search it saved in device memory, or takes the
  * next queued item, runs `budget` search iterations and saves what is
  * unfinished.  Search stacks

@@ -228,6 +228,7 @@ struct HostJob {
   int64_t n_items;
   int64_t fed = 0;              // items appended to the device queue so far
   size_t per_chunk = 0;         // items per arena chunk
+  double est_nodes = 0.0;       // estimated search nodes of the whole job
   std::vector<int> chunks;
 };
 
@@ -346,6 +347,7 @@ static void sv_split(dls_server *s, HostJob *j) {
     int64_t target = std::min<int64_t>(s->G, s->cfg.items_per_job);
     if (m > 0) {
       const double est = estimate_nodes(info, cur.data(), d, splitmix64((uint64_t)j->id), 256);
+      j->est_nodes = est;
       const double want = est / (double)s->cfg.item_nodes;
       if (want > (double)target)
         target = (int64_t)std::min<double>(want, (double)s->cfg.items_per_job);
@@ -647,9 +649,11 @@ int dls_server_step(dls_server *s) {
   }
   // feed the device queue: enough items for the lanes that are idle plus a
   // margin for those that free up during the epoch (twice the items taken
-  // in the last epoch, at least min_backlog), in equal shares from every
-  // active job with items left -- so a job admitted now is served within an
-  // epoch or two even while a big job still has most of its items left
+  // in the last epoch, at least min_backlog), taken first from the admitted
+  // job with the least estimated work not yet fed (shortest remaining work
+  // first) -- so a job admitted now is served within an epoch or two even
+  // while a big job still has most of its items left, and of two big jobs
+  // one finishes first instead of both finishing last
   {
     int64_t finished = s->finished_done;
     std::vector<HostJob *> feed;
@@ -665,26 +669,26 @@ int dls_server_step(dls_server *s) {
     const long long margin = std::max<long long>(s->cfg.min_backlog, 2 * (long long)s->taken_last);
     const long long room = (long long)s->cfg.queue_items - backlog;
     long long want = std::min(room, idle + margin - backlog);
-    while (want > 0 && !feed.empty()) {
-      const long long share = std::max(1ll, want / (long long)feed.size());
-      std::vector<HostJob *> left;
-      for (HostJob *j : feed) {
-        const long long take = std::min({share, want, (long long)(j->n_items - j->fed)});
-        for (long long t = 0; t < take; ++t) {
-          const int64_t item = j->fed + t;
-          const size_t base = (size_t)j->chunks[(size_t)(item / (int64_t)j->per_chunk)] *
-                                  s->cfg.chunk_bytes +
-                              (size_t)(item % (int64_t)j->per_chunk) * j->depth;
-          const unsigned long long pos = (q0 + qn) % (unsigned long long)s->cfg.queue_items;
-          s->h_queue_stage[pos] = make_uint2((unsigned)j->slot, (unsigned)base);
-          ++qn;
-        }
-        j->fed += take;
-        want -= take;
-        if (j->fed < j->n_items) left.push_back(j);
-        if (want <= 0) break;
+    auto unfed_work = [](const HostJob *j) {
+      return j->est_nodes * (double)(j->n_items - j->fed) / (double)j->n_items;
+    };
+    std::stable_sort(feed.begin(), feed.end(), [&](const HostJob *a, const HostJob *b) {
+      return unfed_work(a) < unfed_work(b);
+    });
+    for (HostJob *j : feed) {
+      if (want <= 0) break;
+      const long long take = std::min(want, (long long)(j->n_items - j->fed));
+      for (long long t = 0; t < take; ++t) {
+        const int64_t item = j->fed + t;
+        const size_t base = (size_t)j->chunks[(size_t)(item / (int64_t)j->per_chunk)] *
+                                s->cfg.chunk_bytes +
+                            (size_t)(item % (int64_t)j->per_chunk) * j->depth;
+        const unsigned long long pos = (q0 + qn) % (unsigned long long)s->cfg.queue_items;
+        s->h_queue_stage[pos] = make_uint2((unsigned)j->slot, (unsigned)base);
+        ++qn;
       }
-      feed.swap(left);
+      j->fed += take;
+      want -= take;
     }
   }
   // new queue entries (the ring may wrap)
