@@ -185,8 +185,10 @@ __device__ __forceinline__ bool snap_step(SnapLane &s, const Geo &g, const SnapS
   st.sw[(s.sp + 1) * (int)B] = snap_pack<VSYM>(DG ? dg0 : 0u, s.p, Lr);
   // a dead end resumes the entry just written if candidates remain at p,
   // else the deepest live one (read back after the write; used only on a
-  // dead end)
-  const int rd = keep ? s.sp + 1 : s.sp;
+  // dead end).  A lane that finishes -- no candidate left, no live entry --
+  // reads the entry just written as well, so that every position read back
+  // is a valid one (it indexes the position table below).
+  const int rd = (keep || s.sp <= s.bot) ? s.sp + 1 : s.sp;
   const uint4 ea = st.sa[rd * (int)B];
   const uint32_t ew = st.sw[rd * (int)B];
   const bool push = keep && !dead;
