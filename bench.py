@@ -52,10 +52,10 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) per prefix of k_snapshot on the order-8 workload,
 # per split depth: ncu captures of 16 of the 64 diagonals, squared-count
 # order after the split (depth 25: 149 590 prefixes, 4.953 MB read; depth
-# 28: 273 038 prefixes, 9.844 MB read; 0 written while the kernel ran),
+# 28: 273 038 prefixes, 9.893 MB read; 0 written while the kernel ran),
 # scaled per prefix; the profile summary under profiles/ gives the commands
-TRAFFIC_PER_PREFIX = {("dls8_diag64", "k_snapshot", 25): 4.952832e6 / 149590,
-                      ("dls8_diag64", "k_snapshot", 28): 9.843968e6 / 273038}
+TRAFFIC_PER_PREFIX = {("dls8_diag64", "k_snapshot", 25): 4.953088e6 / 149590,
+                      ("dls8_diag64", "k_snapshot", 28): 9.892864e6 / 273038}
 
 
 def parse():
