@@ -214,6 +214,13 @@ typedef struct {
                              positions after the prefix whose cell is not
                              forced by a line with all other cells earlier;
                              0 = snapshots where they apply (default)        */
+    int lookahead;        /* 1 = lookahead (Section 2.4.2) in the persistent
+                             snapshot search: a placement after which the cell
+                             after the next one has no candidate is a dead end
+                             at once; only where no cell after the prefix lies
+                             on a diagonal and without DLS_VSYM (BAD_ARG
+                             otherwise); same counts, fewer nodes.  0 = off
+                             (default)                                       */
 } dls_launch_t;
 
 /* What a dls_count_ex call with this shape runs. */

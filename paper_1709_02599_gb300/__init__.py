@@ -35,11 +35,12 @@ class Launch:
     check_every: int = 0
     words: int = 0
     stack: int = 0
+    lookahead: int = 0
 
     def c(self):
         return _lib.LaunchT(self.kernel, self.block_threads, self.blocks_per_sm,
                             self.lanes_per_prefix, self.split_pos, self.donate,
-                            self.check_every, self.words, self.stack)
+                            self.check_every, self.words, self.stack, self.lookahead)
 
 
 def lib():

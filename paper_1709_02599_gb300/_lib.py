@@ -52,7 +52,8 @@ class LaunchT(ctypes.Structure):
                 ("donate", ctypes.c_int),
                 ("check_every", ctypes.c_int),
                 ("words", ctypes.c_int),
-                ("stack", ctypes.c_int)]
+                ("stack", ctypes.c_int),
+                ("lookahead", ctypes.c_int)]
 
 
 class LaunchInfo(ctypes.Structure):

@@ -28,6 +28,8 @@ SHAPES = [
     {},
     {"block_threads": 64},
     {"block_threads": 256},
+    {"lookahead": 1},
+    {"lookahead": 1, "block_threads": 64},
     {"check_every": 16},
     {"stack": 1},
     {"words": 1},
@@ -137,10 +139,16 @@ def tune(n, flags, order, base, depths, suffixes=("given", "heuristic", "heurist
     for k in list(built):
         if k != (best["depth"], best["suffix"]):
             del built[k]
+    from . import DlsError
     for sh in shapes:
         if not sh:
             continue
-        sec, tot = time_plan(n, flags, o, d_pre, Launch(**sh), reps)
+        try:
+            sec, tot = time_plan(n, flags, o, d_pre, Launch(**sh), reps)
+        except DlsError as e:
+            if e.code != 3:      # a shape that does not apply to this problem
+                raise
+            continue
         if tot != total_ref:
             raise RuntimeError("autotune: totals differ between trials")
         trials.append({"depth": best["depth"], "suffix": best["suffix"], "launch": sh,

@@ -420,7 +420,7 @@ __device__ void snap_donate(SnapLane &s, bool &busy, const KParams &p, const Sna
 //                [stack: (cap + 2) * B entries of 16 bytes, then as many of 4]
 __device__ __forceinline__ void snap_setup(const KParams &p, int diag, uint32_t *smem,
                                            const Cell *&tbl, SnapTable &tb, SnapStack &st,
-                                           SnapLane &s) {
+                                           SnapLane &s, bool lookahead) {
   const unsigned B = blockDim.x;
   const int rows = (p.order_len + 31) & ~31;
   Cell *t = reinterpret_cast<Cell *>(smem);
@@ -431,6 +431,12 @@ __device__ __forceinline__ void snap_setup(const KParams &p, int diag, uint32_t 
     const int nx = min(idx + 1, p.order_len - 1);
     snap_row(p.g.n, diag != 0, p.wr, p.wc, p.ci[idx], p.cj[idx], p.ci[nx], p.cj[nx], tsh[idx],
              tdm[idx]);
+    if (lookahead) {
+      // the cell two positions on (the last cell stands in past the end;
+      // the lookahead is not used at the last cell)
+      const int n2 = min(idx + 2, p.order_len - 1);
+      tdm[idx] = make_uint2((uint32_t)(p.ci[n2] * p.wr), (uint32_t)(p.cj[n2] * p.wc));
+    }
   }
   uint4 *sa0 = reinterpret_cast<uint4 *>(tdm + rows);
   st.sa = sa0 + threadIdx.x;
@@ -466,7 +472,7 @@ __global__ void __launch_bounds__(512)
   SnapTable tb;
   SnapStack st;
   SnapLane s;
-  snap_setup(p, diag, smem, tbl, tb, st, s);
+  snap_setup(p, diag, smem, tbl, tb, st, s, false);
   uint32_t ovf = 0u;
   unsigned long long lane_total = 0ull;
   const long long item = (long long)blockIdx.x * B + threadIdx.x;
@@ -486,7 +492,7 @@ __global__ void __launch_bounds__(512)
   if (NODES) block_reduce_add(s.nodes, p.nodes, red);
 }
 
-template <bool VSYM, bool NODES, bool DG>
+template <bool VSYM, bool NODES, bool DG, bool LA>
 __global__ void __launch_bounds__(512)
     k_snapshot(const __grid_constant__ KParams p, int diag) {
   extern __shared__ uint32_t smem[];
@@ -497,7 +503,7 @@ __global__ void __launch_bounds__(512)
   SnapTable tb;
   SnapStack st;
   SnapLane s;
-  snap_setup(p, diag, smem, tbl, tb, st, s);
+  snap_setup(p, diag, smem, tbl, tb, st, s, LA);
   uint32_t ovf = 0u;
 
   unsigned long long lane_total = 0ull;
@@ -525,7 +531,7 @@ __global__ void __launch_bounds__(512)
       // every lane is busy here: step until one finishes
       bool fin;
       do {
-        fin = snap_step<VSYM, NODES, DG>(s, p.g, st, tb, B, ovf);
+        fin = snap_step<VSYM, NODES, DG, LA>(s, p.g, st, tb, B, ovf);
       } while (!__any_sync(FULL, fin));
       if (fin) {
         busy = false;
@@ -533,7 +539,7 @@ __global__ void __launch_bounds__(512)
       }
     } else {
       for (int it = 0; it <= p.check_mask; ++it) {
-        if (busy && snap_step<VSYM, NODES, DG>(s, p.g, st, tb, B, ovf)) {
+        if (busy && snap_step<VSYM, NODES, DG, LA>(s, p.g, st, tb, B, ovf)) {
           busy = false;
           flush_count(s.prefix, s.cnt, p, lane_total);
         }
@@ -626,6 +632,7 @@ struct Shape {
   int check_mask;
   int words;  // 0 auto, 1 shared memory, 2 registers
   int stack;  // 0 auto, 1 one entry per position, 2 snapshots
+  int lookahead;
 };
 
 static int resolve_shape(const dls_launch_t *cfg, int depth, int last,
@@ -660,6 +667,8 @@ static int resolve_shape(const dls_launch_t *cfg, int depth, int last,
   if (sh->words < 0 || sh->words > 2) return DLS_ERR_BAD_ARG;
   sh->stack = c.stack;
   if (sh->stack < 0 || sh->stack > 2) return DLS_ERR_BAD_ARG;
+  sh->lookahead = c.lookahead;
+  if (sh->lookahead < 0 || sh->lookahead > 1) return DLS_ERR_BAD_ARG;
   return DLS_OK;
 }
 
@@ -722,7 +731,7 @@ static const void *pick_kernel(int kind, bool reg, bool vsym, bool nodes, bool s
 template <bool VSYM, bool NODES, bool DG>
 static const void *snapshot_ptr(bool plain) {
   return plain ? (const void *)k_plain_snap<VSYM, NODES, DG>
-               : (const void *)k_snapshot<VSYM, NODES, DG>;
+               : (const void *)k_snapshot<VSYM, NODES, DG, false>;
 }
 
 template <bool VSYM>
@@ -733,8 +742,11 @@ static const void *pick_snapshot2(bool plain, bool nodes, bool dg) {
 }
 
 // dg: some cell at or after the prefix depth lies on a diagonal (the
-// diagonal words change during the search)
-static const void *pick_snapshot(bool plain, bool vsym, bool nodes, bool dg) {
+// diagonal words change during the search); la: the persistent kernel with
+// the lookahead (no diagonal words, no vertical symmetry only)
+static const void *pick_snapshot(bool plain, bool vsym, bool nodes, bool dg, bool la) {
+  if (la) return nodes ? (const void *)k_snapshot<false, true, false, true>
+                       : (const void *)k_snapshot<false, false, false, true>;
   return vsym ? pick_snapshot2<true>(plain, nodes, dg) : pick_snapshot2<false>(plain, nodes, dg);
 }
 
@@ -857,8 +869,10 @@ static int prepare_launch(int n, uint32_t flags, const uint8_t *order, int order
   const bool plain = sh.kernel == DLS_KERNEL_PLAIN;
   pr->run = snap ? (plain ? DLS_RUN_PLAIN_SNAPSHOT : DLS_RUN_SNAPSHOT)
                  : (plain ? DLS_RUN_PLAIN : DLS_RUN_PERSISTENT);
-  pr->fn = snap ? pick_snapshot(plain, vsym, d_nodes != nullptr,
-                                diagonal_cells_after(info, n, flags, depth))
+  const bool dgw = diagonal_cells_after(info, n, flags, depth);
+  const bool la = snap && !plain && sh.lookahead && !dgw && !vsym;
+  if (sh.lookahead && !la) return DLS_ERR_BAD_ARG;
+  pr->fn = snap ? pick_snapshot(plain, vsym, d_nodes != nullptr, dgw, la)
                 : pick_kernel(sh.kernel, reg, vsym, d_nodes != nullptr, sh.lanes_log2 > 0);
   auto smem_for = [&](int block) {
     return snap ? smem_bytes_snapshot(order_len, kp.snap_cap, block)

@@ -159,9 +159,15 @@ __device__ __forceinline__ void snap_place(Words<true> &w, uint32_t rs, uint32_t
 // ovf is set (and the stack index held at cap, so every access stays in the
 // lane's cap + 2 slots) if a lane ever needs more entries than cap -- which
 // the bound on cap excludes.
-template <bool VSYM, bool NODES, bool DG>
+// LA (lookahead, Section 2.4.2; only without diagonal words and without
+// vertical symmetry): the cell after the next one must still have a
+// candidate, or the placement is a dead end already -- placing the next cell
+// only removes candidates.  Its field shifts are in dm (the diagonal masks
+// are not needed there).
+template <bool VSYM, bool NODES, bool DG, bool LA = false>
 __device__ __forceinline__ bool snap_step(SnapLane &s, const Geo &g, const SnapStack &st,
                                           const SnapTable &tb, unsigned B, uint32_t &ovf) {
+  static_assert(!LA || (!DG && !VSYM), "lookahead: no diagonal words, no symmetry");
   const uint32_t nv = s.L & (0u - s.L);
   const uint32_t Lr = s.L ^ nv;
   const bool keep = Lr != 0u;
@@ -176,7 +182,8 @@ __device__ __forceinline__ bool snap_step(SnapLane &s, const Geo &g, const SnapS
   const unsigned leaves = leaf ? (unsigned)__popc(L1) : 0u;
   s.cnt += leaves;
   if (NODES) s.nodes += leaves;
-  const bool dead = leaf || L1 == 0u;
+  bool dead = leaf || L1 == 0u;
+  if (LA) dead = dead || snap_cands<false, false>(s.w, s.dm.x, s.dm.y, 0u, g) == 0u;
   // entry e lives in slot e + 1 (slot 0 is never live, slot cap + 1 is
   // spare): the state before placing nv is written to the first free slot
   // every iteration; a push keeps it

@@ -152,6 +152,30 @@ def test_describe_launch_names_the_kernel(dls):
         dls.describe_launch(9, D, o9, 17, 10, dls.Launch(stack=2))
 
 
+def test_lookahead_where_it_applies(dls):
+    """Lookahead (Section 2.4.2): same counts, fewer nodes, where no cell
+    after the prefix lies on a diagonal and without vertical symmetry;
+    refused elsewhere."""
+    for n, flags, after, kind in ((7, D, 14, dls.ORDER_HEURISTIC), (6, D, 10, dls.ORDER_HEURISTIC),
+                                  (6, 0, 3, None), (5, 0, 4, None)):
+        wl = gpu_cases.split(dls, n, flags, after, kind=kind)
+        ref_c, ref_n = oracle.count_many(n, flags, wl.oracle_order, wl.oracle_prefixes,
+                                         threads=THREADS)
+        t = torch.from_numpy(wl.prefixes).cuda()
+        for sh in (dict(lookahead=1), dict(lookahead=1, block_threads=32, check_every=1)):
+            nodes = torch.zeros(1, dtype=torch.uint64, device="cuda")
+            c = dls.count(n, flags, wl.order, t, nodes=nodes, launch=dls.Launch(**sh))
+            torch.cuda.synchronize()
+            assert (c.cpu().numpy() == ref_c).all(), (n, flags, sh)
+            assert int(nodes.cpu().numpy()[0]) <= int(ref_n.sum())
+    for n, flags, after in ((6, D, 5), (6, D | V, 2)):
+        wl = gpu_cases.split(dls, n, flags, after)
+        with pytest.raises(dls.DlsError) as e:
+            dls.count(n, flags, wl.order, torch.from_numpy(wl.prefixes).cuda(),
+                      launch=dls.Launch(lookahead=1))
+        assert e.value.code == 3
+
+
 def test_snapshot_stack_deep_orders(dls):
     """Orders whose cells after the prefix are mostly free (row-major order
     from an empty square, so nothing is forced early): the snapshot stack
@@ -242,7 +266,7 @@ def test_bench_configuration_against_oracle(dls, suffix):
     ref, _ = oracle.count_many(n, D, o_order, o_pre[sel], threads=THREADS)
     assert int(ref.sum()) > 0
     d_pre = torch.from_numpy(pre).cuda()
-    for launch in (dict(), dict(block_threads=64)):
+    for launch in (dict(), dict(block_threads=64), dict(lookahead=1)):
         counts = torch.empty(len(pre), dtype=torch.uint64, device="cuda")
         total = torch.empty(1, dtype=torch.uint64, device="cuda")
         plan = dls.Plan(n, D, order, d_pre, counts, total, dls.Launch(**launch))
