@@ -1,25 +1,28 @@
 // dls_kernels.cu -- the batch kernels (Algorithm 4 of the paper on sm_103a)
 // and the C-ABI entry points that launch them.
 //
-// The per-lane search (state, step, prefix loading) is in dls_search.cuh.
-// Row/column words and the stack live in shared memory in a thread-minor
-// layout (word w of thread t at w * blockDim + t), so a warp's accesses hit
-// 32 distinct banks whatever positions its lanes are at; or, where they fit,
-// the row and column words are packed into two 64-bit registers.  The
-// diagonal words, the current position's candidates and value stay in
+// Two per-lane searches: the one-entry-per-position search of
+// dls_search.cuh, whose row/column words and stack live in shared memory in
+// a thread-minor layout (word w of thread t at w * blockDim + t, so a warp's
+// accesses hit 32 distinct banks whatever positions its lanes are at) or,
+// where they fit, with the row and column words packed into two 64-bit
+// registers; and the snapshot search of dls_snapshot.cuh (register words, a
+// stack entry only where candidates remain), the default where the words fit
 // registers.
 //
 // Kernels:
-//   k_plain      -- one thread per work item, the comparison baseline.
+//   k_plain      -- one thread per work item, per-position search: the
+//                   comparison baseline of the paper's loop structure.
+//   k_plain_snap -- one thread per prefix, snapshot search: the baseline
+//                   with the batched kernel's own search step.
 //   k_persistent -- a resident grid; warps take work items from a global
 //                   atomic queue as lanes go idle, and once the queue is empty
 //                   idle lanes take the shallowest untried subtree of a busy
 //                   lane in the same warp (ballot + shuffle + shared memory).
-//   k_snapshot   -- the same grid, queue and donation with the search of
-//                   dls_snapshot.cuh: register words and a stack of state
-//                   snapshots kept only where candidates remain, so that a
-//                   dead end returns to the deepest open cell in one step.
-//   Both keep per-lane totals, reduce them per block in shared memory and add
+//   k_snapshot   -- the same grid, queue and donation with the snapshot
+//                   search, so that a dead end returns to the deepest open
+//                   cell in one step; optional lookahead (Section 2.4.2).
+//   All keep per-lane totals, reduce them per block in shared memory and add
 //   one 64-bit atomic per block to the global total.
 //
 // Work items: prefix p is split into `lanes` items (p, s); item s keeps the
