@@ -199,3 +199,21 @@ def test_argument_errors(dls):
     with pytest.raises(DlsError) as e:   # depth beyond the order
         dls.extend_prefixes(6, D, orders.md_ad_rows(6), np.zeros((1, 0), np.uint8), 37)
     assert e.value.code == 3
+
+
+def test_fig1_workunit_decomposition(dls, golden):
+    """Section 5.2: the order-9 search is cut into workunits by the values of
+    the first 10 cells of the Fig. 1 order after row 0.  The library and the
+    oracle enumerate them independently and agree on 1 255 884; the paper
+    prints 1 225 884 -- one digit different, 30 000 apart (reading R7 of the
+    design notes: a misprint), so the printed figure is recorded, not
+    asserted."""
+    o = orders.row0(9) + fig1_order()
+    ident = np.array([orders.identity(9)], np.uint8)
+    o_units, _ = oracle.extend(9, D, o, ident, 9 + 10)
+    units, _ = dls.extend_prefixes(9, D, np.array(o, np.uint8), ident, 9 + 10)
+    assert (units == o_units).all()
+    assert len(units) == 1255884
+    printed = golden["dls9_decomposition_10"]
+    a, b = str(printed), str(len(units))
+    assert len(a) == len(b) and sum(x != y for x, y in zip(a, b)) == 1
