@@ -205,9 +205,8 @@ def test_fig1_workunit_decomposition(dls, golden):
     """Section 5.2: the order-9 search is cut into workunits by the values of
     the first 10 cells of the Fig. 1 order after row 0.  The library and the
     oracle enumerate them independently and agree on 1 255 884; the paper
-    prints 1 225 884 -- one digit different, 30 000 apart (reading R7 of the
-    design notes: a misprint), so the printed figure is recorded, not
-    asserted."""
+    prints 1 225 884 -- one digit different, 30 000 apart, taken as a
+    misprint -- so the printed figure is recorded, not asserted."""
     o = orders.row0(9) + fig1_order()
     ident = np.array([orders.identity(9)], np.uint8)
     o_units, _ = oracle.extend(9, D, o, ident, 9 + 10)
