@@ -160,6 +160,27 @@ int dls_sample_prefix(int n, uint32_t flags, const uint8_t *order,
                       int order_len, int depth, const uint32_t *draws,
                       int64_t n_draws, uint8_t *out, int64_t *draws_used);
 
+/* An estimate of the size of the search below one prefix: the number of
+ * values the search of Algorithm 4 places after the prefix (every accepted
+ * placement, the last cell's included) -- the `nodes` a counting pass
+ * reports.  Not a method of the paper: it is D. E. Knuth's random-descent
+ * estimate ("Estimating the efficiency of backtrack programs", Math. Comp.
+ * 29, 1975).  Each of `probes` descents fills the cells after the prefix in
+ * order with an admissible value drawn uniformly at random, multiplying up
+ * the numbers of admissible values met (d_1, d_1 d_2, ...) and summing those
+ * products until a cell has none or the last cell is reached; *nodes_out =
+ * the mean of the sums, an unbiased estimate.  The draws are splitmix64
+ * (Steele, Lea and Flood 2014) of the counter (probe << 32 | cell position)
+ * XORed with splitmix64(seed), taken modulo the number of admissible
+ * values: the result is a pure function of the arguments.  The serving path
+ * sizes its work items with it (seed = job id, 256 probes).  An invalid
+ * prefix gives 0.  prefix: `depth` value bytes along the order, host
+ * memory.  Errors: INVALID_N, BAD_ORDER, BAD_ARG (unknown flags, depth
+ * outside [0, order_len], probes < 1, NULL nodes_out). */
+int dls_estimate_nodes(int n, uint32_t flags, const uint8_t *order, int order_len,
+                       const uint8_t *prefix, int depth, uint64_t seed, int probes,
+                       double *nodes_out);
+
 /* Number of squares represented by one square whose row 0 is 0..n-1:
  * n! for diagonal and ordinary Latin squares (Section 2.2; the order-9 total
  * of Section 5.2.1 is the fixed-row count times 9!), 2^(n/2) (n/2)! for

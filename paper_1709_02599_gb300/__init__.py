@@ -124,6 +124,21 @@ def sample_prefix(n, flags, order, depth, draws):
     return out[:depth].copy(), int(used.value)
 
 
+def estimate_nodes(n, flags, order, prefix, seed=0, probes=256):
+    """Knuth's random-descent estimate of the search nodes below ``prefix``
+    (uint8 values along ``order``): ``probes`` seeded descents, their mean
+    (dls_estimate_nodes).  0.0 for an invalid prefix."""
+    L = lib()
+    o, op, ol = _order(order)
+    p = _u8(prefix).ravel()
+    out = ctypes.c_double(0.0)
+    _lib.check(L.dls_estimate_nodes(n, flags, op, ol,
+                                    p.ctypes.data_as(_lib.u8p) if p.size else None, p.size,
+                                    int(seed) & ((1 << 64) - 1), probes, ctypes.byref(out)),
+               "dls_estimate_nodes")
+    return out.value
+
+
 def multiplier(n, flags):
     return lib().dls_multiplier(n, flags).value()
 

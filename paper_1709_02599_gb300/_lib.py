@@ -121,6 +121,9 @@ def load():
                                         c_int, u8p, c_i64, i64p, i64p]),
         "dls_sample_prefix": (c_int, [c_int, c_u32, u8p, c_int, c_int, u32p, c_i64,
                                       u8p, i64p]),
+        "dls_estimate_nodes": (c_int, [c_int, c_u32, u8p, c_int, u8p, c_int,
+                                       ctypes.c_uint64, c_int,
+                                       ctypes.POINTER(ctypes.c_double)]),
         "dls_multiplier": (U128, [c_int, c_u32]),
         "dls_mul_u64": (U128, [ctypes.c_uint64, U128]),
         "dls_add_u128": (U128, [U128, U128]),

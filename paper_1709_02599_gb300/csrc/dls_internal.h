@@ -29,6 +29,15 @@ bool vsym_all_zero(int n, uint32_t flags);
 // Records the text of the last CUDA error for dls_last_cuda_error().
 void set_cuda_error(const char *what);
 
+// splitmix64 (Steele, Lea, Flood 2014), the library's counter-based
+// generator for random probes.
+uint64_t splitmix64(uint64_t x);
+
+// Knuth's random-descent estimate of the search nodes below a prefix
+// (dls_estimate_nodes), probes keyed by `key`; 0 for an invalid prefix.
+double estimate_nodes(const OrderInfo &info, const uint8_t *prefix, int depth, uint64_t key,
+                      int probes);
+
 // Host bitmask search state (Section 3).
 struct HostState {
   int n;

@@ -277,49 +277,6 @@ struct dls_server {
   std::vector<std::thread> workers;
 };
 
-// splitmix64 (Steele, Lea, Flood 2014): the server's counter-based generator
-// for the random probes below, keyed by (job id, probe, position).
-static uint64_t splitmix64(uint64_t x) {
-  x += 0x9e3779b97f4a7c15ull;
-  x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
-  x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
-  return x ^ (x >> 31);
-}
-
-// Knuth's estimate of the size of the search below a prefix (D. E. Knuth,
-// "Estimating the efficiency of backtrack programs", 1975): a random descent
-// along the order takes, at each cell, the product of the numbers of
-// admissible values met so far as its estimate of the nodes at that depth
-// and adds them up, stopping at a dead end or the last cell; the mean over
-// descents is an unbiased estimate of the number of search nodes.  (The
-// same estimate of the completions alone is nearly always 0 here: most
-// descents end at a dead end.)  Used only to choose how finely a job is
-// split -- the counts never depend on it.
-static double estimate_nodes(const OrderInfo &info, const uint8_t *prefix, int depth,
-                             uint64_t key, int probes) {
-  HostState base;
-  base.init(info);
-  for (int t = 0; t < depth; ++t)
-    if (!base.place(t, prefix[t])) return 0.0;
-  double sum = 0.0;
-  for (int pr = 0; pr < probes; ++pr) {
-    HostState s = base;
-    double w = 1.0;
-    for (int t = depth; t < info.len; ++t) {
-      const uint32_t c = s.candidates(t);
-      const int k = __builtin_popcount(c);
-      w *= (double)k;
-      sum += w;
-      if (k == 0 || t == info.len - 1) break;
-      const uint64_t r = splitmix64(key ^ splitmix64(((uint64_t)pr << 32) | (uint64_t)t));
-      uint32_t v = c;
-      for (int q = (int)(r % (uint64_t)k); q > 0; --q) v &= v - 1u;
-      s.toggle(t, v & (0u - v));
-    }
-  }
-  return sum / probes;
-}
-
 // Splits a submitted job into work items (worker thread, no lock held but
 // at the end): the prefix is extended a few cells deeper (Section 5.2), at
 // most to two cells before the end, until there are enough items -- one per
