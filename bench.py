@@ -54,8 +54,11 @@ L2_FLUSH_BYTES = 256 << 20
 # order after the split (depth 25: 149 590 prefixes, 4.953 MB read; depth
 # 28: 273 038 prefixes, 9.893 MB read; 0 written while the kernel ran),
 # scaled per prefix; the profile summary under profiles/ gives the commands
+# (key "k_snapshot fused": the same kernel with the fused step, captured the
+# same way at depth 25: 5.015 MB read, 0 written)
 TRAFFIC_PER_PREFIX = {("dls8_diag64", "k_snapshot", 25): 4.953088e6 / 149590,
-                      ("dls8_diag64", "k_snapshot", 28): 9.892864e6 / 273038}
+                      ("dls8_diag64", "k_snapshot", 28): 9.892864e6 / 273038,
+                      ("dls8_diag64", "k_snapshot fused", 25): 5.015040e6 / 149590}
 
 
 def parse():
@@ -458,6 +461,8 @@ def main():
     peak_tops = sms * ISSUE_LANES_PER_SM * sm_max_mhz * 1e6 / 1e12
     achieved_tops = nodes * OPS_PER_NODE / step_s / 1e12
 
+    # the traffic figures belong to the kernel variant they were captured on
+    kernel_id = run["kernel"] + (" fused" if run.get("fused") else "")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * step_s, "higher_is_better": True,
@@ -479,8 +484,8 @@ def main():
             "d2h_bytes_per_step": int(P * 8), "entry": "dls_count_host"},
         "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops,
                      "unit": "Tops/s", "frac": achieved_tops / peak_tops,
-                     "traffic": (TRAFFIC_PER_PREFIX[(spec.name, run["kernel"], depth)] * P
-                                 if (spec.name, run["kernel"], depth) in TRAFFIC_PER_PREFIX
+                     "traffic": (TRAFFIC_PER_PREFIX[(spec.name, kernel_id, depth)] * P
+                                 if (spec.name, kernel_id, depth) in TRAFFIC_PER_PREFIX
                                  else None),
                      "algorithmic_bytes": int(P * (depth + 8)),
                      "ops_per_node": OPS_PER_NODE,

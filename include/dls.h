@@ -242,6 +242,16 @@ typedef struct {
                              on a diagonal and without DLS_VSYM (BAD_ARG
                              otherwise); same counts, fewer nodes.  0 = off
                              (default)                                       */
+    int fuse;             /* the snapshot search's fused step: when the cell
+                             after a placement has exactly one candidate (and
+                             is not the last cell), the same iteration places
+                             it -- the next iteration's move, so the counts,
+                             nodes and stack entries are unchanged and the
+                             iterations fewer; only where no cell after the
+                             prefix lies on a diagonal, without DLS_VSYM and
+                             without the lookahead.  1 = on (BAD_ARG where it
+                             does not apply), -1 = off, 0 = on where it
+                             applies (default)                              */
 } dls_launch_t;
 
 /* What a dls_count_ex call with this shape runs. */
@@ -262,6 +272,7 @@ typedef struct {
     int grid_blocks;      /* 0 = nothing to launch                           */
     int smem_bytes;       /* dynamic shared memory per block                 */
     int stack_entries;    /* snapshot entries per lane (0 otherwise)         */
+    int fused;            /* 1 = the snapshot search takes the fused step    */
 } dls_launch_info;
 
 /* Resolves the kernel and launch shape that dls_count_ex would use for these

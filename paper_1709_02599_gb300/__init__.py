@@ -36,11 +36,13 @@ class Launch:
     words: int = 0
     stack: int = 0
     lookahead: int = 0
+    fuse: int = 0
 
     def c(self):
         return _lib.LaunchT(self.kernel, self.block_threads, self.blocks_per_sm,
                             self.lanes_per_prefix, self.split_pos, self.donate,
-                            self.check_every, self.words, self.stack, self.lookahead)
+                            self.check_every, self.words, self.stack, self.lookahead,
+                            self.fuse)
 
 
 def lib():
@@ -158,7 +160,7 @@ def describe_launch(n, flags, order, depth, n_prefixes, launch=None):
     """The kernel and launch shape dls_count_ex would use (dls_describe_launch):
     a dict with 'kernel' (k_snapshot / k_persistent / k_plain_snap / k_plain), 'words'
     ('registers' or 'shared'), 'block_threads', 'grid_blocks', 'smem_bytes',
-    'stack_entries'."""
+    'stack_entries', 'fused' (the snapshot search's fused step)."""
     o, op, ol = _order(order)
     cfg = (launch or Launch()).c()
     info = _lib.LaunchInfo()
@@ -168,7 +170,8 @@ def describe_launch(n, flags, order, depth, n_prefixes, launch=None):
     return {"kernel": _lib.RUN_NAMES[info.run],
             "words": "registers" if info.words == 2 else "shared",
             "block_threads": info.block_threads, "grid_blocks": info.grid_blocks,
-            "smem_bytes": info.smem_bytes, "stack_entries": info.stack_entries}
+            "smem_bytes": info.smem_bytes, "stack_entries": info.stack_entries,
+            "fused": bool(info.fused)}
 
 
 def count(n, flags, order, prefixes, counts=None, total=None, nodes=None, launch=None,

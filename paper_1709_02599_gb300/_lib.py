@@ -53,7 +53,8 @@ class LaunchT(ctypes.Structure):
                 ("check_every", ctypes.c_int),
                 ("words", ctypes.c_int),
                 ("stack", ctypes.c_int),
-                ("lookahead", ctypes.c_int)]
+                ("lookahead", ctypes.c_int),
+                ("fuse", ctypes.c_int)]
 
 
 class LaunchInfo(ctypes.Structure):
@@ -62,7 +63,8 @@ class LaunchInfo(ctypes.Structure):
                 ("block_threads", ctypes.c_int),
                 ("grid_blocks", ctypes.c_int),
                 ("smem_bytes", ctypes.c_int),
-                ("stack_entries", ctypes.c_int)]
+                ("stack_entries", ctypes.c_int),
+                ("fused", ctypes.c_int)]
 
 
 class ServerCfg(ctypes.Structure):

@@ -28,6 +28,8 @@ SHAPES = [
     {},
     {"block_threads": 64},
     {"block_threads": 256},
+    {"fuse": -1},
+    {"fuse": -1, "block_threads": 64},
     {"lookahead": 1},
     {"lookahead": 1, "block_threads": 64},
     {"check_every": 16},

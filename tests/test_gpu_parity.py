@@ -176,6 +176,42 @@ def test_lookahead_where_it_applies(dls):
         assert e.value.code == 3
 
 
+def test_fused_step_where_it_applies(dls):
+    """The fused step (a following cell with one candidate is placed in the
+    same iteration) makes the next iteration's move early: counts and node
+    counts equal the oracle's, with the step on and off, in the persistent
+    and plain kernels; refused where diagonal words or vertical symmetry
+    are in play, and with the lookahead."""
+    for n, flags, after, kind in ((7, D, 14, dls.ORDER_HEURISTIC), (6, D, 10, dls.ORDER_HEURISTIC),
+                                  (6, 0, 3, None), (5, 0, 4, None), (6, 0, 8, None)):
+        wl = gpu_cases.split(dls, n, flags, after, kind=kind)
+        ref_c, ref_n = oracle.count_many(n, flags, wl.oracle_order, wl.oracle_prefixes,
+                                         threads=THREADS)
+        t = torch.from_numpy(wl.prefixes).cuda()
+        depth = wl.prefixes.shape[1]
+        for sh in (dict(fuse=1), dict(fuse=-1), dict(fuse=1, kernel=dls.KERNEL_PLAIN),
+                   dict(fuse=1, block_threads=32, check_every=1), dict()):
+            launch = dls.Launch(**sh)
+            assert dls.describe_launch(n, flags, wl.order, depth, len(t),
+                                       launch)["fused"] == (sh.get("fuse", 0) >= 0)
+            nodes = torch.zeros(1, dtype=torch.uint64, device="cuda")
+            c = dls.count(n, flags, wl.order, t, nodes=nodes, launch=launch)
+            torch.cuda.synchronize()
+            assert (c.cpu().numpy() == ref_c).all(), (n, flags, sh)
+            assert int(nodes.cpu().numpy()[0]) == int(ref_n.sum()), (n, flags, sh)
+    for n, flags, after, sh in ((6, D, 5, dict(fuse=1)), (6, D | V, 2, dict(fuse=1)),
+                                (6, 0, 3, dict(fuse=1, lookahead=1)),
+                                (6, 0, 3, dict(fuse=1, stack=1))):
+        wl = gpu_cases.split(dls, n, flags, after)
+        with pytest.raises(dls.DlsError) as e:
+            dls.count(n, flags, wl.order, torch.from_numpy(wl.prefixes).cuda(),
+                      launch=dls.Launch(**sh))
+        assert e.value.code == 3, (n, flags, sh)
+    # where it does not apply, the default runs the unfused step
+    wl = gpu_cases.split(dls, 6, D, 5)
+    assert not dls.describe_launch(6, D, wl.order, wl.prefixes.shape[1], 10)["fused"]
+
+
 def test_snapshot_stack_deep_orders(dls):
     """Orders whose cells after the prefix are mostly free (row-major order
     from an empty square, so nothing is forced early): the snapshot stack
@@ -266,7 +302,7 @@ def test_bench_configuration_against_oracle(dls, suffix):
     ref, _ = oracle.count_many(n, D, o_order, o_pre[sel], threads=THREADS)
     assert int(ref.sum()) > 0
     d_pre = torch.from_numpy(pre).cuda()
-    for launch in (dict(), dict(block_threads=64), dict(lookahead=1)):
+    for launch in (dict(), dict(fuse=-1), dict(block_threads=64), dict(lookahead=1)):
         counts = torch.empty(len(pre), dtype=torch.uint64, device="cuda")
         total = torch.empty(1, dtype=torch.uint64, device="cuda")
         plan = dls.Plan(n, D, order, d_pre, counts, total, dls.Launch(**launch))
