@@ -78,3 +78,25 @@ def vsym10_rows2(dls, seed=0, k=2000):
     picks = dls_inputs.choose(len(allp), k, seed)
     return Workload(n, D | V, order, allp[picks], o_order, o_allp[picks],
                     population=len(allp), depth=3 * (n // 2))
+
+
+def sampled_rows(dls, n, flags, rows, count=6):
+    """Up to `count` random partial squares with `rows` rows filled (row 0
+    included), each decoded from the same seeded draws by the library's and
+    the oracle's samplers (draws that run out are skipped by both)."""
+    vs = bool(flags & V)
+    order = dls.fill_order(n, flags, first_rows=rows)
+    o_order = orders.md_ad_rows(n, vsym=vs, first_rows=rows)
+    depth = rows * len(orders.identity(n, vs))
+    pre, o_pre = [], []
+    for k in range(count):
+        draws = dls_inputs.draws(1 << 14, seed=n * 100 + rows, stream=k)
+        a, ua = dls.sample_prefix(n, flags, order, depth, draws)
+        b, ub = oracle.sample_prefix(n, flags, o_order, depth, draws)
+        assert ua == ub
+        if b is None:
+            continue
+        pre.append(a)
+        o_pre.append(b)
+    return Workload(n, flags, order, np.array(pre, np.uint8).reshape(-1, depth), o_order,
+                    np.array(o_pre, np.uint8).reshape(-1, depth), depth=depth)

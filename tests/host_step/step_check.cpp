@@ -1,20 +1,27 @@
-// step_check.cpp -- runs the kernels' snapshot search step (snap_step of
-// dls_snapshot.cuh, compiled for the host through shim.h) on one lane per
-// prefix, with no warp and no donation, for tests/test_host_step.py.
+// step_check.cpp -- runs the kernels' per-lane search steps (snap_step of
+// dls_snapshot.cuh, dfs_step of dls_search.cuh, compiled for the host
+// through shim.h) on one lane per work item, with no warp and no donation,
+// for tests/test_host_step.py.
 //
-//   step_check n flags mode order.bin prefixes.bin depth cap
+//   step_check n flags mode order.bin prefixes.bin depth cap [lanes_log2 split_pos]
 //
-// mode: 0 = the plain step (diagonal words when a cell after the prefix lies
-// on a diagonal), 1 = lookahead, 2 = fused step (1 and 2 only without
-// diagonal words and without vertical symmetry; exit 2 otherwise).
+// mode, the snapshot step: 0 = plain (diagonal words when a cell after the
+// prefix lies on a diagonal), 1 = lookahead, 2 = fused step (1 and 2 only
+// without diagonal words and without vertical symmetry; exit 2 otherwise).
+// mode, the per-position step (one stack entry per position): 10 = words in
+// registers (exit 2 where they do not fit), 11 = words in the shared-memory
+// layout, 12 = as 11 with vertical symmetry taken at run time (the serving
+// kernel's step).  lanes_log2 / split_pos (per-position step only): each
+// prefix is split into 2^lanes_log2 work items at order position split_pos,
+// run one after the other and summed.
 // order.bin: the fill order as (i, j) byte pairs; prefixes.bin: depth value
-// bytes per prefix.  cap: stack entries per lane.  The position table is
-// built as the kernels' setup builds it.  Every stack slot starts as 0xff
-// bytes, so a read of a slot never written shows up as a bad position.
+// bytes per prefix.  cap: stack entries per lane (snapshot step).  The
+// tables are built as the kernels' setup builds them.  Every stack slot
+// starts as 0xff bytes, so a read of a slot never written shows up.
 //
 // stdout: "count nodes" per prefix.  stderr: one line
 // "iters I maxsp M overflow O badpos B".  Exit 3 when a step leaves the lane
-// at a position outside the order or a stack index outside [0, cap].
+// at a position outside the order or a stack index outside its stack.
 #include "shim.h"
 
 #include <cstdio>
@@ -49,6 +56,54 @@ bool search(SnapLane &s, const Geo &g, const SnapStack &st, const SnapTable &tb,
   }
 }
 
+// The per-position step over one work item (the kernels' load_item, then
+// dfs_step until the item is done).  words: 2n words of the lane for the
+// shared-memory layout (stride 1); stk: one entry per order position.
+template <bool REG, bool VSYM, bool SPLIT, bool RTV>
+bool search_pos(const Geo &g, const Split &sp, const Cell *tbl, int len, const uint8_t *rec,
+                uint32_t sub, uint32_t *words, uint32_t *stk, unsigned long long &cnt,
+                unsigned long long &nodes, Run &run) {
+  Lane<REG> s{};
+  s.w.tb = reinterpret_cast<char *>(words);
+  s.w.clear(2 * g.n, 1u);
+  s.sub = sub;
+  s.splitc = 0u;
+  s.cnt = 0ull;
+  s.nodes = 0ull;
+  cnt = nodes = 0ull;
+  if (!place_prefix<REG, VSYM>(s.w, g, rec, tbl)) return true;
+  if (g.depth == len) {
+    cnt = sub == 0u ? 1ull : 0ull;
+    return true;
+  }
+  const uint32_t L = s.w.template cands<VSYM>(tbl[g.depth], g);
+  if (g.depth == g.last) {
+    if (sub == 0u) cnt = nodes = (unsigned)__popc(L);
+    return true;
+  }
+  if (L == 0u) return true;
+  s.p = g.depth;
+  s.L = L;
+  s.v = 0u;
+  s.info = tbl[g.depth];
+  for (;;) {
+    ++run.iters;
+    // with the run-time flag the step is the serving kernel's: VSYM = false
+    // (only the prefix placement above takes the flag at compile time)
+    const bool fin = dfs_step<REG, RTV ? false : VSYM, true, SPLIT, RTV>(s, g, sp, stk, tbl, 1u);
+    if (fin) break;
+    // a lane that goes on stands on a cell after the prefix, before the last
+    if (s.p < g.depth || s.p >= g.last) {
+      ++run.badpos;
+      return false;
+    }
+    run.maxsp = std::max(run.maxsp, s.p - g.depth);
+  }
+  cnt = s.cnt;
+  nodes = s.nodes;
+  return true;
+}
+
 std::vector<uint8_t> read_file(const char *path) {
   std::vector<uint8_t> out;
   FILE *f = std::fopen(path, "rb");
@@ -60,11 +115,77 @@ std::vector<uint8_t> read_file(const char *path) {
   return out;
 }
 
+template <bool REG, bool VSYM, bool RTV>
+int run_items(const Geo &g, const Split &sp, const Cell *tbl, int len,
+              const std::vector<uint8_t> &pre) {
+  const int depth = g.depth;
+  const long long P = depth ? (long long)pre.size() / depth : 1;
+  std::vector<uint32_t> words(2 * (size_t)g.n);
+  std::vector<uint32_t> stk((size_t)len, ~0u);
+  Run run;
+  for (long long k = 0; k < P; ++k) {
+    const uint8_t *rec = pre.data() + (size_t)k * (size_t)depth;
+    unsigned long long cnt = 0, nodes = 0;
+    for (uint32_t sub = 0; sub < (1u << sp.lanes_log2); ++sub) {
+      unsigned long long c = 0, nd = 0;
+      const bool ok = sp.lanes_log2 > 0
+                          ? search_pos<REG, VSYM, true, RTV>(g, sp, tbl, len, rec, sub,
+                                                             words.data(), stk.data(), c, nd, run)
+                          : search_pos<REG, VSYM, false, RTV>(g, sp, tbl, len, rec, sub,
+                                                              words.data(), stk.data(), c, nd,
+                                                              run);
+      if (!ok) {
+        std::fprintf(stderr, "iters %llu maxsp %d overflow %u badpos %d\n", run.iters,
+                     run.maxsp, run.ovf, run.badpos);
+        return 3;
+      }
+      cnt += c;
+      nodes += nd;
+    }
+    std::printf("%llu %llu\n", cnt, nodes);
+  }
+  std::fprintf(stderr, "iters %llu maxsp %d overflow %u badpos %d\n", run.iters, run.maxsp,
+               run.ovf, run.badpos);
+  return 0;
+}
+
+// The per-position step (modes 10-12): cell descriptors for register words
+// (bit shifts) or for the shared-memory layout (byte offsets of the lane's
+// 2n words: rows, then columns), as the kernels' setup makes them.
+int run_pos(int n, uint32_t flags, int mode, const std::vector<uint8_t> &ob,
+            const std::vector<uint8_t> &pre, int depth, const Split &sp) {
+  const bool diag = (flags & 1u) != 0, vsym = (flags & 2u) != 0;
+  const int len = (int)ob.size() / 2;
+  std::vector<Cell> tbl(len);
+  for (int t = 0; t < len; ++t) {
+    const int i = ob[2 * t], j = ob[2 * t + 1];
+    tbl[t] = mode == 10 ? describe_regs(i, j, n, diag, vsym ? n / 2 : 8, vsym ? n : 8)
+                        : describe_shared(i, j, n, diag, 1u, n);
+  }
+  Geo g;
+  g.n = n;
+  g.all = (1u << n) - 1u;
+  g.pairmask = (1u << (n / 2)) - 1u;
+  g.depth = depth;
+  g.last = len - 1;
+  g.vsmask = vsym ? 0xffffffffu : 0u;
+  if (mode == 10)
+    return vsym ? run_items<true, true, false>(g, sp, tbl.data(), len, pre)
+                : run_items<true, false, false>(g, sp, tbl.data(), len, pre);
+  if (mode == 12)
+    return vsym ? run_items<false, true, true>(g, sp, tbl.data(), len, pre)
+                : run_items<false, false, true>(g, sp, tbl.data(), len, pre);
+  return vsym ? run_items<false, true, false>(g, sp, tbl.data(), len, pre)
+              : run_items<false, false, false>(g, sp, tbl.data(), len, pre);
+}
+
 }  // namespace
 
 int main(int argc, char **argv) {
-  if (argc != 8) {
-    std::fprintf(stderr, "usage: step_check n flags mode order.bin prefixes.bin depth cap\n");
+  if (argc != 8 && argc != 10) {
+    std::fprintf(stderr,
+                 "usage: step_check n flags mode order.bin prefixes.bin depth cap "
+                 "[lanes_log2 split_pos]\n");
     return 1;
   }
   const int n = std::atoi(argv[1]);
@@ -76,8 +197,18 @@ int main(int argc, char **argv) {
   const int cap = std::atoi(argv[7]);
   const int len = (int)ob.size() / 2;
   const bool diag = (flags & 1u) != 0, vsym = (flags & 2u) != 0;
-  if (n < 2 || n > 10 || len < 1 || depth < 0 || depth > len || cap < 1) return 1;
+  const bool pos = mode >= 10;
+  if (n < 2 || n > (pos ? DLS_MAX_N : 10) || len < 1 || depth < 0 || depth > len || cap < 1)
+    return 1;
   if (vsym && (n % 2)) return 1;  // no such squares; the library answers 0
+  Split sp{-1, 0};
+  if (argc == 10) {
+    sp.lanes_log2 = std::atoi(argv[8]);
+    sp.pos = std::atoi(argv[9]);
+    if (!pos || sp.lanes_log2 < 0 || sp.lanes_log2 > 5 || sp.pos < depth || sp.pos > len - 2)
+      return 1;
+  }
+  if (mode == 10 && (vsym ? n * (n / 2) > 64 : n > 8)) return 2;
   // register words: 8-bit fields without symmetry, n/2 value pairs with it
   const int wr = vsym ? n / 2 : 8, wc = vsym ? n : 8;
   bool dg = false;
@@ -85,7 +216,8 @@ int main(int argc, char **argv) {
     const int i = ob[2 * t], j = ob[2 * t + 1];
     if (diag && (i == j || i + j == n - 1)) dg = true;
   }
-  if (mode != 0 && (dg || vsym)) return 2;
+  if ((mode == 1 || mode == 2) && (dg || vsym)) return 2;
+  if (pos) return run_pos(n, flags, mode, ob, pre, depth, sp);
 
   std::vector<Cell> tbl(len);
   std::vector<uint4> tsh(len);

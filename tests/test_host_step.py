@@ -69,13 +69,14 @@ def entry_bound(order, n, flags, depth):
     return max(1, bound)
 
 
-def run_step(exe, tmp_path, n, flags, mode, order, prefixes, depth, cap):
+def run_step(exe, tmp_path, n, flags, mode, order, prefixes, depth, cap, split=None):
     ob = tmp_path / "order.bin"
     pb = tmp_path / "prefixes.bin"
     np.ascontiguousarray(order, dtype=np.uint8).tofile(ob)
     np.ascontiguousarray(prefixes, dtype=np.uint8).tofile(pb)
+    extra = [str(x) for x in split] if split else []
     r = subprocess.run([exe, str(n), str(flags), str(mode), str(ob), str(pb), str(depth),
-                        str(cap)], capture_output=True, text=True)
+                        str(cap)] + extra, capture_output=True, text=True)
     assert r.returncode == 0, (r.returncode, r.stderr)
     out = np.array([[int(x) for x in line.split()] for line in r.stdout.splitlines()],
                    dtype=np.uint64).reshape(-1, 2)
@@ -153,3 +154,49 @@ def test_step_on_one_diagonal_of_the_order8_workload(dls, step_check, tmp_path):
     iters = check_workload(step_check, tmp_path, wl, n, D)
     assert set(iters) == {0, 1, 2}
     assert iters[2] < 0.75 * iters[0], iters
+
+
+# ------------------------------------------------ the per-position step --
+# dfs_step (dls_search.cuh): k_persistent and k_plain (orders above 8, lane
+# splits, shared-memory words) and, with the symmetry flag taken at run
+# time, the serving kernel.
+
+
+def check_position_step(exe, tmp_path, wl, n, flags):
+    depth = wl.prefixes.shape[1]
+    ref_c, ref_n = oracle.count_many(n, flags, wl.oracle_order, wl.oracle_prefixes, threads=4)
+    fits = n * (n // 2) <= 64 if flags & V else n <= 8
+    splits = [None]
+    if depth + 2 <= len(wl.order) - 2:
+        splits += [(2, depth + 2), (3, min(depth + 5, len(wl.order) - 2))]
+    ran = 0
+    for mode in ([10] if fits else []) + [11, 12]:
+        for split in splits:
+            c, nd, info = run_step(exe, tmp_path, n, flags, mode, wl.order, wl.prefixes, depth,
+                                   1, split)
+            assert (c == ref_c).all(), (n, flags, mode, split)
+            assert (nd == ref_n).all(), (n, flags, mode, split)
+            assert info["badpos"] == 0, info
+            assert info["maxsp"] <= len(wl.order) - 2 - depth, info
+            ran += 1
+    return ran
+
+
+@pytest.mark.parametrize("n,flags,after", [(6, D, 5), (6, D | V, 2), (5, 0, 4), (7, D, 14),
+                                           (6, V, 0)])
+def test_position_step_against_oracle(dls, step_check, tmp_path, n, flags, after):
+    wl = gpu_cases.split(dls, n, flags, after)
+    assert check_position_step(step_check, tmp_path, wl, n, flags) >= 6
+
+
+@pytest.mark.parametrize("n,flags,rows", [(9, D, 4), (10, D | V, 5), (12, D | V, 7), (9, 0, 6),
+                                          (10, D, 5), (11, D, 6)])
+def test_position_step_on_larger_orders(dls, step_check, tmp_path, n, flags, rows):
+    """Orders above 8 from sampled partial squares: shared-memory words (and
+    register fields for symmetric order 10).  Rows chosen so that some
+    sampled squares have completions."""
+    wl = gpu_cases.sampled_rows(dls, n, flags, rows)
+    assert len(wl.prefixes) > 0
+    ref, _ = oracle.count_many(n, flags, wl.oracle_order, wl.oracle_prefixes, threads=4)
+    assert int(ref.sum()) > 0
+    check_position_step(step_check, tmp_path, wl, n, flags)
