@@ -200,3 +200,27 @@ def test_position_step_on_larger_orders(dls, step_check, tmp_path, n, flags, row
     ref, _ = oracle.count_many(n, flags, wl.oracle_order, wl.oracle_prefixes, threads=4)
     assert int(ref.sum()) > 0
     check_position_step(step_check, tmp_path, wl, n, flags)
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5])
+def test_steps_on_every_order_length_and_depth(dls, step_check, tmp_path, n):
+    """Degenerate shapes: every prefix of the row-major order as a partial
+    order (one cell up to the whole square), split at every depth from 0 to
+    its length, with the plain and fused snapshot steps and the per-position
+    step (orders 2 to 4 in full; order 5 at a few lengths)."""
+    full = dls.fill_order(n, 0, dls.ORDER_ROW_MAJOR)
+    lengths = range(1, len(full) + 1) if n < 5 else (1, 2, 6, 12, 19, 24, 25)
+    for length in lengths:
+        order = full[:length]
+        o_order = [tuple(map(int, c)) for c in order]
+        for depth in range(length + 1):
+            pre, _ = dls.extend_prefixes(n, 0, order, np.zeros((1, 0), np.uint8), depth)
+            if len(pre) == 0:
+                continue
+            pre = pre[::max(1, len(pre) // 200)]
+            ref_c, ref_n = oracle.count_many(n, 0, o_order, pre)
+            cap = entry_bound(order, n, 0, depth)
+            for mode in (0, 2, 11):
+                c, nd, info = run_step(step_check, tmp_path, n, 0, mode, order, pre, depth, cap)
+                assert (c == ref_c).all() and (nd == ref_n).all(), (length, depth, mode)
+                assert info["badpos"] == 0 and info["overflow"] == 0, (length, depth, mode)
