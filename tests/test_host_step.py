@@ -182,7 +182,7 @@ def check_position_step(exe, tmp_path, wl, n, flags):
     return ran
 
 
-@pytest.mark.parametrize("n,flags,after", [(6, D, 5), (6, D | V, 2), (5, 0, 4), (7, D, 14),
+@pytest.mark.parametrize("n,flags,after", [(6, D, 5), (6, D | V, 2), (5, 0, 4), (6, D, 12),
                                            (6, V, 0)])
 def test_position_step_against_oracle(dls, step_check, tmp_path, n, flags, after):
     wl = gpu_cases.split(dls, n, flags, after)
