@@ -51,3 +51,15 @@ def dls():
     import paper_1709_02599_gb300 as m
     m.lib()
     return m
+
+
+@pytest.fixture(scope="session")
+def emulated(tmp_path_factory):
+    """The library built for the CPU on the stand-in CUDA runtime of
+    tests/host_kernels (see host_emulation.py); skipped without g++."""
+    import host_emulation
+    d = tmp_path_factory.mktemp("host_emulation")
+    exe = host_emulation.build(str(d))
+    if exe is None:
+        pytest.skip("g++ is not available")
+    return host_emulation.Emulated(exe, str(d))

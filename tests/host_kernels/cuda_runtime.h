@@ -24,6 +24,7 @@
 #define __global__
 #define __launch_bounds__(...)
 #define __grid_constant__
+#define __align__(n) __attribute__((aligned(n)))
 
 struct dim3 {
   unsigned x, y, z;
@@ -47,6 +48,11 @@ inline int __ffs(int v) {
 inline unsigned long long atomicAdd(unsigned long long *a, unsigned long long v) {
   const unsigned long long old = *a;
   *a = old + v;
+  return old;
+}
+inline unsigned atomicSub(unsigned *a, unsigned v) {
+  const unsigned old = *a;
+  *a = old - v;
   return old;
 }
 
@@ -101,7 +107,9 @@ typedef enum {
 
 struct CUstream_st;
 struct CUgraph_st;
+struct CUevent_st;
 typedef CUstream_st *cudaStream_t;
+typedef CUevent_st *cudaEvent_t;
 typedef CUgraph_st *cudaGraph_t;
 typedef CUgraph_st *cudaGraphExec_t;
 
@@ -123,6 +131,7 @@ enum cudaStreamCaptureMode {
   cudaStreamCaptureModeRelaxed = 2
 };
 #define cudaStreamNonBlocking 0x01
+#define cudaEventDisableTiming 0x02
 
 const char *cudaGetErrorString(cudaError_t e);
 cudaError_t cudaGetDevice(int *dev);
@@ -131,12 +140,38 @@ cudaError_t cudaDeviceGetAttribute(int *v, cudaDeviceAttr a, int dev);
 cudaError_t cudaFuncSetAttribute(const void *fn, cudaFuncAttribute a, int v);
 cudaError_t cudaOccupancyMaxActiveBlocksPerMultiprocessor(int *n, const void *fn, int block,
                                                           size_t smem);
+// kernels passed by name, as the runtime's template overloads allow
+template <class F>
+cudaError_t cudaFuncSetAttribute(F *fn, cudaFuncAttribute a, int v) {
+  return cudaFuncSetAttribute((const void *)fn, a, v);
+}
+template <class F>
+cudaError_t cudaOccupancyMaxActiveBlocksPerMultiprocessor(int *n, F *fn, int block, size_t smem) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, (const void *)fn, block, smem);
+}
 cudaError_t cudaMalloc(void **p, size_t bytes);
 template <class T>
 cudaError_t cudaMalloc(T **p, size_t bytes) {
   return cudaMalloc(reinterpret_cast<void **>(p), bytes);
 }
 cudaError_t cudaFree(void *p);
+cudaError_t cudaMallocHost(void **p, size_t bytes);
+template <class T>
+cudaError_t cudaMallocHost(T **p, size_t bytes) {
+  return cudaMallocHost(reinterpret_cast<void **>(p), bytes);
+}
+cudaError_t cudaFreeHost(void *p);
+cudaError_t cudaGetLastError();
+// a __device__ variable is an ordinary one here
+template <class T>
+cudaError_t cudaGetSymbolAddress(void **p, const T &symbol) {
+  *p = const_cast<void *>(static_cast<const void *>(&symbol));
+  return cudaSuccess;
+}
+cudaError_t cudaEventCreateWithFlags(cudaEvent_t *e, unsigned flags);
+cudaError_t cudaEventRecord(cudaEvent_t e, cudaStream_t s = nullptr);
+cudaError_t cudaEventSynchronize(cudaEvent_t e);
+cudaError_t cudaEventDestroy(cudaEvent_t e);
 cudaError_t cudaMemsetAsync(void *p, int v, size_t bytes, cudaStream_t s = nullptr);
 cudaError_t cudaMemcpyAsync(void *dst, const void *src, size_t bytes, cudaMemcpyKind k,
                             cudaStream_t s = nullptr);

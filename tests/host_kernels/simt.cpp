@@ -35,6 +35,7 @@ struct CUstream_st {
 struct CUgraph_st {
   std::vector<std::function<void()>> ops;
 };
+struct CUevent_st {};
 
 namespace shim {
 
@@ -192,8 +193,7 @@ void run_wave(unsigned first, unsigned count, dim3 grid, dim3 block, size_t smem
 
 void run_grid(dim3 grid, dim3 block, size_t smem, const std::function<void()> &body) {
   if (G != nullptr) fail("nested launch");
-  if (block.x == 0 || block.x % 32u || block.y != 1 || block.z != 1 || grid.y != 1 ||
-      grid.z != 1)
+  if (block.x == 0 || block.y != 1 || block.z != 1 || grid.y != 1 || grid.z != 1)
     fail("launch shape outside what the kernels use");
   for (unsigned first = 0; first < grid.x; first += kResident)
     run_wave(first, std::min(kResident, grid.x - first), grid, block, smem, body);
@@ -291,6 +291,26 @@ cudaError_t cudaMemcpy(void *dst, const void *src, size_t bytes, cudaMemcpyKind)
   return cudaSuccess;
 }
 cudaError_t cudaStreamSynchronize(cudaStream_t) { return cudaSuccess; }
+cudaError_t cudaMallocHost(void **p, size_t bytes) {
+  *p = std::malloc(bytes ? bytes : 1);
+  return *p ? cudaSuccess : cudaErrorMemoryAllocation;
+}
+cudaError_t cudaFreeHost(void *p) {
+  std::free(p);
+  return cudaSuccess;
+}
+cudaError_t cudaGetLastError() { return cudaSuccess; }
+// every call completes before it returns, so an event is always reached
+cudaError_t cudaEventCreateWithFlags(cudaEvent_t *e, unsigned) {
+  *e = new CUevent_st();
+  return cudaSuccess;
+}
+cudaError_t cudaEventRecord(cudaEvent_t, cudaStream_t) { return cudaSuccess; }
+cudaError_t cudaEventSynchronize(cudaEvent_t) { return cudaSuccess; }
+cudaError_t cudaEventDestroy(cudaEvent_t e) {
+  delete e;
+  return cudaSuccess;
+}
 cudaError_t cudaStreamCreateWithFlags(cudaStream_t *s, unsigned) {
   *s = new CUstream_st();
   return cudaSuccess;

@@ -6,48 +6,11 @@ import os
 import numpy as np
 import pytest
 
-import dls_inputs
-import oracle
-from oracle import orders
+from gpu_cases import make_jobs, oracle_counts
 
 pytestmark = pytest.mark.gpu
 D, V = 1, 2
 THREADS = max(1, min(16, os.cpu_count() or 1))
-
-
-def _cheap(n, vsym, k):
-    # the oracle must finish these quickly: order 9 with 2-3 rows fixed has
-    # 1e6..1e10 completions per job, order 8 with 2 rows ~1e6
-    return not (n == 9 and k <= 3) and not (n == 8 and k == 2 and not vsym)
-
-
-def make_jobs(dls, count, seed=11):
-    from paper_1709_02599_gb300 import serving
-    jobs = []
-    for spec in dls_inputs.serving_jobs(10 * count, seed=seed):
-        n, vs, k = spec["n"], spec["vsym"], spec["rows"]
-        if not _cheap(n, vs, k):
-            continue
-        built = serving.build_job(n, vs, k, spec["draws"])
-        flags = D | (V if vs else 0)
-        w = n // 2 if vs else n
-        o_order = orders.md_ad_rows(n, vsym=vs, first_rows=k)
-        o_pre, _ = oracle.sample_prefix(n, flags, o_order, k * w, spec["draws"])
-        if built is None:
-            assert o_pre is None
-            continue
-        bflags, order, prefix = built
-        o_order = orders.heuristic_complete(n, o_order[:k * w], True, vs)
-        assert [tuple(c) for c in order] == o_order and (prefix == o_pre).all()
-        jobs.append(dict(n=n, flags=flags, order=order, prefix=prefix, o_order=o_order,
-                         o_prefix=o_pre, arrival=spec["arrival"]))
-        if len(jobs) == count:
-            break
-    return jobs
-
-
-def oracle_counts(jobs):
-    return [oracle.count(j["n"], j["flags"], j["o_order"], j["o_prefix"])[0] for j in jobs]
 
 
 def test_mix_equals_alone_equals_oracle(dls):
