@@ -1,8 +1,6 @@
 """Serving: jobs of mixed order, flags and partial square, counted by the
 continuous-batching server.  Each job's count must be the same when it runs
 alone, when it runs in the mix, and in the oracle."""
-import os
-
 import numpy as np
 import pytest
 
@@ -10,7 +8,6 @@ from gpu_cases import make_jobs, oracle_counts
 
 pytestmark = pytest.mark.gpu
 D, V = 1, 2
-THREADS = max(1, min(16, os.cpu_count() or 1))
 
 
 def test_mix_equals_alone_equals_oracle(dls):
