@@ -125,15 +125,18 @@ def test_queue_shared_by_many_blocks(dls, emulated):
 
 
 def test_host_buffer_entry_and_plans(dls, emulated):
-    wl = gpu_cases.split(dls, 6, D, 5)
-    ref_c, _ = oracle.count_many(6, D, wl.oracle_order, wl.oracle_prefixes)
-    for sh in (dict(), dict(stack=1), dict(kernel=1), dict(lanes_per_prefix=4)):
-        for entry in ("host", "noalloc"):
-            rc, (c, total, _) = emulated.count(entry, 6, D, wl.order, wl.prefixes, **sh)
-            assert rc == 0 and (c == ref_c).all(), (entry, sh)
-            assert total == int(ref_c.sum()), (entry, sh)  # the plain 128-bit sum
-        rc, (c, total, _) = emulated.count("plan", 6, D, wl.order, wl.prefixes, **sh)
-        assert rc == 0 and (c == ref_c).all() and total == int(ref_c.sum()), sh
+    # order 6 (diagonal words in the search) and order 7 with both diagonals
+    # in the prefix (the fused step by default)
+    for n, after, step in ((6, 5, 1), (7, 14, 200)):
+        wl = every(gpu_cases.split(dls, n, D, after), step)
+        ref_c, _ = oracle.count_many(n, D, wl.oracle_order, wl.oracle_prefixes)
+        for sh in (dict(), dict(stack=1), dict(kernel=1), dict(lanes_per_prefix=4)):
+            for entry in ("host", "noalloc"):
+                rc, (c, total, _) = emulated.count(entry, n, D, wl.order, wl.prefixes, **sh)
+                assert rc == 0 and (c == ref_c).all(), (entry, sh)
+                assert total == int(ref_c.sum()), (entry, sh)  # the plain 128-bit sum
+            rc, (c, total, _) = emulated.count("plan", n, D, wl.order, wl.prefixes, **sh)
+            assert rc == 0 and (c == ref_c).all() and total == int(ref_c.sum()), sh
 
 
 def test_describe_launch_and_argument_errors(dls, emulated):
@@ -160,3 +163,48 @@ def test_describe_launch_and_argument_errors(dls, emulated):
             (9, o9, 17, dict(words=2)), (8, o8, 15, dict(check_every=3))):
         rc, _ = emulated.count("count", n, D, order, np.zeros((4, depth), np.uint8), **sh)
         assert rc == ERR_BAD_ARG, (n, depth, sh)
+
+
+def test_edge_cases(dls, emulated):
+    """The GPU edge-case test's inputs, with several launch shapes: an empty
+    batch, whole squares as prefixes, one cell left, invalid prefixes,
+    orders 1 to 3, odd vertically symmetric orders and order 16 with every
+    mask bit in use."""
+    from oracle import orders
+    shapes = (dict(), dict(stack=1), dict(kernel=1), dict(block_threads=32, check_every=1))
+
+    def counts(n, flags, order, pre, sh):
+        rc, res = emulated.count("count", n, flags, order, pre, **sh)
+        assert rc == 0, (n, sh)
+        return res[0]
+
+    order = dls.fill_order(6, D)
+    o_order = orders.md_ad_rows(6)
+    ident = np.array([orders.identity(6)], np.uint8)
+    full, _ = oracle.extend(6, D, o_order, ident, 36)
+    bad = full[:5].copy()
+    bad[:, 20] = (bad[:, 20] + 1) % 6
+    ok, _ = oracle.extend(6, D, o_order, ident, 10)
+    inval = ok[:40].copy()
+    inval[::2, 7] = 9
+    inval[1::2, 9] = inval[1::2, 8]
+    o16 = [(0, j) for j in range(16)] + [(1, 1), (1, 14), (2, 2), (15, 0), (15, 15), (3, 5)]
+    ref16 = oracle.count(16, D, o16, list(range(16)))[0]
+    for sh in shapes:
+        assert len(counts(6, D, order, np.zeros((0, 6), np.uint8), sh)) == 0
+        pre = np.concatenate([full, bad])
+        c = counts(6, D, order, pre, sh)
+        assert (c == oracle.count_many(6, D, o_order, pre)[0]).all() and c[:128].sum() == 128
+        assert (counts(6, D, order, full[:, :35], sh) == 1).all()
+        pre = np.concatenate([ok[:40], inval])
+        c = counts(6, D, order, pre, sh)
+        assert (c == oracle.count_many(6, D, o_order, pre)[0]).all() and (c[40:] == 0).all()
+        assert counts(1, D, [(0, 0)], np.zeros((1, 0), np.uint8), sh)[0] == 1
+        for n in (2, 3):
+            o = dls.fill_order(n, D)
+            assert counts(n, D, o, np.arange(n, dtype=np.uint8)[None], sh)[0] == 0
+        for n in (5, 7):
+            o = dls.fill_order(n, D | V)
+            assert counts(n, D | V, o, np.arange(n // 2, dtype=np.uint8)[None], sh)[0] == 0
+        c = counts(16, D, o16, np.arange(16, dtype=np.uint8)[None], sh)
+        assert c[0] == ref16, sh
