@@ -208,3 +208,27 @@ def test_edge_cases(dls, emulated):
             assert counts(n, D | V, o, np.arange(n // 2, dtype=np.uint8)[None], sh)[0] == 0
         c = counts(16, D, o16, np.arange(16, dtype=np.uint8)[None], sh)
         assert c[0] == ref16, sh
+
+
+def test_bench_configuration_sample(dls, emulated):
+    """The benchmark's launch as the autotuner chose it on the GB300 (split
+    depth 25, squared-count order after the split, fused step, blocks of
+    64) on every 100th prefix of one of its 64 diagonal fillings."""
+    import dls_inputs
+    from oracle import orders
+    from paper_1709_02599_gb300 import autotune
+    n, depth = 8, 25
+    order0 = dls.fill_order(n, D)
+    ident = np.arange(n, dtype=np.uint8)[None]
+    diags, _ = dls.extend_prefixes(n, D, order0, ident, n + (n - 1))
+    pick = dls_inputs.choose(len(diags), 64, 0)[dls_inputs.choose(64, 1, 3)]
+    order, pre, _ = autotune.build_problem(n, D, order0, diags[pick], depth, "heuristic_sq")
+    o_order = orders.heuristic_complete(n, orders.md_ad_rows(n)[:depth], squares=True)
+    o_diags, _ = oracle.extend(n, D, orders.md_ad_rows(n),
+                               np.array([orders.identity(n)], np.uint8), n + (n - 1))
+    o_pre, _ = oracle.extend(n, D, o_order, o_diags[pick], depth)
+    wl = every(gpu_cases.Workload(n, D, order, pre, o_order, o_pre), 100)
+    rc, info = emulated.count("describe", n, D, wl.order, wl.prefixes, block_threads=64)
+    assert rc == 0 and info["run"] == 2 and info["fused"] == 1
+    check_counts(emulated, wl, n, D, [dict(block_threads=64), dict(block_threads=64, fuse=-1),
+                                      dict(kernel=1, block_threads=64)])
