@@ -139,3 +139,17 @@ def test_quorum_of_the_two_kernel_families_on_the_stand_in(dls, problem, emulate
                                   batch=64, counter=kernels,
                                   quorum=(Launch(), Launch(kernel=KERNEL_PLAIN, stack=1)))
     assert (res["counts"] == ref).all() and res["disagreements"] == 0
+
+
+@pytest.mark.gpu
+def test_default_counter_on_the_gpu(dls, tmp_path):
+    """The default counter (the library on the GPU) with the two kernel
+    families as the quorum."""
+    from paper_1709_02599_gb300 import Launch, KERNEL_PLAIN, workunits
+    wl = gpu_cases.split(dls, 7, D, 10)
+    ref, _ = oracle.count_many(7, D, wl.oracle_order, wl.oracle_prefixes, threads=8)
+    res = workunits.run_workunits(7, D, wl.order, wl.prefixes, str(tmp_path / "g.jsonl"),
+                                  batch=1000,
+                                  quorum=(Launch(), Launch(kernel=KERNEL_PLAIN, stack=1)))
+    assert (res["counts"] == ref).all() and res["total"] == 171200
+    assert res["disagreements"] == 0 and res["units"] == 3
