@@ -65,7 +65,7 @@ typedef enum {
     DLS_ERR_BAD_ARG = 3,      /* NULL pointer, negative size, bad depth ...  */
     DLS_ERR_CAPACITY = 4,     /* output buffer too small; *n_out = needed    */
     DLS_ERR_CUDA = 5,         /* a CUDA call failed (dls_last_cuda_error())  */
-    DLS_ERR_TIMEOUT = 6,      /* a bounded wait or budget ran out            */
+    DLS_ERR_TIMEOUT = 6,      /* reserved: no entry point returns it         */
     DLS_ERR_ABORTED = 7,      /* stopped through dls_server_abort()          */
     DLS_ERR_NO_MEMORY = 8,    /* host or device allocation failed            */
     DLS_ERR_BAD_STATE = 9,    /* object used after release / wrong sequence  */
@@ -429,6 +429,13 @@ int dls_server_step(dls_server *srv);
 int dls_server_poll(dls_server *srv, int64_t *ids, uint64_t *counts, int cap,
                     int *n_done);
 int dls_server_get_stats(dls_server *srv, dls_server_stats *out);
+/* Stops the server; may be called from any thread, also while another
+ * thread is inside dls_server_step().  The next dls_server_step() reads the
+ * running epoch's results and returns DLS_ERR_ABORTED instead of launching
+ * another; so do all later steps and submissions.  Jobs completed so far
+ * stay available to dls_server_poll(); unfinished ones never complete.
+ * Then call dls_server_destroy().  Errors: BAD_ARG (NULL). */
+int dls_server_abort(dls_server *srv);
 /* Waits for the running epoch and frees everything. */
 void dls_server_destroy(dls_server *srv);
 

@@ -148,6 +148,7 @@ def load():
         "dls_server_step": (c_int, [vp]),
         "dls_server_poll": (c_int, [vp, i64p, u64p, c_int, ctypes.POINTER(c_int)]),
         "dls_server_get_stats": (c_int, [vp, ctypes.POINTER(ServerStats)]),
+        "dls_server_abort": (c_int, [vp]),
         "dls_server_destroy": (None, [vp]),
         "dls_plan_create": (c_int, [ctypes.POINTER(vp), c_int, c_u32, u8p, c_int, vp,
                                     c_int, c_i64, vp, vp, ctypes.POINTER(LaunchT)]),

@@ -29,6 +29,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -275,6 +276,8 @@ struct dls_server {
   std::condition_variable cv;
   bool stopping = false;
   std::vector<std::thread> workers;
+  // set by dls_server_abort from any thread; read without the lock
+  std::atomic<bool> aborted{false};
 };
 
 // Splits a submitted job into work items (worker thread, no lock held but
@@ -493,6 +496,7 @@ int dls_server_submit(dls_server *s, int n, uint32_t flags, const uint8_t *order
                       int order_len, const uint8_t *prefix, int depth,
                       int64_t *job_id) {
   if (s == nullptr || job_id == nullptr) return DLS_ERR_BAD_ARG;
+  if (s->aborted.load()) return DLS_ERR_ABORTED;
   OrderInfo info;
   int rc = validate_order(n, flags, order, order_len, &info);
   if (rc) return rc;
@@ -545,6 +549,7 @@ int dls_server_step(dls_server *s) {
   std::lock_guard<std::mutex> g(s->mu);
   int rc = sv_collect(s);
   if (rc) return rc;
+  if (s->aborted.load()) return DLS_ERR_ABORTED;  // no further epoch
   cudaError_t e;
   int prev;
   if (cudaGetDevice(&prev) == cudaSuccess && prev != s->dev) cudaSetDevice(s->dev);
@@ -720,6 +725,12 @@ int dls_server_get_stats(dls_server *s, dls_server_stats *out) {
   for (auto *j : s->active) act += (j != nullptr);
   out->active = act;
   out->free_arena_bytes = s->free_chunks.size() * s->cfg.chunk_bytes;
+  return DLS_OK;
+}
+
+int dls_server_abort(dls_server *s) {
+  if (s == nullptr) return DLS_ERR_BAD_ARG;
+  s->aborted.store(true);
   return DLS_OK;
 }
 

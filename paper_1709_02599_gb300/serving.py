@@ -70,6 +70,11 @@ class Server:
             if time.perf_counter() - t0 > timeout_s:
                 raise TimeoutError("server did not drain in %.0f s" % timeout_s)
 
+    def abort(self):
+        """Stop the server (dls_server_abort; any thread): the next step
+        raises DlsError with code ABORTED instead of launching an epoch."""
+        _lib.check(lib().dls_server_abort(self._h), "dls_server_abort")
+
     def close(self):
         if self._h:
             lib().dls_server_destroy(self._h)

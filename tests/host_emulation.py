@@ -135,7 +135,7 @@ class Emulated:
     def serve(self, jobs, mode="all", max_jobs=0, arena_bytes=0, chunk_bytes=0, budget=0,
               block_threads=0, items_per_job=0, max_order=0):
         """jobs: dicts with n, flags, order (uint8 [L, 2]), prefix (uint8
-        [d]); mode: all, stream or alone (kernel_check.cpp).  Returns
+        [d]); mode: all, stream, alone or abort (kernel_check.cpp).  Returns
         (create_rc, submit_rcs, {job id: count}, stats)."""
         path = os.path.join(self.d, "jobs.txt")
         with open(path, "w") as f:
@@ -152,7 +152,7 @@ class Emulated:
         create = int(lines[0].split()[1])
         if create != 0:
             return create, [], {}, None
-        rcs, done, stats = [], {}, None
+        rcs, done, stats, stats_step = [], {}, None, None
         for line in lines[1:]:
             w = line.split()
             if not w:
@@ -165,5 +165,9 @@ class Emulated:
                 stats = dict(zip(["submitted", "admitted", "completed", "epochs",
                                   "max_pending", "min_free_arena"], map(int, w[1:])))
             elif w[0] == "step":
-                raise AssertionError("dls_server_step returned %s" % w[1])
+                if mode != "abort":
+                    raise AssertionError("dls_server_step returned %s" % w[1])
+                stats_step = int(w[1])
+        if stats is not None and stats_step is not None:
+            stats["step_rc"] = stats_step
         return create, rcs, done, stats

@@ -23,7 +23,9 @@
 // of jobs.txt (one per line: n flags order_len depth, then the order's
 // 2 * order_len bytes and the prefix's depth bytes, as integers).  mode
 // "all" submits every job before the first step, "stream" one job per
-// step, "alone" the next job only once the previous one is done.  Steps
+// step, "alone" the next job only once the previous one is done, "abort"
+// every job, then dls_server_abort from another thread once two epochs have
+// run (and one more submission after the next step).  Steps
 // until every job is done (at most 100000 steps).  Prints "rc R" for each
 // submission in order, then "job ID COUNT" per completed job, then "stats
 // submitted admitted completed epochs max_pending min_free_arena" (the last
@@ -32,6 +34,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <string>
+#include <thread>
 #include <utility>
 #include <vector>
 
@@ -126,16 +129,36 @@ int run_serve(int argc, char **argv) {
     std::printf("rc %d\n", r);
     if (r == 0) ++accepted;
   };
-  if (mode == "all")
+  if (mode == "all" || mode == "abort")
     for (; next < jobs.size(); ++next) submit(jobs[next]);
   int64_t max_pending = 0;
+  bool abort_sent = false;
   size_t min_free = (size_t)-1;
   for (int step = 0; step < 100000 && ((int64_t)done.size() < accepted || next < jobs.size());
        ++step) {
     if (next < jobs.size() &&
         (mode == "stream" || (mode == "alone" && (int64_t)done.size() == accepted)))
       submit(jobs[next++]);
+    if (mode == "abort" && !abort_sent) {
+      dls_server_stats ran;
+      dls_server_get_stats(srv, &ran);
+      if (ran.epochs >= 2) {
+        std::thread stopper([srv]() { dls_server_abort(srv); });
+        stopper.join();
+        abort_sent = true;
+      }
+    }
     rc = dls_server_step(srv);
+    if (mode == "abort" && rc == DLS_ERR_ABORTED) {
+      std::printf("step %d\n", rc);
+      submit(jobs[0]);
+      int64_t ids[64];
+      uint64_t counts[64];
+      int got = 0;
+      dls_server_poll(srv, ids, counts, 64, &got);
+      for (int k = 0; k < got; ++k) done.emplace_back(ids[k], counts[k]);
+      break;
+    }
     dls_server_stats now;
     dls_server_get_stats(srv, &now);
     max_pending = std::max(max_pending, now.pending);

@@ -16,7 +16,7 @@ from gpu_cases import make_jobs, oracle_counts
 from oracle import orders
 
 D, V = 1, 2
-ERR_INVALID_N, ERR_BAD_ORDER = 1, 2
+ERR_INVALID_N, ERR_BAD_ORDER, ERR_ABORTED = 1, 2, 7
 SMALL_ARENA = dict(arena_bytes=4 << 20, max_jobs=64)
 
 
@@ -94,3 +94,18 @@ def test_hourglass_classes_against_oracle(dls, emulated):
     other = [c for c in full if c not in hc][0]
     rc, _ = emulated.classes(6, D, np.array(hc[:-1] + [other], np.uint8), hg)
     assert rc == ERR_BAD_ORDER
+
+
+def test_abort_from_another_thread(dls, emulated):
+    """dls_server_abort from another thread once two epochs have run: the next step
+    and later submissions return DLS_ERR_ABORTED and no epoch follows; the
+    jobs completed by then keep their exact counts."""
+    jobs = make_jobs(dls, 16, seed=5)
+    ref = oracle_counts(jobs)
+    create, rcs, done, st = emulated.serve(jobs, mode="abort", budget=16, items_per_job=32,
+                                           **SMALL_ARENA)
+    assert create == 0
+    assert rcs == [0] * len(jobs) + [ERR_ABORTED]
+    assert st["step_rc"] == ERR_ABORTED and st["epochs"] == 2
+    assert len(done) == st["completed"] < len(jobs)
+    assert all(done[k] == ref[k] for k in done)

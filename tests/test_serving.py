@@ -88,3 +88,31 @@ def test_server_rejects_bad_jobs(dls):
     res = dict(srv.drain())
     assert res == {a: 0, b: 0}
     srv.close()
+
+
+def test_abort_from_another_thread(dls):
+    import threading
+    from paper_1709_02599_gb300 import serving
+    jobs = make_jobs(dls, 16, seed=5)
+    ref = oracle_counts(jobs)
+    srv = serving.Server(budget=16, items_per_job=32)
+    ids = [srv.submit(j["n"], j["flags"], j["order"], j["prefix"]) for j in jobs]
+    got = {}
+    for _ in range(100000):
+        srv.step()
+        got.update(dict(srv.poll()))
+        if srv.stats()["epochs"] >= 2:
+            break
+    stopper = threading.Thread(target=srv.abort)
+    stopper.start()
+    stopper.join()
+    with pytest.raises(dls.DlsError) as e:
+        srv.step()
+    assert e.value.code == 7
+    with pytest.raises(dls.DlsError) as e:
+        srv.submit(jobs[0]["n"], jobs[0]["flags"], jobs[0]["order"], jobs[0]["prefix"])
+    assert e.value.code == 7
+    got.update(dict(srv.poll()))
+    srv.close()
+    want = dict(zip(ids, ref))
+    assert all(got[i] == want[i] for i in got)
