@@ -153,4 +153,52 @@ def run_workunits(n, flags, order, prefixes, path, batch=1 << 20, quorum=None, c
             "disagreements": disagreements}
 
 
-__all__ = ["run_workunits", "gpu_counter"]
+def count_split(n, flags, depth, path, batch=1 << 20, quorum=1, counter=None,
+                first_rows=1):
+    """Section 5.2's run: row 0 fixed to 0..n-1, the cells after it in the
+    Section 2.3 order (Fig. 1 for order 9), every valid assignment of the
+    first `depth` cells one prefix, counted through run_workunits (quorum 2:
+    the batched kernel and the plain per-position one).  Returns
+    run_workunits' dict plus 'prefixes', 'row0_fixed' (the exact count with
+    row 0 fixed) and 'squares' (x the row-0 multiplier)."""
+    from . import (KERNEL_PLAIN, ORDER_HEURISTIC, Launch, extend_prefixes, fill_order,
+                   multiplier)
+    order = fill_order(n, flags, ORDER_HEURISTIC, first_rows)
+    w = n // 2 if flags & 2 else n
+    base = np.arange(w, dtype=np.uint8)[None]
+    prefixes, _ = extend_prefixes(n, flags, order, base, depth)
+    launches = (Launch(), Launch(kernel=KERNEL_PLAIN, stack=1))[:max(1, quorum)]
+    res = run_workunits(n, flags, order, prefixes, path, batch=batch, quorum=launches,
+                        counter=counter)
+    res["prefixes"] = len(prefixes)
+    res["row0_fixed"] = res["total"]
+    res["squares"] = res["total"] * multiplier(n, flags)
+    return res
+
+
+def main(argv=None):
+    """python -m paper_1709_02599_gb300.workunits --n 9 --depth 19
+    --checkpoint dls9.jsonl [--quorum 2] prints one JSON line: the exact
+    count with row 0 fixed and the number of squares.  Interrupted, the same
+    command resumes from the checkpoint."""
+    import argparse
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, required=True)
+    ap.add_argument("--vsym", action="store_true")
+    ap.add_argument("--depth", type=int, required=True,
+                    help="prefix length, row 0 included (order 9, Section 5.2: 19)")
+    ap.add_argument("--checkpoint", required=True)
+    ap.add_argument("--batch", type=int, default=1 << 20)
+    ap.add_argument("--quorum", type=int, default=1, choices=(1, 2))
+    a = ap.parse_args(argv)
+    flags = 1 | (2 if a.vsym else 0)
+    res = count_split(a.n, flags, a.depth, a.checkpoint, batch=a.batch, quorum=a.quorum)
+    print(json.dumps({k: v for k, v in res.items() if k != "counts"}))
+    return 0
+
+
+__all__ = ["run_workunits", "gpu_counter", "count_split"]
+
+
+if __name__ == "__main__":
+    main()

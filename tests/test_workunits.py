@@ -153,3 +153,32 @@ def test_default_counter_on_the_gpu(dls, tmp_path):
                                   quorum=(Launch(), Launch(kernel=KERNEL_PLAIN, stack=1)))
     assert (res["counts"] == ref).all() and res["total"] == 171200
     assert res["disagreements"] == 0 and res["units"] == 3
+
+
+def test_count_split_on_the_stand_in(dls, emulated, tmp_path):
+    """count_split (the command line's run): order 6 split 4 cells past row 0,
+    a quorum of the two kernel families on the stand-in runtime."""
+    from paper_1709_02599_gb300 import ORDER_HEURISTIC, workunits
+    order = dls.fill_order(6, D, ORDER_HEURISTIC)
+
+    def kernels(prefixes, launch):
+        rc, res = emulated.count("count", 6, D, order, prefixes, **dataclasses.asdict(launch))
+        assert rc == 0
+        return res[0]
+
+    res = workunits.count_split(6, D, 10, str(tmp_path / "h.jsonl"), batch=16, quorum=2,
+                                counter=kernels)
+    assert res["row0_fixed"] == 128 and res["squares"] == 92160
+    assert res["disagreements"] == 0 and res["units"] == (res["prefixes"] + 15) // 16
+
+
+def test_count_split_makes_the_order9_workunits(dls, tmp_path):
+    """Section 5.2: row 0 and the first 10 cells of the Fig. 1 order give
+    1 255 884 workunits (the number the assignments of those cells have)."""
+    from paper_1709_02599_gb300 import workunits
+
+    def zeros(prefixes, launch):
+        return np.zeros(len(prefixes), np.uint64)
+
+    res = workunits.count_split(9, D, 19, str(tmp_path / "i.jsonl"), counter=zeros)
+    assert res["prefixes"] == 1255884 and res["units"] == 2 and res["total"] == 0
