@@ -7,6 +7,13 @@ Every hourglass (row 0, both diagonals, last row) is enumerated by the prefix
 split, dls_hourglass_classes keeps the canonical ones with their class sizes
 (GPU), dls_count counts the completions of the canonical ones (GPU), and the
 total is the sum of class size x completions (Corollary 1).
+
+For orders whose hourglasses do not fit in memory at once (order 9 has
+1.49e9), count_symmetry_broken_resumable does the same in workunits.  A
+workunit is a batch of short prefixes of the hourglass order (row 0 and the
+main diagonal).  Each is extended to its hourglasses, the canonical ones are
+kept, and their weighted completions are counted.  The batches go through
+workunits.run_workunits, with its checkpoint and optional quorum.
 """
 import ctypes
 
@@ -80,3 +87,113 @@ def count_symmetry_broken(n, flags=DIAGONAL, launch=None, min_items=1 << 20):
             "class_size_sum": int(sizes.sum().item()), "max_class": int(sz.max()) if len(sz) else 0,
             "squares_counted": int(ct.sum()), "items": int(len(items)), "split_depth": depth,
             "order": order, "hourglass_values": hg, "class_sizes": sizes.cpu().numpy()}
+
+
+def hourglass_order(n, flags):
+    """The hourglass cells (row 0, main diagonal, anti-diagonal, last row;
+    left half with vertical symmetry) followed by the other cells in the
+    Section 2.3 order.  Returns (order, number of hourglass cells)."""
+    vsym = bool(flags & VSYM)
+    k = hourglass_len(n, vsym)
+    order = fill_order(n, flags, ORDER_HOURGLASS)
+    return order_complete(n, flags, order, k, ORDER_HEURISTIC), k
+
+
+def weighted_counter(n, flags, order, k, classes_fn=None, count_fn=None, min_items=1 << 20):
+    """counter(bases, launch) for workunits.run_workunits.  bases are prefixes
+    of the first cells of `order` (k hourglass cells first).  For each base
+    it returns the sum, over the canonical hourglasses that extend it, of
+    class size x completions (Corollary 1).
+
+    classes_fn(hourglasses) -> class sizes, and count_fn(prefixes, launch) ->
+    completion counts; both default to the library on the GPU."""
+    order = np.ascontiguousarray(order, dtype=np.uint8).reshape(-1, 2)
+    if classes_fn is None:
+        def classes_fn(hg):
+            import torch
+            return hourglass_classes(n, flags, order[:k],
+                                     torch.from_numpy(hg).cuda()).cpu().numpy()
+    if count_fn is None:
+        def count_fn(prefixes, launch):
+            import torch
+            c = dls_count(n, flags, order, torch.from_numpy(prefixes).cuda(), launch=launch)
+            torch.cuda.synchronize()
+            return c.cpu().numpy()
+
+    def counter(bases, launch):
+        bases = np.ascontiguousarray(bases, dtype=np.uint8)
+        out = np.zeros(len(bases), np.uint64)
+        hg, hpar = extend_prefixes(n, flags, order, bases, k)
+        if len(hg) == 0:
+            return out
+        sizes = np.asarray(classes_fn(hg)).astype(np.int64)
+        canon = np.nonzero(sizes > 0)[0]
+        if len(canon) == 0:
+            return out
+        reps, rbase, rsize = hg[canon], hpar[canon], sizes[canon].astype(np.uint64)
+        # split the representatives further while there are few of them
+        # (Section 5.2), so that every lane has work
+        depth, items, parent = k, reps, np.arange(len(reps), dtype=np.int64)
+        while len(items) < min_items and depth < len(order) - 2:
+            nxt, par = extend_prefixes(n, flags, order, items, depth + 1)
+            if len(nxt) == 0:
+                break
+            items, parent, depth = nxt, parent[par], depth + 1
+        per_rep = np.zeros(len(reps), np.uint64)
+        if len(items) and len(items[0]) == depth:
+            np.add.at(per_rep, parent, np.asarray(count_fn(items, launch), dtype=np.uint64))
+        np.add.at(out, rbase, rsize * per_rep)
+        return out
+
+    return counter
+
+
+def count_symmetry_broken_resumable(n, flags, path, batch=64, quorum=1, base_depth=None,
+                                    classes_fn=None, count_fn=None, min_items=1 << 20):
+    """count_symmetry_broken in workunits of `batch` base prefixes (row 0
+    and the main diagonal by default), checkpointed at `path`.  Returns
+    workunits.run_workunits' dict with 'total' = squares with row 0 fixed,
+    plus 'bases' and 'base_depth'."""
+    from . import KERNEL_PLAIN
+    from .workunits import run_workunits
+    order, k = hourglass_order(n, flags)
+    w = n // 2 if flags & VSYM else n
+    if base_depth is None:
+        base_depth = w
+        while base_depth < k and int(order[base_depth][0]) == int(order[base_depth][1]):
+            base_depth += 1  # the main-diagonal cells after row 0
+    if not w <= base_depth <= k:
+        raise ValueError("base_depth must lie between row 0 and the hourglass")
+    ident = np.arange(w, dtype=np.uint8)[None]
+    bases, _ = extend_prefixes(n, flags, order, ident, base_depth)
+    launches = (Launch(), Launch(kernel=KERNEL_PLAIN, stack=1))[:max(1, quorum)]
+    res = run_workunits(n, flags, order, bases, path, batch=batch, quorum=launches,
+                        counter=weighted_counter(n, flags, order, k, classes_fn, count_fn,
+                                                 min_items))
+    res["bases"] = int(len(bases))
+    res["base_depth"] = int(base_depth)
+    return res
+
+
+def main(argv=None):
+    """python -m paper_1709_02599_gb300.symmetry --n 9 --checkpoint sym9.jsonl
+    prints one JSON line: the squares with row 0 fixed, counted through
+    canonical hourglasses in resumable workunits."""
+    import argparse
+    import json
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, required=True)
+    ap.add_argument("--vsym", action="store_true")
+    ap.add_argument("--checkpoint", required=True)
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--quorum", type=int, default=1, choices=(1, 2))
+    a = ap.parse_args(argv)
+    flags = DIAGONAL | (VSYM if a.vsym else 0)
+    res = count_symmetry_broken_resumable(a.n, flags, a.checkpoint, batch=a.batch,
+                                          quorum=a.quorum)
+    print(json.dumps({k: v for k, v in res.items() if k != "counts"}))
+    return 0
+
+
+if __name__ == "__main__":
+    main()

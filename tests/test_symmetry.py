@@ -70,3 +70,12 @@ def test_vsym10_total(dls, golden):
     ref = oracle.hourglass_classes(10, D | V, full, res["hourglass_values"][idx], threads=THREADS)
     assert (res["class_sizes"][idx].astype(np.int64) == ref).all()
     assert res["total"] == golden["vsym10_row0_fixed"]
+
+
+def test_order8_total_resumable(dls, golden, tmp_path):
+    """The same total through workunits of base prefixes (row 0 and the main
+    diagonal: 1 854 bases), the class sizes and completions on the GPU."""
+    from paper_1709_02599_gb300 import symmetry
+    res = symmetry.count_symmetry_broken_resumable(8, D, str(tmp_path / "sym8.jsonl"), batch=256)
+    assert res["bases"] == 1854 and res["base_depth"] == 15 and res["units"] == 8
+    assert res["total"] == golden["dls8_row0_fixed"]
