@@ -15,7 +15,14 @@ persistent kernel launched from a CUDA graph.  Reported:
 * e2e       -- through dls_count_host (host buffers, copies inside the timed
                region);
 * roofline  -- integer-issue roofline of the search kernel;
-* cpu_baseline -- the oracle on the host cores, on a bounded sample.
+* oracle_check -- the oracle recounts 4 of the 64 diagonal fillings from its
+               own order and split: prefixes and counts must agree exactly
+               (the bench fails otherwise);
+* cpu_baseline -- the oracle's rate on that sample, on the host cores;
+* workloads.vsym10_rows2 -- the same for the largest single-GPU
+               configuration: vertically symmetric order 10, 2000 seed-drawn
+               fillings of rows 1-2, the 20 smallest checked by the oracle;
+* serving   -- a replay of the serving mix with latency percentiles.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -70,6 +77,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-config4", action="store_true",
+                    help="skip the second leg (vertically symmetric order 10, 2000 rows-1-2 "
+                         "prefixes)")
     ap.add_argument("--workload", default="dls8_diag64", choices=["dls8_diag64", "vsym10_rows2"])
     ap.add_argument("--diagonals", type=int, default=0,
                     help="base prefixes per rank (0 = the workload's own: 64 diagonal "
@@ -101,11 +111,15 @@ def dist_env():
 
 class Dls8Diag64:
     """Order 8, row 0 identity, `units` seed-drawn main-diagonal fillings
-    (row 0 + main diagonal), split 20 cells past row 0 by default."""
+    (row 0 + main diagonal), split 20 cells past row 0 by default.  The
+    oracle checks the counts of 4 seed-chosen fillings of the 64."""
     name, n, flags, units, unit_name = "dls8_diag64", 8, 1, DIAGS, "diagonal fillings"
     default_depth = 8 + AFTER_ROW0
     depths = [8 + 14, 8 + 17, 8 + 20, 8 + 23]
     first_rows = 1
+    check_units = 4
+    check_rule = "4 seed-chosen diagonal fillings of the 64"
+    oracle_extra = 0          # cells the oracle splits deeper for its threads
 
     def base_depth(self):
         return self.n + (self.n - 1)
@@ -117,9 +131,16 @@ class Dls8Diag64:
         picks = dls_inputs.choose(len(allb), k, seed)
         return order, allb[picks]
 
-    def oracle_sample(self, seed, n_units, depth, suffix):
-        """The oracle's own order and prefixes for n_units of the run's base
-        prefixes, split at `depth` (cells after the split in `suffix` order)."""
+    def check_bases(self, seed, gpu_base_sums):
+        """Indices (into the run's base prefixes) of the bases the oracle
+        checks."""
+        return dls_inputs.choose(len(gpu_base_sums), self.check_units, seed + 1000)
+
+    def oracle_sample(self, seed, units, base_idx, depth, suffix):
+        """The oracle's own order and prefixes for the run's base prefixes
+        `base_idx` (of the `units` drawn with `seed`), split at `depth` (cells
+        after the split in `suffix` order).  Returns (order, prefixes,
+        parents): parents[k] = position in base_idx of prefix k's base."""
         import oracle
         from oracle import orders
         vs = bool(self.flags & 2)
@@ -129,33 +150,78 @@ class Dls8Diag64:
                                                 squares=suffix == "heuristic_sq")
         ident = np.array([orders.identity(self.n, vs)], np.uint8)
         allb, _ = oracle.extend(self.n, self.flags, o_order, ident, self.base_depth())
-        picks = dls_inputs.choose(len(allb), self.units, seed)
-        sub = picks[dls_inputs.choose(len(picks), n_units, seed + 1000)]
-        pre, _ = oracle.extend(self.n, self.flags, o_order, allb[sub], depth)
-        return o_order, pre
+        picks = dls_inputs.choose(len(allb), units, seed)
+        pre, par = oracle.extend(self.n, self.flags, o_order, allb[picks][np.asarray(base_idx)],
+                                 depth)
+        return o_order, pre, par
 
 
 class Vsym10Rows2(Dls8Diag64):
     """Order 10, vertically symmetric, row 0 identity; `units` seed-drawn
-    fillings of rows 1 and 2 out of the 2 153 120 valid ones."""
+    fillings of rows 1 and 2 out of the 2 153 120 valid ones.  The oracle
+    checks the 20 with the smallest GPU counts."""
     name, n, flags, units, unit_name = "vsym10_rows2", 10, 3, 2000, "rows-1-2 prefixes"
     default_depth = 19
     depths = [17, 19, 21, 23]
     first_rows = 3
+    check_units = 20
+    check_rule = "the 20 rows-1-2 prefixes of the 2000 with the smallest GPU counts"
+    oracle_extra = 4
 
     def base_depth(self):
         return 15
+
+    def check_bases(self, seed, gpu_base_sums):
+        return np.argsort(np.asarray(gpu_base_sums, dtype=np.uint64), kind="stable")[
+            :self.check_units]
 
 
 SPECS = {"dls8_diag64": Dls8Diag64(), "vsym10_rows2": Vsym10Rows2()}
 
 
-def run_oracle(spec, o_order, pre, threads):
+def run_oracle(spec, o_order, pre, threads, extra=0):
+    """Oracle counts of `pre` (summed back from `extra` cells deeper, where
+    the split is finer for the threads).  Returns (counts per prefix, nodes,
+    seconds)."""
     import oracle
     t0 = time.perf_counter()
-    counts, nodes = oracle.count_many(spec.n, spec.flags, o_order, pre, threads=threads)
-    dt = time.perf_counter() - t0
-    return int(counts.sum()), int(nodes.sum()), dt
+    if extra:
+        depth = min(pre.shape[1] + extra, len(o_order) - 1)
+        sub, par = oracle.extend(spec.n, spec.flags, o_order, pre, depth)
+        c, nd = oracle.count_many(spec.n, spec.flags, o_order, sub, threads=threads)
+        counts = np.zeros(len(pre), np.uint64)
+        np.add.at(counts, par, c)
+        nodes = int(nd.sum())
+    else:
+        counts, nd = oracle.count_many(spec.n, spec.flags, o_order, pre, threads=threads)
+        nodes = int(nd.sum())
+    return counts, nodes, time.perf_counter() - t0
+
+
+def oracle_check(spec, seed, units, depth, suffix, pre, par, counts, threads):
+    """The oracle counts the prefixes of the bases spec.check_bases() picks,
+    from its own order and split; they must equal the GPU's prefixes byte for
+    byte and its counts exactly (RuntimeError otherwise).  Returns the line's
+    'oracle_check' object, the oracle's rate on that sample (squares/s) and
+    the number of prefixes it counted."""
+    sums = np.zeros(units, np.uint64)
+    np.add.at(sums, par, counts)
+    idx = np.asarray(spec.check_bases(seed, sums))
+    o_order, o_pre, o_par = spec.oracle_sample(seed, units, idx, depth, suffix)
+    c, _, dt = run_oracle(spec, o_order, o_pre, threads, spec.oracle_extra)
+    agree = True
+    for k, b in enumerate(idx):
+        g = par == b
+        o = o_par == k
+        if not (g.sum() == o.sum() and (pre[g] == o_pre[o]).all()
+                and (counts[g] == c[o]).all()):
+            agree = False
+    squares = int(c.sum())
+    out = {"bases": int(len(idx)), "which": spec.check_rule, "prefixes": int(len(o_pre)),
+           "squares": squares, "agree": agree, "oracle_seconds": round(dt, 2)}
+    if not agree:
+        raise RuntimeError("oracle check failed: %s" % json.dumps(out))
+    return out, (squares / dt if dt > 0 else None), len(o_pre)
 
 
 # --------------------------------------------------------------- clocks --
@@ -301,14 +367,16 @@ def reference_arm(args):
         return 0
     threads = os.cpu_count() or 1
     spec = SPECS[args.workload]
-    o_order, pre = spec.oracle_sample(0, 1, spec.default_depth, "heuristic_sq")
+    base_idx = dls_inputs.choose(spec.units, 1, 1000)
+    o_order, pre, _ = spec.oracle_sample(0, spec.units, base_idx, spec.default_depth,
+                                         "heuristic_sq")
     for _ in range(args.warmup):
         run_oracle(spec, o_order, pre, threads)
     sq = 0
     t = 0.0
     for _ in range(args.steps):
         c, _, dt = run_oracle(spec, o_order, pre, threads)
-        sq += c
+        sq += int(c.sum())
         t += dt
     value = sq / t
     line = {
@@ -330,26 +398,16 @@ def reference_arm(args):
     return 0
 
 
-def main():
-    args = parse()
-    if args.impl == "reference":
-        return reference_arm(args)
+def run_leg(dls, spec, args, steps, stream, flush, seed, rank, ws, units=None,
+            plain_per_position=True):
+    """One workload: autotune (cached), then the graph-launched batched count
+    timed over `steps` steps, the plain launches, the host-buffer entry, the
+    roofline and the oracle check.  Returns (leg dict, step seconds, squares
+    per step, the plan's count of our kernel launches per step)."""
     import torch
-    import paper_1709_02599_gb300 as dls
-
-    ws, rank, local = dist_env()
-    if ws > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    dev = torch.cuda.current_device()
-    stream = torch.cuda.Stream()
-
     from paper_1709_02599_gb300 import autotune
-    spec = SPECS[args.workload]
     N, FLAGS = spec.n, spec.flags
-    units = args.diagonals or spec.units
-    seed = rank
+    units = units or spec.units
     order0, base = spec.product_base(dls, seed, units)
     fixed = json.loads(args.launch) if args.launch else None
     tuned = None
@@ -375,7 +433,6 @@ def main():
     d_pre = torch.from_numpy(pre).to("cuda")
     counts = torch.empty(P, dtype=torch.uint64, device="cuda")
     total = torch.empty(1, dtype=torch.uint64, device="cuda")
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     launch = dls.Launch(**cfg)
     plan = dls.Plan(N, FLAGS, order, d_pre, counts, total, launch)
     run = dls.describe_launch(N, FLAGS, order, depth, P, launch)
@@ -396,26 +453,22 @@ def main():
 
     if ws > 1:
         torch.distributed.barrier()
-    sampler = ClockSampler(gpu_bus_id(dev)) if rank == 0 else None
+    sampler = ClockSampler(gpu_bus_id(torch.cuda.current_device())) if rank == 0 else None
     if sampler:
         sampler.start()
     torch.cuda.synchronize()
     t_wall0 = time.perf_counter()
-    times = timed_steps(lambda: plan.launch(stream), stream, args.steps, flush)
+    times = timed_steps(lambda: plan.launch(stream), stream, steps, flush)
     t_wall = time.perf_counter() - t_wall0
     clocks = sampler.stop() if sampler else None
     if int(total.cpu().numpy()[0]) != squares:
         raise RuntimeError("count changed between runs")
+    counts_np = counts.cpu().numpy()
     step_s = sum(times) / len(times)
     if ws > 1:
         t = torch.tensor([step_s], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         step_s = float(t.item())
-        from paper_1709_02599_gb300 import shard
-        squares_all = shard.allreduce_total(squares)
-    else:
-        squares_all = squares
-    value = squares_all / step_s
 
     # plain one-thread-per-prefix launches on the same workload: with the same
     # search step (the batching comparison) and with the per-position step
@@ -425,7 +478,7 @@ def main():
         for _ in range(max(args.warmup, 1)):
             pplan.launch(stream)
         torch.cuda.synchronize()
-        pt = timed_steps(lambda: pplan.launch(stream), stream, args.steps, flush)
+        pt = timed_steps(lambda: pplan.launch(stream), stream, steps, flush)
         if int(total.cpu().numpy()[0]) != squares:
             raise RuntimeError("plain launch count differs")
         pplan.close()
@@ -436,37 +489,38 @@ def main():
     plain = plain_pp = None
     if not args.no_plain:
         plain = plain_leg(0)
-        if plain["kernel"] != "k_plain":
+        if plain["kernel"] != "k_plain" and plain_per_position:
             plain_pp = plain_leg(1)
 
     # end to end through the host-buffer entry point
-    e2e_step = None
+    e2e = None
     if not args.no_e2e:
         pinned_in = torch.from_numpy(pre).pin_memory()
         pinned_out = torch.empty(P, dtype=torch.int64).pin_memory()
         for _ in range(2):
             dls.count_host(N, FLAGS, order, pinned_in, pinned_out, launch, stream)
         e2e_t = []
-        for _ in range(args.steps):
+        for _ in range(steps):
             t0 = time.perf_counter()
             _, tot = dls.count_host(N, FLAGS, order, pinned_in, pinned_out, launch, stream)
             e2e_t.append(time.perf_counter() - t0)
             if tot != squares:
                 raise RuntimeError("host-buffer count differs")
         e2e_step = sum(e2e_t) / len(e2e_t)
+        e2e = {"value": squares / e2e_step, "unit": UNIT, "h2d_bytes_per_step": int(P * depth),
+               "d2h_bytes_per_step": int(P * 8), "entry": "dls_count_host"}
 
-    props = torch.cuda.get_device_properties(dev)
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
     sms = props.multi_processor_count
     sm_max_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
     peak_tops = sms * ISSUE_LANES_PER_SM * sm_max_mhz * 1e6 / 1e12
     achieved_tops = nodes * OPS_PER_NODE / step_s / 1e12
-
     # the traffic figures belong to the kernel variant they were captured on
     kernel_id = run["kernel"] + (" fused" if run.get("fused") else "")
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * step_s, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+    tkey = (spec.name, kernel_id, depth)
+    leg = {
+        "value": squares / step_s, "unit": UNIT, "steps": steps,
+        "ms_per_step": 1e3 * step_s,
         "config": {"workload": spec.name if units == spec.units else
                    "%s (profiling case: %d %s)" % (spec.name, units, spec.unit_name),
                    "n": N, "flags": "diagonal" + (", vertically symmetric" if FLAGS & 2 else ""),
@@ -478,33 +532,81 @@ def main():
                    "l2": "flushed: 256 MiB write between timed steps"},
         "plain": plain,
         "plain_per_position_step": plain_pp,
-        "e2e": None if e2e_step is None else {
-            "value": squares_all / e2e_step if ws == 1 else squares / e2e_step,
-            "unit": UNIT, "h2d_bytes_per_step": int(P * depth),
-            "d2h_bytes_per_step": int(P * 8), "entry": "dls_count_host"},
+        "e2e": e2e,
         "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops,
                      "unit": "Tops/s", "frac": achieved_tops / peak_tops,
-                     "traffic": (TRAFFIC_PER_PREFIX[(spec.name, kernel_id, depth)] * P
-                                 if (spec.name, kernel_id, depth) in TRAFFIC_PER_PREFIX
+                     "traffic": (TRAFFIC_PER_PREFIX[tkey] * P if tkey in TRAFFIC_PER_PREFIX
                                  else None),
                      "algorithmic_bytes": int(P * (depth + 8)),
                      "ops_per_node": OPS_PER_NODE,
                      "peak_from": "%d SMs x 4 schedulers x 32 lanes x %.0f MHz" % (sms, sm_max_mhz)},
-        "gpu_launches": args.steps,
         "clocks": clocks,
         "wall_s_timed_region": t_wall,
     }
     if rank == 0 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
-        o_order, opre = spec.oracle_sample(seed, 2, depth_sel, suffix_sel)
-        c, _, dt = run_oracle(spec, o_order, opre, threads)
-        line["cpu_baseline"] = {"value": c / dt, "unit": UNIT, "cores": threads,
-                                "kind": "oracle",
-                                "sample": "all %d prefixes of 2 seed-chosen %s of the %d, "
-                                          "same split and fill order as the GPU run "
-                                          "(%d squares, %.1f s)" % (len(opre), spec.unit_name,
-                                                                   units, c, dt)}
+        chk, rate, n_pre = oracle_check(spec, seed, units, depth_sel, suffix_sel, pre, par,
+                                        counts_np, threads)
+        leg["oracle_check"] = chk
+        leg["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+                               "sample": "all %d prefixes of %s, same split and fill order as "
+                                         "the GPU run (%d squares, %.1f s)"
+                                         % (n_pre, spec.check_rule, chk["squares"],
+                                            chk["oracle_seconds"])}
     plan.close()
+    return leg, step_s, squares
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    import torch
+    import paper_1709_02599_gb300 as dls
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    seed = rank
+    spec = SPECS[args.workload]
+    leg, step_s, squares = run_leg(dls, spec, args, args.steps, stream, flush, seed, rank, ws,
+                                   units=args.diagonals or spec.units)
+    if ws > 1:
+        from paper_1709_02599_gb300 import shard
+        squares_all = shard.allreduce_total(squares)
+    else:
+        squares_all = squares
+    value = squares_all / step_s
+    e2e = leg["e2e"]
+    if e2e is not None and ws > 1:
+        e2e = dict(e2e, note="per-rank rate (host timers are not reduced)")
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * step_s, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": leg["config"],
+        "plain": leg["plain"],
+        "plain_per_position_step": leg["plain_per_position_step"],
+        "e2e": e2e,
+        "roofline": leg["roofline"],
+        "gpu_launches": args.steps,
+        "clocks": leg["clocks"],
+        "wall_s_timed_region": leg["wall_s_timed_region"],
+    }
+    for k in ("oracle_check", "cpu_baseline"):
+        if k in leg:
+            line[k] = leg[k]
+    # the largest single-GPU configuration as a second leg: the vertically
+    # symmetric order-10 workload, fewer steps (one pass is ~1 s)
+    if not args.no_config4 and spec.name != "vsym10_rows2" and not args.diagonals:
+        leg4, _, _ = run_leg(dls, SPECS["vsym10_rows2"], args, min(args.steps, 5), stream, flush,
+                             seed, rank, ws, plain_per_position=False)
+        leg4["gpu_launches"] = leg4["steps"]
+        line["workloads"] = {"vsym10_rows2": leg4}
     if rank == 0 and args.serve_jobs > 0:
         line["serving"] = serving_leg(args.serve_jobs, args.serve_limit)
     if ws > 1:

@@ -323,7 +323,10 @@ int dls_count_ex(int n, uint32_t flags, const uint8_t *order, int order_len,
  * counts -- multiply by dls_multiplier() for whole-square totals).
  * Synchronous: returns after the copies back have landed.  The device
  * buffers come from a per-(device, stream) area that grows on demand and
- * lives until dls_release().  Also returns DLS_ERR_INTERNAL if the snapshot
+ * lives until dls_release().  Calls on the same stream from several host
+ * threads at once share that area (one may even reallocate it under the
+ * other's kernel) and race: serialise them, or give each thread its own
+ * stream.  Also returns DLS_ERR_INTERNAL if the snapshot
  * search reported a stack overflow (excluded by its entry bound; the kernel
  * drops the entry rather than write past its stack). */
 int dls_count_host(int n, uint32_t flags, const uint8_t *order,
@@ -331,6 +334,27 @@ int dls_count_host(int n, uint32_t flags, const uint8_t *order,
                    int64_t n_prefixes, uint64_t *h_counts,
                    dls_u128 *total_out, const dls_launch_t *cfg,
                    void *stream);
+
+/* What the last count on a work area reported.  status: DLS_OK, or
+ * DLS_ERR_INTERNAL when the snapshot search reported a stack overflow
+ * (excluded by its entry bound; the kernel drops the entry rather than write
+ * past its stack, so the counts are not to be trusted).  prefixes_started:
+ * the prefixes of which at least one work item was handed to a lane (all of
+ * them once a count has run to its end). */
+typedef struct {
+    int status;
+    int64_t prefixes_started;
+} dls_count_status;
+
+/* Status of the last count enqueued on `stream` (of the current device)
+ * through dls_count, dls_count_plain or dls_count_ex: waits for the stream,
+ * then reads the status word that each such count clears before its kernel
+ * and the kernel sets.  This is how callers of the device-buffer entries
+ * learn of a stack overflow (the host-buffer entries return it themselves).
+ * out: HOST, caller-owned.  Returns DLS_OK when *out was filled; BAD_ARG
+ * (out NULL), BAD_STATE (nothing counted on that stream since
+ * dls_release()), CUDA. */
+int dls_stream_status(void *stream, dls_count_status *out);
 
 /* ---------------------------------------------------- symmetry breaking */
 
@@ -453,8 +477,11 @@ void dls_server_destroy(dls_server *srv);
  * not both).  Synchronous.  Every call shares the array: calls that overlap
  * on the GPU race and give wrong counts, so serialise them.  The first call
  * on a device looks up the array's device address (cudaGetSymbolAddress);
- * make it before any stream capture.  Allocates no device memory and calls
- * no cudaMalloc/cudaFree. */
+ * make it before any stream capture.  After cudaDeviceReset(), call
+ * dls_release() (which forgets that address) before the next call.  Like
+ * dls_count_host() it returns DLS_ERR_INTERNAL when the snapshot search
+ * reported a stack overflow.  Allocates no device memory and calls no
+ * cudaMalloc/cudaFree. */
 #define DLS_NOALLOC_SCRATCH_BYTES (4u << 20)
 int dls_count_host_noalloc(int n, uint32_t flags, const uint8_t *order,
                            int order_len, const uint8_t *h_prefixes, int depth,
@@ -462,7 +489,8 @@ int dls_count_host_noalloc(int n, uint32_t flags, const uint8_t *order,
                            dls_u128 *total_out, const dls_launch_t *cfg,
                            void *stream);
 
-/* Free the library's per-(device, stream) work areas and cached plans. */
+/* Free the library's per-(device, stream) work areas and forget the device
+ * address of the allocation-free entry's array. */
 void dls_release(void);
 
 /* ------------------------------------------------------------ plans */
@@ -479,6 +507,11 @@ int dls_plan_create(dls_plan **plan_out, int n, uint32_t flags,
                     uint64_t *d_counts, uint64_t *d_total,
                     const dls_launch_t *cfg);
 int dls_plan_launch(dls_plan *plan, void *stream);
+/* Status of the plan's last launch (as dls_stream_status; every launch
+ * clears the plan's own status word first): waits for `stream`, the stream
+ * the plan was last launched on.  Errors: BAD_STATE (no plan), BAD_ARG,
+ * CUDA. */
+int dls_plan_status(dls_plan *plan, void *stream, dls_count_status *out);
 void dls_plan_destroy(dls_plan *plan);
 
 #ifdef __cplusplus

@@ -242,6 +242,16 @@ def release():
     lib().dls_release()
 
 
+def stream_status(stream=None):
+    """Status of the last count enqueued on ``stream`` (dls_stream_status):
+    waits for the stream; returns (status code, prefixes started).  Status
+    DLS_ERR_INTERNAL (10) means the counts are not to be trusted."""
+    out = _lib.CountStatus()
+    _lib.check(lib().dls_stream_status(_stream_handle(stream), ctypes.byref(out)),
+               "dls_stream_status")
+    return int(out.status), int(out.prefixes_started)
+
+
 class Plan:
     """One dls_count_ex call frozen into a CUDA graph (dls_plan_*)."""
 
@@ -259,6 +269,14 @@ class Plan:
 
     def launch(self, stream=None):
         _lib.check(lib().dls_plan_launch(self._h, _stream_handle(stream)), "dls_plan_launch")
+
+    def status(self, stream=None):
+        """(status code, prefixes started) of the last launch on ``stream``
+        (dls_plan_status); waits for the stream."""
+        out = _lib.CountStatus()
+        _lib.check(lib().dls_plan_status(self._h, _stream_handle(stream), ctypes.byref(out)),
+                   "dls_plan_status")
+        return int(out.status), int(out.prefixes_started)
 
     def close(self):
         if self._h:

@@ -67,6 +67,11 @@ class LaunchInfo(ctypes.Structure):
                 ("fused", ctypes.c_int)]
 
 
+class CountStatus(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int),
+                ("prefixes_started", ctypes.c_int64)]
+
+
 class ServerCfg(ctypes.Structure):
     _fields_ = [("max_jobs", ctypes.c_int),
                 ("arena_bytes", ctypes.c_size_t),
@@ -142,6 +147,7 @@ def load():
                                            ctypes.POINTER(U128), ctypes.POINTER(LaunchT), vp]),
         "dls_hourglass_classes": (c_int, [c_int, c_u32, u8p, c_int, vp, c_int64_t, vp, vp]),
         "dls_release": (None, []),
+        "dls_stream_status": (c_int, [vp, ctypes.POINTER(CountStatus)]),
         "dls_server_default_cfg": (None, [ctypes.POINTER(ServerCfg)]),
         "dls_server_create": (c_int, [ctypes.POINTER(ServerCfg), ctypes.POINTER(vp)]),
         "dls_server_submit": (c_int, [vp, c_int, c_u32, u8p, c_int, u8p, c_int, i64p]),
@@ -153,6 +159,7 @@ def load():
         "dls_plan_create": (c_int, [ctypes.POINTER(vp), c_int, c_u32, u8p, c_int, vp,
                                     c_int, c_i64, vp, vp, ctypes.POINTER(LaunchT)]),
         "dls_plan_launch": (c_int, [vp, vp]),
+        "dls_plan_status": (c_int, [vp, vp, ctypes.POINTER(CountStatus)]),
         "dls_plan_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():

@@ -29,6 +29,14 @@ bool vsym_all_zero(int n, uint32_t flags);
 // Records the text of the last CUDA error for dls_last_cuda_error().
 void set_cuda_error(const char *what);
 
+// The status code that a count's status word (bits set by the kernels)
+// stands for (dls_kernels.cu).
+int status_code(unsigned word);
+
+// Forgets the device addresses of the allocation-free entry's array
+// (dls_noalloc.cu; called by dls_release()).
+void noalloc_forget();
+
 // splitmix64 (Steele, Lea, Flood 2014), the library's counter-based
 // generator for random probes.
 uint64_t splitmix64(uint64_t x);

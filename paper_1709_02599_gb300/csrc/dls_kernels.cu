@@ -48,6 +48,15 @@
 
 namespace dls {
 
+// Status word of a count (word 1 of its work area, after the queue head):
+// bits the kernels set, read back by the host entry points and by
+// dls_stream_status / dls_plan_status.
+constexpr unsigned ST_OVERFLOW = 1u;  // a snapshot stack would have overflowed
+
+__device__ __forceinline__ void raise_status(const unsigned long long *queue, unsigned bit) {
+  atomicOr(reinterpret_cast<unsigned *>(const_cast<unsigned long long *>(queue + 1)), bit);
+}
+
 struct KParams {
   Geo g;                 // order size, admissible values, prefix length, last
   Split sp;              // item split over lanes
@@ -493,7 +502,7 @@ __global__ void __launch_bounds__(512)
       flush_count(s.prefix, s.cnt, p, lane_total);
     }
   }
-  if (ovf) *reinterpret_cast<int *>(p.queue + 1) = 1;
+  if (ovf) raise_status(p.queue, ST_OVERFLOW);
   block_reduce_add(lane_total, p.total, red);
   if (NODES) block_reduce_add(s.nodes, p.nodes, red);
 }
@@ -553,19 +562,27 @@ __global__ void __launch_bounds__(512)
       if (p.donate) snap_donate<VSYM, DG>(s, busy, p, st, tb, lane, B);
     }
   }
-  if (ovf) *reinterpret_cast<int *>(p.queue + 1) = 1;
+  if (ovf) raise_status(p.queue, ST_OVERFLOW);
   block_reduce_add(lane_total, p.total, red);
   if (NODES) block_reduce_add(s.nodes, p.nodes, red);
 }
 
 // ------------------------------------------------------------ host side --
 
+// What the last count on a work area launched (for its status query).
+struct LaunchRecord {
+  int64_t n_prefixes = -1;  // -1: nothing counted yet
+  int lanes_log2 = 0;
+  bool queued = false;      // a persistent kernel that takes items from the queue
+};
+
 struct Workspace {
-  unsigned long long *scratch = nullptr;  // [0] queue head
+  unsigned long long *scratch = nullptr;  // [0] queue head, [1] status word
   uint8_t *h2d = nullptr;                 // host-entry prefix buffer
   size_t h2d_bytes = 0;
   unsigned long long *d2h = nullptr;      // host-entry counts buffer
   size_t d2h_count = 0;
+  LaunchRecord last;
 };
 
 static std::mutex g_ws_mutex;
@@ -941,7 +958,8 @@ static int enqueue_count(int n, uint32_t flags, const uint8_t *order,
                          int64_t n_prefixes, uint64_t *d_counts,
                          uint64_t *d_total, uint64_t *d_nodes,
                          const dls_launch_t *cfg, cudaStream_t stream,
-                         unsigned long long *scratch = nullptr) {
+                         unsigned long long *scratch = nullptr,
+                         LaunchRecord *rec = nullptr) {
   if (n_prefixes > 0 && d_counts == nullptr && d_total == nullptr) return DLS_ERR_BAD_ARG;
   if (n_prefixes > 0 && depth > 0 && d_prefixes == nullptr) return DLS_ERR_BAD_ARG;
   Prepared pr;
@@ -961,21 +979,61 @@ static int enqueue_count(int n, uint32_t flags, const uint8_t *order,
     e = cudaMemsetAsync(d_counts, 0, (size_t)n_prefixes * sizeof(uint64_t), stream);
     if (e != cudaSuccess) return cuda_fail(e);
   }
-  if (pr.grid == 0) return DLS_OK;
-  if (pr.run != DLS_RUN_PLAIN) {  // queue head and / or overflow flag
-    if (scratch == nullptr) {
-      Workspace *ws = nullptr;
-      rc = get_workspace(stream, &ws);
-      if (rc) return rc;
-      scratch = ws->scratch;
-    }
-    pr.kp.queue = scratch;
-    e = cudaMemsetAsync(scratch, 0, 2 * sizeof(unsigned long long), stream);
-    if (e != cudaSuccess) return cuda_fail(e);
+  // the work area: queue head and status word, cleared for every count so
+  // that the status always describes the last one
+  Workspace *ws = nullptr;
+  if (scratch == nullptr) {
+    rc = get_workspace(stream, &ws);
+    if (rc) return rc;
+    scratch = ws->scratch;
   }
+  pr.kp.queue = scratch;
+  e = cudaMemsetAsync(scratch, 0, 2 * sizeof(unsigned long long), stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  LaunchRecord r;
+  r.n_prefixes = n_prefixes;
+  r.lanes_log2 = pr.kp.sp.lanes_log2;
+  r.queued = pr.grid != 0 && (pr.run == DLS_RUN_PERSISTENT || pr.run == DLS_RUN_SNAPSHOT);
+  if (ws != nullptr) {
+    std::lock_guard<std::mutex> g(g_ws_mutex);
+    ws->last = r;
+  }
+  if (rec != nullptr) *rec = r;
+  if (pr.grid == 0) return DLS_OK;
   void *args[] = {&pr.kp, (void *)&pr.diag};
   e = cudaLaunchKernel(pr.fn, dim3(pr.grid), dim3(pr.block), args, pr.smem, stream);
   if (e != cudaSuccess) return cuda_fail(e);
+  return DLS_OK;
+}
+
+// The status code a count's status word stands for: a stack overflow makes
+// its counts untrustworthy (DLS_ERR_INTERNAL).
+int status_code(unsigned word) {
+  if (word & ST_OVERFLOW) return DLS_ERR_INTERNAL;
+  return DLS_OK;
+}
+
+// Reads a work area's queue head and status word after `stream` has
+// finished, and fills *out from them and the record of the count.
+static int read_status(const unsigned long long *scratch, const LaunchRecord &rec,
+                       cudaStream_t stream, dls_count_status *out) {
+  if (rec.n_prefixes < 0) return DLS_ERR_BAD_STATE;
+  unsigned long long w[2] = {0ull, 0ull};
+  cudaError_t e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  e = cudaMemcpy(w, scratch, sizeof(w), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e);
+  out->status = status_code((unsigned)w[1]);
+  int64_t started = rec.n_prefixes;
+  if (rec.queued) {
+    // items handed out (warps take a few past the end); a prefix is started
+    // when its first item was
+    const int64_t lanes = (int64_t)1 << rec.lanes_log2;
+    const int64_t items = (int64_t)std::min<unsigned long long>(
+        w[0], (unsigned long long)(rec.n_prefixes * lanes));
+    started = std::min<int64_t>(rec.n_prefixes, (items + lanes - 1) / lanes);
+  }
+  out->prefixes_started = started;
   return DLS_OK;
 }
 
@@ -1083,8 +1141,6 @@ int dls_count_host(int n, uint32_t flags, const uint8_t *order,
     if (e != cudaSuccess) return cuda_fail(e);
   }
   uint64_t *d_counts = reinterpret_cast<uint64_t *>(ws->d2h);
-  e = cudaMemsetAsync(ws->scratch + 1, 0, sizeof(unsigned long long), st);
-  if (e != cudaSuccess) return cuda_fail(e);
   rc = enqueue_count(n, flags, order, order_len, ws->h2d, depth, n_prefixes,
                      d_counts, nullptr, nullptr, cfg, st);
   if (rc) return rc;
@@ -1098,7 +1154,8 @@ int dls_count_host(int n, uint32_t flags, const uint8_t *order,
   if (e != cudaSuccess) return cuda_fail(e);
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e);
-  if (flag) return DLS_ERR_INTERNAL;
+  rc = status_code((unsigned)flag);
+  if (rc) return rc;
   if (total_out) {
     dls_u128 t = {0, 0};
     if (h_counts) {
@@ -1117,6 +1174,7 @@ int dls_count_host(int n, uint32_t flags, const uint8_t *order,
 }
 
 void dls_release(void) {
+  noalloc_forget();
   std::lock_guard<std::mutex> g(g_ws_mutex);
   for (auto &kv : g_ws) {
     int cur = 0;
@@ -1130,6 +1188,24 @@ void dls_release(void) {
   g_ws.clear();
 }
 
+int dls_stream_status(void *stream, dls_count_status *out) {
+  if (out == nullptr) return DLS_ERR_BAD_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e);
+  const unsigned long long *scratch = nullptr;
+  LaunchRecord rec;
+  {
+    std::lock_guard<std::mutex> g(g_ws_mutex);
+    auto it = g_ws.find({dev, st});
+    if (it == g_ws.end()) return DLS_ERR_BAD_STATE;
+    scratch = it->second.scratch;
+    rec = it->second.last;
+  }
+  return read_status(scratch, rec, st, out);
+}
+
 // ------------------------------------------------------------------ plans
 
 }  // extern "C"
@@ -1138,7 +1214,8 @@ struct dls_plan {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaStream_t capture = nullptr;
-  unsigned long long *scratch = nullptr;  // the plan's own queue head
+  unsigned long long *scratch = nullptr;  // the plan's own queue head, status word
+  dls::LaunchRecord rec;
 };
 
 extern "C" {
@@ -1171,7 +1248,7 @@ int dls_plan_create(dls_plan **plan_out, int n, uint32_t flags,
   }
   if (rc == DLS_OK) {
     rc = enqueue_count(n, flags, order, order_len, d_prefixes, depth, n_prefixes,
-                       d_counts, d_total, nullptr, cfg, pl->capture, pl->scratch);
+                       d_counts, d_total, nullptr, cfg, pl->capture, pl->scratch, &pl->rec);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(pl->capture, &g);
     if (rc == DLS_OK && e != cudaSuccess) rc = cuda_fail(e);
@@ -1194,6 +1271,12 @@ int dls_plan_launch(dls_plan *plan, void *stream) {
   cudaError_t e = cudaGraphLaunch(plan->exec, reinterpret_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e);
   return DLS_OK;
+}
+
+int dls_plan_status(dls_plan *plan, void *stream, dls_count_status *out) {
+  if (plan == nullptr || plan->exec == nullptr) return DLS_ERR_BAD_STATE;
+  if (out == nullptr) return DLS_ERR_BAD_ARG;
+  return read_status(plan->scratch, plan->rec, reinterpret_cast<cudaStream_t>(stream), out);
 }
 
 void dls_plan_destroy(dls_plan *plan) {

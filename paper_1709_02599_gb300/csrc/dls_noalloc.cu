@@ -25,7 +25,9 @@
 // cudaGetSymbolAddress() on the first call made while that device is
 // current (the host-side symbol is only a stand-in and must never be handed
 // to a kernel).  That first call is synchronous like every call of this
-// entry point; make it before any stream capture.
+// entry point; make it before any stream capture.  dls_release() forgets
+// the addresses; after cudaDeviceReset() call it before the next call, since
+// the array can then live at another address.
 
 #include <cuda_runtime.h>
 
@@ -76,6 +78,13 @@ static int noalloc_address(unsigned char **out) {
 
 static size_t round256(size_t x) { return (x + 255u) & ~size_t(255u); }
 
+// Forgets the looked-up addresses (dls_release): after a device reset the
+// library's module can be loaded again at another address.
+void noalloc_forget() {
+  std::lock_guard<std::mutex> g(g_noalloc_mutex);
+  g_noalloc_addr.clear();
+}
+
 }  // namespace dls
 
 using namespace dls;
@@ -111,6 +120,9 @@ int dls_count_host_noalloc(int n, uint32_t flags, const uint8_t *order,
       return DLS_ERR_CUDA;
     }
   }
+  // word 1 of the array is the count's status word (the snapshot search's
+  // stack-overflow flag); the launch clears it, and it is read back with the
+  // counts
   rc = enqueue_count_with_scratch(n, flags, order, order_len, d_pre, depth, n_prefixes,
                                   d_counts, cfg, st, queue);
   if (rc) return rc;
@@ -128,11 +140,21 @@ int dls_count_host_noalloc(int n, uint32_t flags, const uint8_t *order,
       return DLS_ERR_CUDA;
     }
   }
+  unsigned long long status = 0ull;
+  e = cudaMemcpyAsync(&status, queue + 1, sizeof(status), cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) {
+    set_cuda_error(cudaGetErrorString(e));
+    return DLS_ERR_CUDA;
+  }
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     set_cuda_error(cudaGetErrorString(e));
     return DLS_ERR_CUDA;
   }
+  // a stack overflow (the kernel dropped a stack entry rather than write past
+  // its stack) makes the counts untrustworthy, as dls_count_host reports it
+  rc = status_code((unsigned)status);
+  if (rc) return rc;
   if (total_out) {
     dls_u128 t = {0, 0};
     for (int64_t k = 0; k < n_prefixes; ++k) t = dls_add_u128(t, dls_u128{host_counts[k], 0});

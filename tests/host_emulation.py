@@ -55,6 +55,14 @@ def host_source(text, name):
                         + lines[k][m.end():])
     text = "\n".join(lines)
     if name == "dls_kernels.cu":
+        # test hook of this build only: DLS_STANDIN_SNAP_CAP, when set, replaces
+        # the snapshot stack's entry bound, so that a test can make the stack
+        # overflow and see the entry points report it
+        cap = "kp.snap_cap = snap ? std::max(1, snapshot_entries(info, n, flags, depth)) : 0;"
+        assert cap in text
+        text = text.replace(cap, cap + ' if (snap && std::getenv("DLS_STANDIN_SNAP_CAP")) '
+                            'kp.snap_cap = std::atoi(std::getenv("DLS_STANDIN_SNAP_CAP"));')
+        text = "#include <cstdlib>\n" + text
         text += '\n#include "launch_kparams.inc"\n'
     assert "__shared__" not in text and "<<<" not in text, name
     return text
@@ -92,9 +100,13 @@ class Emulated:
     def __init__(self, exe, workdir):
         self.exe, self.d = exe, workdir
 
-    def _run(self, args, timeout=600):
+    def _run(self, args, timeout=600, env=None):
+        full_env = None
+        if env:
+            full_env = dict(os.environ)
+            full_env.update({k: str(v) for k, v in env.items()})
         r = subprocess.run([self.exe] + [str(a) for a in args], capture_output=True, text=True,
-                           timeout=timeout)
+                           timeout=timeout, env=full_env)
         assert r.returncode == 0, (r.returncode, r.stderr[-2000:])
         return r.stdout.split("\n")
 
@@ -105,15 +117,19 @@ class Emulated:
         np.ascontiguousarray(records, dtype=np.uint8).tofile(p)
         return o, p
 
-    def count(self, entry, n, flags, order, prefixes, **launch):
+    def count(self, entry, n, flags, order, prefixes, env=None, **launch):
         """entry: count, host, noalloc, plan or describe.  Returns (rc,
         result): (counts, total, nodes) for the counting entries, a dict for
-        describe, None when rc != 0."""
+        describe, None when rc != 0.  After count and plan, self.last_status
+        holds (status, prefixes started) of dls_stream_status /
+        dls_plan_status.  env: extra environment of the driver process."""
         prefixes = np.ascontiguousarray(prefixes, dtype=np.uint8)
         depth = prefixes.shape[1] if prefixes.ndim == 2 else 0
         o, p = self._files(order, prefixes)
-        lines = self._run([entry, n, flags, o, p, depth] + [launch.get(k, 0) for k in FIELDS])
+        lines = self._run([entry, n, flags, o, p, depth] + [launch.get(k, 0) for k in FIELDS],
+                          env=env)
         rc = int(lines[0].split()[1])
+        self.last_status = None
         if rc != 0:
             return rc, None
         if entry == "describe":
@@ -121,6 +137,9 @@ class Emulated:
                     "stack_entries", "fused"]
             return 0, dict(zip(keys, map(int, lines[1].split())))
         head = lines[1].split()
+        if "status" in head:
+            k = head.index("status")
+            self.last_status = (int(head[k + 1]), int(head[k + 3]))
         counts = np.array([int(x) for x in lines[2:] if x.strip()], dtype=np.uint64)
         return 0, (counts, int(head[1]), int(head[3]))
 

@@ -55,6 +55,11 @@ inline unsigned atomicSub(unsigned *a, unsigned v) {
   *a = old - v;
   return old;
 }
+inline unsigned atomicOr(unsigned *a, unsigned v) {
+  const unsigned old = *a;
+  *a = old | v;
+  return old;
+}
 
 namespace shim {
 // warp operations: the calling lane waits until all lanes of its warp call

@@ -9,12 +9,13 @@
 //   kernel_check serve jobs.txt mode max_jobs arena_bytes chunk_bytes budget
 //                block_threads items_per_job max_order
 //
-// ENTRY: count (dls_count_ex with node counting), host (dls_count_host),
-// noalloc (dls_count_host_noalloc), plan (dls_plan_create, then two
-// dls_plan_launch), describe (dls_describe_launch).  "Device" buffers are
-// host memory here.  Output: "rc R" and, when R = 0, "total T nodes N"
-// (nodes 0 where the entry does not count them) and one count per prefix;
-// describe prints "run W block grid smem entries fused" instead.
+// ENTRY: count (dls_count_ex with node counting, then dls_stream_status),
+// host (dls_count_host), noalloc (dls_count_host_noalloc), plan
+// (dls_plan_create, then two dls_plan_launch and dls_plan_status), describe
+// (dls_describe_launch).  "Device" buffers are host memory here.  Output:
+// "rc R" and, when R = 0, "total T nodes N" (nodes 0 where the entry does
+// not count them; count and plan add "status S started K") and one count per
+// prefix; describe prints "run W block grid smem entries fused" instead.
 //
 // classes: dls_hourglass_classes over `len`-byte hourglass records; prints
 // "rc R" and one class size per record.
@@ -54,10 +55,14 @@ std::vector<uint8_t> read_file(const char *path) {
 }
 
 void print_counts(int rc, unsigned long long total, unsigned long long nodes,
-                  const std::vector<uint64_t> &counts) {
+                  const std::vector<uint64_t> &counts, const dls_count_status *st = nullptr) {
   std::printf("rc %d\n", rc);
   if (rc != 0) return;
-  std::printf("total %llu nodes %llu\n", total, nodes);
+  if (st)
+    std::printf("total %llu nodes %llu status %d started %lld\n", total, nodes, st->status,
+                (long long)st->prefixes_started);
+  else
+    std::printf("total %llu nodes %llu\n", total, nodes);
   for (uint64_t c : counts) std::printf("%llu\n", (unsigned long long)c);
 }
 
@@ -229,9 +234,11 @@ int main(int argc, char **argv) {
   std::vector<uint64_t> counts((size_t)P, 0xdeadbeefull);
   uint64_t total = 0xdeadbeefull, nodes = 0;
   if (entry == "count") {
-    const int rc = dls_count_ex(n, flags, order.data(), len, pre.data(), depth, P,
-                                counts.data(), &total, &nodes, &cfg, nullptr);
-    print_counts(rc, total, nodes, counts);
+    int rc = dls_count_ex(n, flags, order.data(), len, pre.data(), depth, P,
+                          counts.data(), &total, &nodes, &cfg, nullptr);
+    dls_count_status st{-1, -1};
+    if (rc == 0) rc = dls_stream_status(nullptr, &st);
+    print_counts(rc, total, nodes, counts, &st);
   } else if (entry == "host" || entry == "noalloc") {
     dls_u128 t{0, 0};
     const int rc = entry == "host"
@@ -258,9 +265,11 @@ int main(int argc, char **argv) {
       total = 0xdeadbeefull;
       rc = dls_plan_launch(plan, nullptr);
     }
+    dls_count_status st{-1, -1};
+    if (rc == 0) rc = dls_plan_status(plan, nullptr, &st);
     if (plan) dls_plan_destroy(plan);
     if (rc == 0 && (first != counts || first_total != total)) rc = 99;  // replays differ
-    print_counts(rc, total, 0, counts);
+    print_counts(rc, total, 0, counts, &st);
   } else {
     std::fprintf(stderr, "unknown entry %s\n", entry.c_str());
     return 1;

@@ -44,15 +44,45 @@ def test_oracle_sample_is_the_gpu_workload(dls):
     spec = bench.SPECS["dls8_diag64"]
     order0, base = spec.product_base(dls, 0, spec.units)
     for depth, suffix in ((25, "heuristic_sq"), (28, "heuristic")):
-        o_order, o_pre = spec.oracle_sample(0, 2, depth, suffix)
         sub = dls_inputs.choose(spec.units, 2, 1000)
-        order, pre, _ = autotune.build_problem(spec.n, spec.flags, order0, base[sub], depth,
-                                               suffix)
+        o_order, o_pre, o_par = spec.oracle_sample(0, spec.units, sub, depth, suffix)
+        order, pre, par = autotune.build_problem(spec.n, spec.flags, order0, base[sub], depth,
+                                                 suffix)
         assert [tuple(map(int, c)) for c in order] == list(o_order)
-        assert pre.shape == o_pre.shape and (pre == o_pre).all()
+        assert pre.shape == o_pre.shape and (pre == o_pre).all() and (par == o_par).all()
     # and the oracle counts them: a few prefixes, against their own split
     c, _ = oracle.count_many(spec.n, spec.flags, o_order, o_pre[:50], threads=4)
     assert c.dtype == np.uint64 and len(c) == 50
+
+
+def test_oracle_check_agrees_and_catches_a_wrong_count(dls):
+    """bench.oracle_check on an 8-diagonal profiling case: counts the oracle
+    itself produced for the checked diagonals pass; one count off by one, a
+    missing prefix's count, or a prefix of another base, raise."""
+    from paper_1709_02599_gb300 import autotune
+    spec = bench.SPECS["dls8_diag64"]
+    units, depth, suffix = 8, 28, "heuristic_sq"
+    order0, base = spec.product_base(dls, 0, units)
+    order, pre, par = autotune.build_problem(spec.n, spec.flags, order0, base, depth, suffix)
+    idx = spec.check_bases(0, np.zeros(units, np.uint64))
+    o_order, o_pre, o_par = spec.oracle_sample(0, units, idx, depth, suffix)
+    ref, _ = oracle.count_many(spec.n, spec.flags, o_order, o_pre, threads=os.cpu_count())
+    counts = np.zeros(len(pre), np.uint64)
+    for k, b in enumerate(idx):
+        counts[par == b] = ref[o_par == k]
+    out, rate, n_pre = bench.oracle_check(spec, 0, units, depth, suffix, pre, par, counts,
+                                          os.cpu_count())
+    assert out["agree"] and out["bases"] == 4 and n_pre == len(o_pre) and rate > 0
+    assert out["squares"] == int(ref.sum())
+    bad = counts.copy()
+    k = int(np.nonzero(np.isin(par, idx) & (counts > 0))[0][0])
+    bad[k] += 1
+    try:
+        bench.oracle_check(spec, 0, units, depth, suffix, pre, par, bad, 2)
+    except RuntimeError as e:
+        assert "oracle check failed" in str(e)
+    else:
+        raise AssertionError("a wrong count passed the check")
 
 
 class _Done:

@@ -274,18 +274,19 @@ def test_config3_order8_diag64_sampled_against_oracle(dls):
     assert (c3 == c).all()
 
 
+@pytest.mark.parametrize("depth", [22, 25, 28, 31])
 @pytest.mark.parametrize("suffix", ["heuristic", "heuristic_sq"])
-def test_bench_configuration_against_oracle(dls, suffix):
-    """The order-8 workload exactly as the benchmark times it: split 28 cells
-    into the order (row 0, both diagonals, the rest of row 1), the Section
-    2.3 order (or its squared-count variant) after the split, counted
-    through a CUDA-graph plan with the
-    default launch and the 64-thread blocks the autotuner picks; the prefixes
-    of 4 seed-chosen diagonals of the 64 against the oracle (its own order
-    and prefixes)."""
+def test_bench_configuration_against_oracle(dls, suffix, depth):
+    """The order-8 workload exactly as the benchmark times it, at every split
+    depth its autotuner can pick (14, 17, 20 or 23 cells past row 0: both
+    diagonals and part of row 1 at 28), the Section 2.3 order (or its
+    squared-count variant) after the split, counted through a CUDA-graph plan
+    with the default launch and the 64-thread blocks the autotuner picks; the
+    prefixes of 4 seed-chosen diagonals of the 64 against the oracle (its own
+    order and prefixes)."""
     import dls_inputs
     from paper_1709_02599_gb300 import autotune
-    n, depth = 8, 28
+    n = 8
     order0 = dls.fill_order(n, D)
     ident = np.arange(n, dtype=np.uint8)[None]
     diags, _ = dls.extend_prefixes(n, D, order0, ident, n + (n - 1))
@@ -467,3 +468,26 @@ def test_host_buffers_and_plan_and_streams(dls):
     dls.count(7, D, wl.order, t, counts=c2, stream=s2, launch=dls.Launch(lanes_per_prefix=2))
     torch.cuda.synchronize()
     assert (c1.cpu().numpy() == ref).all() and (c2.cpu().numpy() == ref).all()
+
+
+def test_status_queries_after_counts_and_plans(dls):
+    """dls_stream_status after dls_count_ex and dls_plan_status after a plan
+    launch: a finished count reports DLS_OK and every prefix started, for
+    the batched and the plain kernels, on a stream of our own."""
+    wl = gpu_cases.split(dls, 7, D, 14)
+    ref, _ = oracle.count_many(7, D, wl.oracle_order, wl.oracle_prefixes, threads=THREADS)
+    P = len(wl.prefixes)
+    d_pre = torch.from_numpy(wl.prefixes).cuda()
+    st = torch.cuda.Stream()
+    for launch in (dls.Launch(), dls.Launch(kernel=dls.KERNEL_PLAIN),
+                   dls.Launch(stack=1), dls.Launch(lanes_per_prefix=4)):
+        with torch.cuda.stream(st):
+            c = dls.count(7, D, wl.order, d_pre, launch=launch, stream=st)
+        assert dls.stream_status(st) == (0, P), launch
+        assert (c.cpu().numpy() == ref).all()
+        counts = torch.empty(P, dtype=torch.uint64, device="cuda")
+        plan = dls.Plan(7, D, wl.order, d_pre, counts, None, launch)
+        plan.launch(st)
+        assert plan.status(st) == (0, P)
+        assert (counts.cpu().numpy() == ref).all()
+        plan.close()

@@ -29,6 +29,7 @@ import oracle
 
 D, V = 1, 2
 ERR_BAD_ARG = 3
+ERR_INTERNAL = 10
 
 
 # launch shapes: both kernel families, both stacks, both word placements,
@@ -137,6 +138,34 @@ def test_host_buffer_entry_and_plans(dls, emulated):
                 assert total == int(ref_c.sum()), (entry, sh)  # the plain 128-bit sum
             rc, (c, total, _) = emulated.count("plan", n, D, wl.order, wl.prefixes, **sh)
             assert rc == 0 and (c == ref_c).all() and total == int(ref_c.sum()), sh
+
+
+def test_status_after_every_entry(dls, emulated):
+    """A finished count reports DLS_OK and every prefix started, through
+    dls_stream_status after dls_count_ex and dls_plan_status after a plan,
+    for both kernel families.  With the snapshot stack bound forced below
+    what the search needs (a hook of this CPU build only), the kernel sets
+    its overflow flag and every entry reports DLS_ERR_INTERNAL: the status
+    queries, dls_count_host and dls_count_host_noalloc."""
+    wl = every(gpu_cases.split(dls, 7, D, 14), 100)
+    P = len(wl.prefixes)
+    for sh in (dict(), dict(kernel=1), dict(stack=1), dict(kernel=1, stack=1)):
+        for entry in ("count", "plan"):
+            rc, _ = emulated.count(entry, 7, D, wl.order, wl.prefixes, **sh)
+            assert rc == 0 and emulated.last_status == (0, P), (entry, sh)
+    for sh in (dict(), dict(kernel=1)):
+        info = emulated.count("describe", 7, D, wl.order, wl.prefixes, **sh)[1]
+        assert info["stack_entries"] > 1
+        low = {"DLS_STANDIN_SNAP_CAP": 1}
+        for entry in ("count", "plan"):
+            rc, _ = emulated.count(entry, 7, D, wl.order, wl.prefixes, env=low, **sh)
+            assert rc == 0 and emulated.last_status[0] == ERR_INTERNAL, (entry, sh)
+        for entry in ("host", "noalloc"):
+            rc, _ = emulated.count(entry, 7, D, wl.order, wl.prefixes, env=low, **sh)
+            assert rc == ERR_INTERNAL, (entry, sh)
+        # the per-position stack has no bound to exceed
+        rc, _ = emulated.count("host", 7, D, wl.order, wl.prefixes, env=low, stack=1, **sh)
+        assert rc == 0
 
 
 def test_describe_launch_and_argument_errors(dls, emulated):

@@ -5,15 +5,17 @@ own pool owns the device memory, or their path must not pay the implicit
 synchronisation of cudaMalloc/cudaFree).  Its device staging and queue head
 live in a fixed array inside the library, shared by every call.  This test
 calls it through the C ABI twice in a row, on different workloads, and checks
-each result against the regular host-buffer entry point dls_count_host --
-integer counts, so they must agree exactly -- and checks that an oversized
-call is refused.  It sits in its own file, collected last."""
+each result against the regular host-buffer entry point dls_count_host and
+against the oracle's counts of the same prefixes -- integer counts, so they
+must agree exactly -- and checks that an oversized call is refused.  It sits
+in its own file, collected last."""
 import ctypes
 
 import numpy as np
 import pytest
 
 import gpu_cases
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -48,6 +50,9 @@ def test_noalloc_matches_host_entry_on_two_calls(dls):
         ref, ref_total = dls.count_host(wl.n, wl.flags, wl.order, wl.prefixes)
         assert (got == ref).all()
         assert got_total == ref_total == int(ref.sum())
+        exact, _ = oracle.count_many(wl.n, wl.flags, wl.oracle_order, wl.oracle_prefixes,
+                                     threads=4)
+        assert (got == exact).all()
     # the plain kernel through the same entry point (no queue head needed)
     from paper_1709_02599_gb300 import _lib
     o = np.ascontiguousarray(first.order)
