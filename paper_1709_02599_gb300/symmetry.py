@@ -99,14 +99,18 @@ def hourglass_order(n, flags):
     return order_complete(n, flags, order, k, ORDER_HEURISTIC), k
 
 
-def weighted_counter(n, flags, order, k, classes_fn=None, count_fn=None, min_items=1 << 20):
+def weighted_counter(n, flags, order, k, classes_fn=None, count_fn=None, min_items=1 << 20,
+                     tally=None):
     """counter(bases, launch) for workunits.run_workunits.  bases are prefixes
     of the first cells of `order` (k hourglass cells first).  For each base
     it returns the sum, over the canonical hourglasses that extend it, of
     class size x completions (Corollary 1).
 
     classes_fn(hourglasses) -> class sizes, and count_fn(prefixes, launch) ->
-    completion counts; both default to the library on the GPU."""
+    completion counts; both default to the library on the GPU.  tally (a
+    dict, optional) receives, per batch of bases (keyed by their bytes), the
+    number of hourglasses extending them and the sum of the class sizes of
+    the canonical ones among them."""
     order = np.ascontiguousarray(order, dtype=np.uint8).reshape(-1, 2)
     if classes_fn is None:
         def classes_fn(hg):
@@ -125,8 +129,12 @@ def weighted_counter(n, flags, order, k, classes_fn=None, count_fn=None, min_ite
         out = np.zeros(len(bases), np.uint64)
         hg, hpar = extend_prefixes(n, flags, order, bases, k)
         if len(hg) == 0:
+            if tally is not None:
+                tally[bases.tobytes()] = (0, 0)
             return out
         sizes = np.asarray(classes_fn(hg)).astype(np.int64)
+        if tally is not None:
+            tally[bases.tobytes()] = (int(len(hg)), int(sizes.sum()))
         canon = np.nonzero(sizes > 0)[0]
         if len(canon) == 0:
             return out
@@ -153,7 +161,16 @@ def count_symmetry_broken_resumable(n, flags, path, batch=64, quorum=1, base_dep
     """count_symmetry_broken in workunits of `batch` base prefixes (row 0
     and the main diagonal by default), checkpointed at `path`.  Returns
     workunits.run_workunits' dict with 'total' = squares with row 0 fixed,
-    plus 'bases' and 'base_depth'."""
+    plus 'bases' and 'base_depth'.
+
+    A quorum (2: the batched and the plain kernel) covers the completion
+    counts only: the class sizes come from the one canonisation kernel.
+    They are checked instead by an invariant of the whole run -- every
+    hourglass lies in exactly one class, so the class sizes of the canonical
+    hourglasses add up to the number of hourglasses.  That needs every
+    workunit, so it is checked when this call counted all of them
+    ('class_check' True; None when some were resumed from the checkpoint)
+    and a failure raises RuntimeError."""
     from . import KERNEL_PLAIN
     from .workunits import run_workunits
     order, k = hourglass_order(n, flags)
@@ -167,11 +184,21 @@ def count_symmetry_broken_resumable(n, flags, path, batch=64, quorum=1, base_dep
     ident = np.arange(w, dtype=np.uint8)[None]
     bases, _ = extend_prefixes(n, flags, order, ident, base_depth)
     launches = (Launch(), Launch(kernel=KERNEL_PLAIN, stack=1))[:max(1, quorum)]
+    tally = {}
     res = run_workunits(n, flags, order, bases, path, batch=batch, quorum=launches,
                         counter=weighted_counter(n, flags, order, k, classes_fn, count_fn,
-                                                 min_items))
+                                                 min_items, tally=tally))
     res["bases"] = int(len(bases))
     res["base_depth"] = int(base_depth)
+    res["class_check"] = None
+    if res["units_resumed"] == 0 and len(bases):
+        hourglasses = sum(h for h, _ in tally.values())
+        size_sum = sum(c for _, c in tally.values())
+        if hourglasses != size_sum:
+            raise RuntimeError("class sizes add up to %d, not to the %d hourglasses"
+                               % (size_sum, hourglasses))
+        res["class_check"] = True
+        res["hourglasses"] = hourglasses
     return res
 
 

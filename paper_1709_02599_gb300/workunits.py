@@ -27,7 +27,8 @@ The checkpoint is a JSON-lines file plus a sidecar file of counts
   the sidecar file.
 - A restarted run skips the workunits whose lines and counts agree, and
   counts again any other one.  That covers a run killed at any point, a line
-  cut short, and counts that do not match their line.
+  cut short, and counts that do not match their line.  A line cut short at
+  the end of the file is removed before new lines are appended.
 
 Counting goes through `counter(prefixes, launch)`, which returns uint64
 counts.  The default counts on the GPU through the library (dls_count_ex);
@@ -89,6 +90,16 @@ def _read_checkpoint(path, config):
     return done
 
 
+def _drop_torn_tail(path):
+    """Cuts a line that an interrupted run left unfinished (no final newline)
+    off the end of the checkpoint, so that the next record starts on a line
+    of its own instead of being joined to the fragment and lost."""
+    with open(path, "rb+") as f:
+        data = f.read()
+        if data and not data.endswith(b"\n"):
+            f.truncate(data.rfind(b"\n") + 1)
+
+
 def run_workunits(n, flags, order, prefixes, path, batch=1 << 20, quorum=None, counter=None,
                   max_rounds=3):
     """Counts every prefix (uint8 [P, depth]) through workunits of `batch`
@@ -114,6 +125,8 @@ def run_workunits(n, flags, order, prefixes, path, batch=1 << 20, quorum=None, c
         with open(path, "w") as f:
             f.write(json.dumps({"kind": "dls-workunits", "version": VERSION, "config": config,
                                 "n_prefixes": P, "batch": int(batch)}) + "\n")
+    else:
+        _drop_torn_tail(path)
     side = path + ".counts"
     if not os.path.exists(side) or os.path.getsize(side) != 8 * P:
         np.zeros(P, np.uint64).tofile(side)

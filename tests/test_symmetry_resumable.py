@@ -44,6 +44,27 @@ def test_totals_equal_the_oracle(dls, emulated, tmp_path, n, flags):
                                                    classes_fn=cf, count_fn=nf, min_items=1)
     assert res["total"] == direct
     assert res["units"] == (res["bases"] + 7) // 8 and res["units_counted"] == res["units"]
+    assert res["class_check"] is True
+
+
+def test_a_wrong_class_size_is_caught(dls, emulated, tmp_path):
+    # the quorum covers the completion counts; a wrong class size from the
+    # canonisation (one size one too large, from a fake of the call) breaks
+    # the whole-run invariant and the run raises
+    from paper_1709_02599_gb300 import symmetry
+    cf, nf = primitives(emulated, 6, D)
+
+    def off_by_one(hg):
+        sizes = np.array(cf(hg), copy=True)
+        nz = np.nonzero(sizes)[0]
+        if len(nz):
+            sizes[nz[0]] += 1
+        return sizes
+
+    with pytest.raises(RuntimeError, match="class sizes"):
+        symmetry.count_symmetry_broken_resumable(6, D, str(tmp_path / "w.jsonl"), batch=8,
+                                                 quorum=2, classes_fn=off_by_one, count_fn=nf,
+                                                 min_items=1)
 
 
 def test_interrupted_run_resumes_and_quorum_agrees(dls, emulated, tmp_path):
@@ -58,6 +79,7 @@ def test_interrupted_run_resumes_and_quorum_agrees(dls, emulated, tmp_path):
     res = symmetry.count_symmetry_broken_resumable(7, D, path, batch=16, classes_fn=cf,
                                                    count_fn=nf, min_items=1)
     assert res["units_resumed"] == 2 and res["total"] == 171200
+    assert res["class_check"] is None  # some units came from the checkpoint
     res = symmetry.count_symmetry_broken_resumable(7, D, str(tmp_path / "q.jsonl"), batch=64,
                                                    quorum=2, classes_fn=cf, count_fn=nf,
                                                    min_items=256)

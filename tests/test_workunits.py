@@ -68,6 +68,26 @@ def test_an_interrupted_run_resumes(dls, problem, tmp_path):
     assert (res["counts"] == ref).all() and res["total"] == 128
 
 
+def test_a_torn_last_line_costs_one_unit_once(dls, problem, tmp_path):
+    # a run killed while writing a record leaves half a line; the next run
+    # counts that unit again, and the run after it resumes every unit (the
+    # new record was not glued to the fragment)
+    from paper_1709_02599_gb300 import workunits
+    wl, ref = problem
+    path = str(tmp_path / "t.jsonl")
+    good = oracle_counter(wl)
+    res = workunits.run_workunits(6, D, wl.order, wl.prefixes, path, batch=5, counter=good)
+    units = res["units"]
+    text = open(path).read()
+    cut = text.rstrip("\n").rfind("\n") + 1
+    open(path, "w").write(text[:cut] + text[cut:cut + 20])  # last record torn
+    res = workunits.run_workunits(6, D, wl.order, wl.prefixes, path, batch=5, counter=good)
+    assert res["units_counted"] == 1 and res["units_resumed"] == units - 1
+    res = workunits.run_workunits(6, D, wl.order, wl.prefixes, path, batch=5, counter=good)
+    assert res["units_counted"] == 0 and res["units_resumed"] == units
+    assert (res["counts"] == ref).all() and res["total"] == 128
+
+
 def test_quorum_recounts_a_disagreement_and_refuses_a_persistent_one(dls, problem, tmp_path):
     from paper_1709_02599_gb300 import Launch, KERNEL_PLAIN, workunits
     wl, ref = problem
