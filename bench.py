@@ -126,7 +126,9 @@ class Dls8Diag64:
 
     def product_base(self, dls, seed, k):
         order = dls.fill_order(self.n, self.flags, first_rows=self.first_rows)
-        ident = np.arange(self.n, dtype=np.uint8)[None]
+        # row 0 = 0..n-1; with vertical symmetry the order lists its left half
+        w = self.n // 2 if self.flags & 2 else self.n
+        ident = np.arange(w, dtype=np.uint8)[None]
         allb, _ = dls.extend_prefixes(self.n, self.flags, order, ident, self.base_depth())
         picks = dls_inputs.choose(len(allb), k, seed)
         return order, allb[picks]

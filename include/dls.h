@@ -65,8 +65,9 @@ typedef enum {
     DLS_ERR_BAD_ARG = 3,      /* NULL pointer, negative size, bad depth ...  */
     DLS_ERR_CAPACITY = 4,     /* output buffer too small; *n_out = needed    */
     DLS_ERR_CUDA = 5,         /* a CUDA call failed (dls_last_cuda_error())  */
-    DLS_ERR_TIMEOUT = 6,      /* reserved: no entry point returns it         */
-    DLS_ERR_ABORTED = 7,      /* stopped through dls_server_abort()          */
+    DLS_ERR_TIMEOUT = 6,      /* a count ran out of its iteration budget     */
+    DLS_ERR_ABORTED = 7,      /* stopped through dls_server_abort() or a
+                                 count's abort flag                         */
     DLS_ERR_NO_MEMORY = 8,    /* host or device allocation failed            */
     DLS_ERR_BAD_STATE = 9,    /* object used after release / wrong sequence  */
     DLS_ERR_INTERNAL = 10     /* a kernel met a state its bounds exclude
@@ -214,8 +215,9 @@ typedef struct {
     int donate;           /* persistent only: 1 = idle lanes take work from
                              busy lanes of their warp once the queue is empty
                              (default), -1 = off                            */
-    int check_every;      /* persistent only: iterations between donation
-                             checks (power of two, default 64)               */
+    int check_every;      /* iterations between donation checks (persistent
+                             kernels) and between checks of the budget and
+                             abort flag (power of two, default 64)           */
     int words;            /* where a lane keeps its row and column words:
                              0 = registers when they fit (n <= 8, or even
                              n <= 10 with DLS_VSYM), else shared memory;
@@ -252,7 +254,30 @@ typedef struct {
                              without the lookahead.  1 = on (BAD_ARG where it
                              does not apply), -1 = off, 0 = on where it
                              applies (default)                              */
+    int64_t budget;       /* stop early after this many search iterations per
+                             lane (the lanes of a warp step together; 0 = no
+                             limit) -- see "Stopping early" below          */
+    const volatile int *abort_flag; /* NULL, or a word the kernel polls (device
+                             memory, or host memory the GPU can read, e.g.
+                             pinned and mapped): once it reads nonzero, the
+                             kernel stops early                             */
 } dls_launch_t;
+
+/* Stopping early (Section 5.2's workunits are restartable; this makes a long
+ * launch restartable too).  With a budget or an abort flag, each warp checks
+ * every check_every iterations (and whenever a lane finishes its prefix):
+ * once its iterations reach the budget, or the flag reads nonzero, it stops.
+ * A lane still searching gives up its prefix: bit 63 (DLS_UNFINISHED) of the
+ * prefix's count is set (counts are below 2^63 for every order the library
+ * takes), and the warp takes no further prefix.  The count's status (the
+ * host-buffer entries' return value, or dls_stream_status /
+ * dls_plan_status) becomes DLS_ERR_TIMEOUT or DLS_ERR_ABORTED when work was
+ * left, and prefixes_started says how many leading prefixes were handed to
+ * lanes.  To finish the job, count again the prefixes whose count has bit 63
+ * set and those from prefixes_started on; every other count is exact.  The
+ * total (d_total) is then partial.  No wait in the kernel depends on the
+ * flag: a warp only reads it. */
+#define DLS_UNFINISHED (1ull << 63)
 
 /* What a dls_count_ex call with this shape runs. */
 typedef enum {
@@ -320,7 +345,10 @@ int dls_count_ex(int n, uint32_t flags, const uint8_t *order, int order_len,
  * page-locked memory makes the copy asynchronous) to the device, counts, and
  * copies the counts back to h_counts (HOST, n_prefixes uint64, may be NULL)
  * and the sum to *total_out (may be NULL; the plain 128-bit sum of the
- * counts -- multiply by dls_multiplier() for whole-square totals).
+ * counts -- multiply by dls_multiplier() for whole-square totals).  A count
+ * that stops early returns DLS_ERR_TIMEOUT or DLS_ERR_ABORTED with its
+ * counts copied back (unfinished ones marked DLS_UNFINISHED, those never
+ * started 0) and *total_out not written.
  * Synchronous: returns after the copies back have landed.  The device
  * buffers come from a per-(device, stream) area that grows on demand and
  * lives until dls_release().  Calls on the same stream from several host
@@ -335,12 +363,13 @@ int dls_count_host(int n, uint32_t flags, const uint8_t *order,
                    dls_u128 *total_out, const dls_launch_t *cfg,
                    void *stream);
 
-/* What the last count on a work area reported.  status: DLS_OK, or
+/* What the last count on a work area reported.  status: DLS_OK;
  * DLS_ERR_INTERNAL when the snapshot search reported a stack overflow
  * (excluded by its entry bound; the kernel drops the entry rather than write
- * past its stack, so the counts are not to be trusted).  prefixes_started:
- * the prefixes of which at least one work item was handed to a lane (all of
- * them once a count has run to its end). */
+ * past its stack, so the counts are not to be trusted); DLS_ERR_TIMEOUT or
+ * DLS_ERR_ABORTED when it stopped early with work left (see "Stopping
+ * early").  prefixes_started: the prefixes of which at least one work item
+ * was handed to a lane (all of them once a count has run to its end). */
 typedef struct {
     int status;
     int64_t prefixes_started;

@@ -19,7 +19,7 @@ import numpy as np
 from . import _lib
 from ._lib import (DIAGONAL, VSYM, DLS_MAX_N, ORDER_MD_AD_ROWS, ORDER_ROW_MAJOR,  # noqa: F401
                    ORDER_HOURGLASS, ORDER_HEURISTIC, ORDER_HEURISTIC_SQ, KERNEL_PERSISTENT,
-                   KERNEL_PLAIN,
+                   KERNEL_PLAIN, ERR_TIMEOUT, ERR_ABORTED, UNFINISHED,
                    DlsError)
 
 
@@ -37,12 +37,14 @@ class Launch:
     stack: int = 0
     lookahead: int = 0
     fuse: int = 0
+    budget: int = 0        # search iterations per lane before stopping (0 = none)
+    abort_flag: int = 0    # address of an int the kernel polls (0 = none)
 
     def c(self):
         return _lib.LaunchT(self.kernel, self.block_threads, self.blocks_per_sm,
                             self.lanes_per_prefix, self.split_pos, self.donate,
                             self.check_every, self.words, self.stack, self.lookahead,
-                            self.fuse)
+                            self.fuse, self.budget, self.abort_flag or None)
 
 
 def lib():

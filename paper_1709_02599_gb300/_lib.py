@@ -28,6 +28,9 @@ RUN_NAMES = {RUN_PERSISTENT: "k_persistent", RUN_PLAIN: "k_plain", RUN_SNAPSHOT:
 
 OK = 0
 ERR_CAPACITY = 4
+ERR_TIMEOUT = 6
+ERR_ABORTED = 7
+UNFINISHED = 1 << 63
 
 u8p = ctypes.POINTER(ctypes.c_uint8)
 u32p = ctypes.POINTER(ctypes.c_uint32)
@@ -54,7 +57,9 @@ class LaunchT(ctypes.Structure):
                 ("words", ctypes.c_int),
                 ("stack", ctypes.c_int),
                 ("lookahead", ctypes.c_int),
-                ("fuse", ctypes.c_int)]
+                ("fuse", ctypes.c_int),
+                ("budget", ctypes.c_int64),
+                ("abort_flag", ctypes.c_void_p)]
 
 
 class LaunchInfo(ctypes.Structure):

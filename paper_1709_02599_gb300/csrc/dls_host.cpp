@@ -239,7 +239,7 @@ const char *dls_strerror(int code) {
     case DLS_ERR_BAD_ARG: return "bad argument";
     case DLS_ERR_CAPACITY: return "output buffer too small";
     case DLS_ERR_CUDA: return "CUDA error";
-    case DLS_ERR_TIMEOUT: return "timeout (reserved)";
+    case DLS_ERR_TIMEOUT: return "stopped: iteration budget spent";
     case DLS_ERR_ABORTED: return "aborted";
     case DLS_ERR_NO_MEMORY: return "out of memory";
     case DLS_ERR_BAD_STATE: return "object in the wrong state";

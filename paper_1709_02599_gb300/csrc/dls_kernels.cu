@@ -52,6 +52,11 @@ namespace dls {
 // bits the kernels set, read back by the host entry points and by
 // dls_stream_status / dls_plan_status.
 constexpr unsigned ST_OVERFLOW = 1u;  // a snapshot stack would have overflowed
+constexpr unsigned ST_TIMEOUT = 2u;   // stopped early: iteration budget spent
+constexpr unsigned ST_ABORTED = 4u;   // stopped early: abort flag seen
+// iterations between two reads of a count's abort flag (a read of mapped
+// host memory takes microseconds)
+constexpr long long POLL_EVERY = 4096;
 
 __device__ __forceinline__ void raise_status(const unsigned long long *queue, unsigned bit) {
   atomicOr(reinterpret_cast<unsigned *>(const_cast<unsigned long long *>(queue + 1)), bit);
@@ -71,8 +76,10 @@ struct KParams {
   unsigned long long *counts;
   unsigned long long *total;
   unsigned long long *nodes;
-  unsigned long long *queue;  // [0] queue head, [1] stack overflow flag
+  unsigned long long *queue;  // [0] queue head, [1] status word
   int snap_cap;               // snapshot stack entries per lane
+  long long budget;           // search iterations per lane before stopping (0: none)
+  const volatile int *abort_flag;  // polled; nonzero stops the count (NULL: none)
   uint8_t ci[DLS_MAX_CELLS];
   uint8_t cj[DLS_MAX_CELLS];
 };
@@ -120,6 +127,41 @@ __device__ __forceinline__ void flush_count(long long prefix, unsigned long long
     else if (cnt)
       atomicAdd(p.counts + prefix, cnt);
   }
+}
+
+// Stopping early.  `spent` = search iterations the warp has made (the same
+// in every lane); returns the status bit to stop with, or 0.  Lane 0 reads
+// the abort flag every POLL_EVERY iterations and shares what it read.
+__device__ __forceinline__ unsigned stop_due(const KParams &p, long long spent,
+                                             long long &next_poll, int lane) {
+  if (p.budget > 0 && spent >= p.budget) return ST_TIMEOUT;
+  if (p.abort_flag != nullptr && spent >= next_poll) {
+    next_poll = spent + POLL_EVERY;
+    int f = 0;
+    if (lane == 0) f = *p.abort_flag;
+    if (__shfl_sync(FULL, f, 0) != 0) return ST_ABORTED;
+  }
+  return 0u;
+}
+
+// A warp that stops: a lane still searching marks its prefix unfinished
+// (with a stored count, the partial count goes with the mark), and the
+// count's status records why, if work was left (a lane was searching, or
+// the queue still held items the warp would have taken).
+__device__ __forceinline__ void stop_warp(const KParams &p, unsigned why, bool busy,
+                                          long long prefix, unsigned long long cnt, bool queued,
+                                          int lane) {
+  if (busy && p.counts != nullptr) {
+    if (p.count_store)
+      p.counts[prefix] = cnt | DLS_UNFINISHED;
+    else
+      atomicOr(p.counts + prefix, DLS_UNFINISHED);
+  }
+  unsigned long long head = 0ull;
+  if (queued && lane == 0) head = *reinterpret_cast<volatile unsigned long long *>(p.queue);
+  head = __shfl_sync(FULL, head, 0);
+  const bool left = __any_sync(FULL, busy) || (queued && (long long)head < p.n_items);
+  if (left && lane == 0) raise_status(p.queue, why);
 }
 
 // Per-block reduction of the lane totals, one global atomic per block.
@@ -183,12 +225,23 @@ __global__ void __launch_bounds__(512) k_plain(const __grid_constant__ KParams p
     busy = !load_item<REG, VSYM, NODES>(s, p, item, tbl, B);
     if (!busy) flush_count(s.prefix, s.cnt, p, lane_total);
   }
+  const bool stoppable = p.budget > 0 || p.abort_flag != nullptr;
+  long long spent = 0, next_poll = 0;
+  unsigned stopped = 0u;
+  int k = 0;
   while (__any_sync(FULL, busy)) {
     if (busy && dfs_step<REG, VSYM, NODES, SPLIT>(s, p.g, p.sp, sbase, tbl, B)) {
       busy = false;
       flush_count(s.prefix, s.cnt, p, lane_total);
     }
+    if (stoppable && ++k > p.check_mask) {
+      spent += k;
+      k = 0;
+      stopped = stop_due(p, spent, next_poll, threadIdx.x & 31);
+      if (stopped) break;
+    }
   }
+  if (stopped) stop_warp(p, stopped, busy, s.prefix, s.cnt, false, threadIdx.x & 31);
   block_reduce_add(lane_total, p.total, red);
   if (NODES) block_reduce_add(s.nodes, p.nodes, red);
 }
@@ -309,8 +362,12 @@ __global__ void __launch_bounds__(512)
   unsigned long long lane_total = 0ull;
   bool busy = false;
   bool qdone = false;
+  const bool stoppable = p.budget > 0 || p.abort_flag != nullptr;
+  long long spent = 0, next_poll = 0;
+  unsigned stopped = 0u;
 
   for (;;) {
+    if (stoppable && (stopped = stop_due(p, spent, next_poll, lane)) != 0u) break;
     // hand queue items to idle lanes, one atomic per warp
     unsigned idle = __ballot_sync(FULL, !busy);
     while (idle != 0u && !qdone) {
@@ -330,11 +387,20 @@ __global__ void __launch_bounds__(512)
     }
     if (idle == FULL) break;  // queue drained and every lane idle
     if (!qdone) {
-      // every lane is busy here: step until one finishes its item
+      // every lane is busy here: step until one finishes its item (or, when
+      // the count may stop early, at most check_every iterations)
       bool fin;
-      do {
-        fin = dfs_step<REG, VSYM, NODES, SPLIT>(s, p.g, p.sp, sbase, tbl, B);
-      } while (!__any_sync(FULL, fin));
+      if (!stoppable) {
+        do {
+          fin = dfs_step<REG, VSYM, NODES, SPLIT>(s, p.g, p.sp, sbase, tbl, B);
+        } while (!__any_sync(FULL, fin));
+      } else {
+        int k = 0;
+        do {
+          fin = dfs_step<REG, VSYM, NODES, SPLIT>(s, p.g, p.sp, sbase, tbl, B);
+        } while (!__any_sync(FULL, fin) && ++k <= p.check_mask);
+        spent += k + 1;
+      }
       if (fin) {
         busy = false;
         flush_count(s.prefix, s.cnt, p, lane_total);
@@ -346,9 +412,11 @@ __global__ void __launch_bounds__(512)
           flush_count(s.prefix, s.cnt, p, lane_total);
         }
       }
+      spent += p.check_mask + 1;
       if (p.donate) donate<REG, VSYM>(s, busy, p, stk, tbl, lane, B);
     }
   }
+  if (stopped) stop_warp(p, stopped, busy, s.prefix, s.cnt, true, lane);
   block_reduce_add(lane_total, p.total, red);
   if (NODES) block_reduce_add(s.nodes, p.nodes, red);
 }
@@ -496,12 +564,23 @@ __global__ void __launch_bounds__(512)
     busy = !snap_load<VSYM, NODES>(s, p, item, tbl, tb);
     if (!busy) flush_count(s.prefix, s.cnt, p, lane_total);
   }
+  const bool stoppable = p.budget > 0 || p.abort_flag != nullptr;
+  long long spent = 0, next_poll = 0;
+  unsigned stopped = 0u;
+  int k = 0;
   while (__any_sync(FULL, busy)) {
     if (busy && snap_step<VSYM, NODES, DG, false, FU>(s, p.g, st, tb, B, ovf)) {
       busy = false;
       flush_count(s.prefix, s.cnt, p, lane_total);
     }
+    if (stoppable && ++k > p.check_mask) {
+      spent += k;
+      k = 0;
+      stopped = stop_due(p, spent, next_poll, threadIdx.x & 31);
+      if (stopped) break;
+    }
   }
+  if (stopped) stop_warp(p, stopped, busy, s.prefix, s.cnt, false, threadIdx.x & 31);
   if (ovf) raise_status(p.queue, ST_OVERFLOW);
   block_reduce_add(lane_total, p.total, red);
   if (NODES) block_reduce_add(s.nodes, p.nodes, red);
@@ -524,7 +603,11 @@ __global__ void __launch_bounds__(512)
   unsigned long long lane_total = 0ull;
   bool busy = false;
   bool qdone = false;
+  const bool stoppable = p.budget > 0 || p.abort_flag != nullptr;
+  long long spent = 0, next_poll = 0;
+  unsigned stopped = 0u;
   for (;;) {
+    if (stoppable && (stopped = stop_due(p, spent, next_poll, lane)) != 0u) break;
     unsigned idle = __ballot_sync(FULL, !busy);
     while (idle != 0u && !qdone) {
       const int nidle = __popc(idle);
@@ -543,11 +626,20 @@ __global__ void __launch_bounds__(512)
     }
     if (idle == FULL) break;  // queue drained and every lane idle
     if (!qdone) {
-      // every lane is busy here: step until one finishes
+      // every lane is busy here: step until one finishes (or, when the
+      // count may stop early, at most check_every iterations)
       bool fin;
-      do {
-        fin = snap_step<VSYM, NODES, DG, LA, FU>(s, p.g, st, tb, B, ovf);
-      } while (!__any_sync(FULL, fin));
+      if (!stoppable) {
+        do {
+          fin = snap_step<VSYM, NODES, DG, LA, FU>(s, p.g, st, tb, B, ovf);
+        } while (!__any_sync(FULL, fin));
+      } else {
+        int k = 0;
+        do {
+          fin = snap_step<VSYM, NODES, DG, LA, FU>(s, p.g, st, tb, B, ovf);
+        } while (!__any_sync(FULL, fin) && ++k <= p.check_mask);
+        spent += k + 1;
+      }
       if (fin) {
         busy = false;
         flush_count(s.prefix, s.cnt, p, lane_total);
@@ -559,9 +651,11 @@ __global__ void __launch_bounds__(512)
           flush_count(s.prefix, s.cnt, p, lane_total);
         }
       }
+      spent += p.check_mask + 1;
       if (p.donate) snap_donate<VSYM, DG>(s, busy, p, st, tb, lane, B);
     }
   }
+  if (stopped) stop_warp(p, stopped, busy, s.prefix, s.cnt, true, lane);
   if (ovf) raise_status(p.queue, ST_OVERFLOW);
   block_reduce_add(lane_total, p.total, red);
   if (NODES) block_reduce_add(s.nodes, p.nodes, red);
@@ -657,6 +751,8 @@ struct Shape {
   int stack;  // 0 auto, 1 one entry per position, 2 snapshots
   int lookahead;
   int fuse;   // -1 off, 0 where it applies, 1 on
+  long long budget;
+  const volatile int *abort_flag;
 };
 
 static int resolve_shape(const dls_launch_t *cfg, int depth, int last,
@@ -695,6 +791,9 @@ static int resolve_shape(const dls_launch_t *cfg, int depth, int last,
   if (sh->lookahead < 0 || sh->lookahead > 1) return DLS_ERR_BAD_ARG;
   sh->fuse = c.fuse;
   if (sh->fuse < -1 || sh->fuse > 1) return DLS_ERR_BAD_ARG;
+  if (c.budget < 0) return DLS_ERR_BAD_ARG;
+  sh->budget = c.budget;
+  sh->abort_flag = c.abort_flag;
   return DLS_OK;
 }
 
@@ -861,6 +960,8 @@ static int prepare_launch(int n, uint32_t flags, const uint8_t *order, int order
   kp.sp.lanes_log2 = sh.lanes_log2;
   kp.sp.pos = sh.split_pos;
   kp.check_mask = sh.check_mask;
+  kp.budget = sh.budget;
+  kp.abort_flag = sh.abort_flag;
   kp.donate = sh.donate;
   kp.count_store = pr->store ? 1 : 0;
   kp.n_prefixes = n_prefixes;
@@ -1010,6 +1111,8 @@ static int enqueue_count(int n, uint32_t flags, const uint8_t *order,
 // its counts untrustworthy (DLS_ERR_INTERNAL).
 int status_code(unsigned word) {
   if (word & ST_OVERFLOW) return DLS_ERR_INTERNAL;
+  if (word & ST_ABORTED) return DLS_ERR_ABORTED;
+  if (word & ST_TIMEOUT) return DLS_ERR_TIMEOUT;
   return DLS_OK;
 }
 

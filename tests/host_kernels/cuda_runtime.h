@@ -60,6 +60,11 @@ inline unsigned atomicOr(unsigned *a, unsigned v) {
   *a = old | v;
   return old;
 }
+inline unsigned long long atomicOr(unsigned long long *a, unsigned long long v) {
+  const unsigned long long old = *a;
+  *a = old | v;
+  return old;
+}
 
 namespace shim {
 // warp operations: the calling lane waits until all lanes of its warp call

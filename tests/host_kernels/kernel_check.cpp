@@ -4,7 +4,7 @@
 //
 //   kernel_check ENTRY n flags order.bin prefixes.bin depth
 //                kernel block blocks_per_sm lanes split_pos donate check_every
-//                words stack lookahead fuse
+//                words stack lookahead fuse budget abort
 //   kernel_check classes n flags order.bin hourglasses.bin len
 //   kernel_check serve jobs.txt mode max_jobs arena_bytes chunk_bytes budget
 //                block_threads items_per_job max_order
@@ -194,10 +194,10 @@ int run_serve(int argc, char **argv) {
 int main(int argc, char **argv) {
   if (argc >= 2 && std::string(argv[1]) == "classes") return run_classes(argc, argv);
   if (argc >= 2 && std::string(argv[1]) == "serve") return run_serve(argc, argv);
-  if (argc != 18) {
+  if (argc != 20) {
     std::fprintf(stderr, "usage: kernel_check ENTRY n flags order.bin prefixes.bin depth "
                          "kernel block blocks_per_sm lanes split_pos donate check_every "
-                         "words stack lookahead fuse\n");
+                         "words stack lookahead fuse budget abort\n");
     return 1;
   }
   const std::string entry = argv[1];
@@ -218,6 +218,12 @@ int main(int argc, char **argv) {
   cfg.stack = std::atoi(argv[15]);
   cfg.lookahead = std::atoi(argv[16]);
   cfg.fuse = std::atoi(argv[17]);
+  cfg.budget = std::atoll(argv[18]);
+  // abort: 0 = no flag, 1 = a flag already set, 2 = a flag that stays clear
+  static int abort_word = 0;
+  const int abort_mode = std::atoi(argv[19]);
+  abort_word = abort_mode == 1 ? 1 : 0;
+  cfg.abort_flag = abort_mode ? &abort_word : nullptr;
   const int len = (int)order.size() / 2;
   const int64_t P = depth ? (int64_t)pre.size() / depth : 1;
   if (pre.empty()) pre.push_back(0);  // a valid pointer for depth 0

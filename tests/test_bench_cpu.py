@@ -53,6 +53,20 @@ def test_oracle_sample_is_the_gpu_workload(dls):
     # and the oracle counts them: a few prefixes, against their own split
     c, _ = oracle.count_many(spec.n, spec.flags, o_order, o_pre[:50], threads=4)
     assert c.dtype == np.uint64 and len(c) == 50
+    # the symmetric order-10 workload: 2000 of the 2 153 120 fillings of rows
+    # 1-2 below the (left-half) identity row, split at every depth the
+    # autotuner tries
+    spec = bench.SPECS["vsym10_rows2"]
+    order0, base = spec.product_base(dls, 0, spec.units)
+    assert base.shape == (2000, 15) and (base[:, :5] == np.arange(5)).all()
+    idx = np.arange(0, 2000, 250)
+    for depth in spec.depths:
+        for suffix in ("given", "heuristic_sq"):
+            order, pre, par = autotune.build_problem(spec.n, spec.flags, order0, base[idx],
+                                                     depth, suffix)
+            o_order, o_pre, o_par = spec.oracle_sample(0, spec.units, idx, depth, suffix)
+            assert [tuple(map(int, c)) for c in order] == list(o_order)
+            assert (pre == o_pre).all() and (par == o_par).all()
 
 
 def test_oracle_check_agrees_and_catches_a_wrong_count(dls):

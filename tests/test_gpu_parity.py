@@ -491,3 +491,42 @@ def test_status_queries_after_counts_and_plans(dls):
         assert plan.status(st) == (0, P)
         assert (counts.cpu().numpy() == ref).all()
         plan.close()
+
+
+def test_budget_and_abort_flag_on_the_gpu(dls):
+    """A small iteration budget stops the count (DLS_ERR_TIMEOUT): every count
+    not marked DLS_UNFINISHED below prefixes_started is exact, and counting the
+    rest again completes the job.  An abort flag in device memory that is set
+    stops it (DLS_ERR_ABORTED); one that stays clear changes nothing."""
+    wl = gpu_cases.split(dls, 7, D, 14)
+    ref, _ = oracle.count_many(7, D, wl.oracle_order, wl.oracle_prefixes, threads=THREADS)
+    P = len(wl.prefixes)
+    d_pre = torch.from_numpy(wl.prefixes).cuda()
+    st = torch.cuda.Stream()
+    for sh in (dict(), dict(kernel=dls.KERNEL_PLAIN), dict(stack=1), dict(lanes_per_prefix=4)):
+        launch = dls.Launch(budget=32, check_every=8, **sh)
+        with torch.cuda.stream(st):
+            c = dls.count(7, D, wl.order, d_pre, launch=launch, stream=st)
+        status, started = dls.stream_status(st)
+        assert status == dls.ERR_TIMEOUT and 0 < started <= P, sh
+        c = c.cpu().numpy()
+        unfinished = (c & np.uint64(dls.UNFINISHED)) != 0
+        assert unfinished.any()
+        done = ~unfinished & (np.arange(P) < started)
+        assert (c[done] == ref[done]).all(), sh
+        redo = np.nonzero(~done)[0]
+        with torch.cuda.stream(st):
+            c2 = dls.count(7, D, wl.order, d_pre[torch.from_numpy(redo).cuda()],
+                           launch=dls.Launch(**sh), stream=st)
+        assert dls.stream_status(st) == (0, len(redo))
+        c[redo] = c2.cpu().numpy()
+        assert (c == ref).all(), sh
+    for value, expect in ((1, dls.ERR_ABORTED), (0, 0)):
+        flag = torch.full((1,), value, dtype=torch.int32, device="cuda")
+        with torch.cuda.stream(st):
+            c = dls.count(7, D, wl.order, d_pre, launch=dls.Launch(abort_flag=flag.data_ptr()),
+                          stream=st)
+        status, started = dls.stream_status(st)
+        assert status == expect
+        if expect == 0:
+            assert started == P and (c.cpu().numpy() == ref).all()

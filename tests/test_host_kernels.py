@@ -29,7 +29,10 @@ import oracle
 
 D, V = 1, 2
 ERR_BAD_ARG = 3
+ERR_TIMEOUT = 6
+ERR_ABORTED = 7
 ERR_INTERNAL = 10
+UNFINISHED = np.uint64(1 << 63)
 
 
 # launch shapes: both kernel families, both stacks, both word placements,
@@ -166,6 +169,57 @@ def test_status_after_every_entry(dls, emulated):
         # the per-position stack has no bound to exceed
         rc, _ = emulated.count("host", 7, D, wl.order, wl.prefixes, env=low, stack=1, **sh)
         assert rc == 0
+
+
+@pytest.mark.parametrize("sh", [dict(), dict(kernel=1), dict(stack=1), dict(kernel=1, stack=1),
+                                dict(lanes_per_prefix=4), dict(kernel=1, lanes_per_prefix=4)])
+def test_budget_stops_and_the_rest_resumes(dls, emulated, sh):
+    """A tiny iteration budget stops the count: DLS_ERR_TIMEOUT, the prefixes a
+    lane was still searching marked DLS_UNFINISHED, those never handed out
+    beyond prefixes_started.  Every other count is already exact, and
+    counting the rest again without a budget completes the job."""
+    wl = every(gpu_cases.split(dls, 7, D, 14), 7)
+    ref, _ = oracle.count_many(7, D, wl.oracle_order, wl.oracle_prefixes)
+    P = len(wl.prefixes)
+    rc, res = emulated.count("count", 7, D, wl.order, wl.prefixes, budget=8, check_every=4,
+                             block_threads=64, **sh)
+    assert rc == 0
+    status, started = emulated.last_status
+    assert status == ERR_TIMEOUT and 0 < started <= P
+    counts = res[0]
+    unfinished = (counts & UNFINISHED) != 0
+    assert unfinished.any()
+    done = ~unfinished & (np.arange(P) < started)
+    assert (counts[done] == ref[done]).all()
+    redo = ~done
+    rc, res2 = emulated.count("count", 7, D, wl.order, wl.prefixes[redo], **sh)
+    assert rc == 0 and emulated.last_status == (0, int(redo.sum()))
+    merged = counts.copy()
+    merged[redo] = res2[0]
+    assert (merged == ref).all()
+    # the host-buffer entries return the status
+    for entry in ("host", "noalloc"):
+        rc, _ = emulated.count(entry, 7, D, wl.order, wl.prefixes, budget=8, check_every=4, **sh)
+        assert rc == ERR_TIMEOUT, entry
+
+
+def test_abort_flag(dls, emulated):
+    """A set abort flag stops the count before any prefix is finished
+    (DLS_ERR_ABORTED); a flag that stays clear changes nothing."""
+    wl = every(gpu_cases.split(dls, 7, D, 14), 7)
+    ref, _ = oracle.count_many(7, D, wl.oracle_order, wl.oracle_prefixes)
+    P = len(wl.prefixes)
+    for sh in (dict(), dict(kernel=1), dict(stack=1)):
+        rc, res = emulated.count("count", 7, D, wl.order, wl.prefixes, abort=1, **sh)
+        assert rc == 0 and emulated.last_status[0] == ERR_ABORTED, sh
+        c = res[0]
+        assert ((c == 0) | ((c & UNFINISHED) != 0)).all()
+        rc, res = emulated.count("count", 7, D, wl.order, wl.prefixes, abort=2, **sh)
+        assert rc == 0 and emulated.last_status == (0, P) and (res[0] == ref).all(), sh
+        rc, _ = emulated.count("plan", 7, D, wl.order, wl.prefixes, abort=1, **sh)
+        assert rc == 0 and emulated.last_status[0] == ERR_ABORTED
+        rc, _ = emulated.count("host", 7, D, wl.order, wl.prefixes, abort=1, **sh)
+        assert rc == ERR_ABORTED
 
 
 def test_describe_launch_and_argument_errors(dls, emulated):
