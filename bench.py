@@ -27,7 +27,9 @@ persistent kernel launched from a CUDA graph.  Reported:
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 With torchrun (N > 1) each rank counts its own 64 diagonals (seed = rank) and
-rank 0 prints the line (weak scaling, no collective on the data path).
+rank 0 prints the line (weak scaling, no collective on the data path); with
+--scaling strong the ranks split one 64-diagonal problem (interleaved
+prefixes, rank 0's tuned split) and the exact total is reduced.
 """
 import argparse
 import json
@@ -77,6 +79,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
+                    help="under torchrun: weak = each rank counts its own 64 diagonals "
+                         "(seed = rank); strong = the ranks split one 64-diagonal problem")
     ap.add_argument("--no-config4", action="store_true",
                     help="skip the second leg (vertically symmetric order 10, 2000 rows-1-2 "
                          "prefixes)")
@@ -200,12 +205,18 @@ def run_oracle(spec, o_order, pre, threads, extra=0):
     return counts, nodes, time.perf_counter() - t0
 
 
-def oracle_check(spec, seed, units, depth, suffix, pre, par, counts, threads):
+def oracle_check(spec, seed, units, depth, suffix, pre, par, counts, threads, share=None,
+                 par_all=None):
     """The oracle counts the prefixes of the bases spec.check_bases() picks,
     from its own order and split; they must equal the GPU's prefixes byte for
-    byte and its counts exactly (RuntimeError otherwise).  Returns the line's
-    'oracle_check' object, the oracle's rate on that sample (squares/s) and
-    the number of prefixes it counted."""
+    byte and its counts exactly (RuntimeError otherwise).  pre / par / counts
+    are this rank's rows; under strong scaling `share` holds their indices in
+    the whole problem and par_all its parents, and only this rank's rows of
+    the checked bases are compared.  Returns the line's 'oracle_check'
+    object, the oracle's rate on that sample (squares/s) and the number of
+    prefixes it counted."""
+    if share is None:
+        share, par_all = np.arange(len(pre), dtype=np.int64), par
     sums = np.zeros(units, np.uint64)
     np.add.at(sums, par, counts)
     idx = np.asarray(spec.check_bases(seed, sums))
@@ -213,10 +224,14 @@ def oracle_check(spec, seed, units, depth, suffix, pre, par, counts, threads):
     c, _, dt = run_oracle(spec, o_order, o_pre, threads, spec.oracle_extra)
     agree = True
     for k, b in enumerate(idx):
-        g = par == b
-        o = o_par == k
-        if not (g.sum() == o.sum() and (pre[g] == o_pre[o]).all()
-                and (counts[g] == c[o]).all()):
+        o_rows = np.nonzero(o_par == k)[0]       # the oracle's prefixes of base b
+        g_all = np.nonzero(par_all == b)[0]      # their places in the whole problem
+        mine = np.nonzero(par == b)[0]           # this rank's rows of base b
+        if len(g_all) != len(o_rows):
+            agree = False
+            continue
+        at = o_rows[np.searchsorted(g_all, share[mine])]
+        if not ((pre[mine] == o_pre[at]).all() and (counts[mine] == c[at]).all()):
             agree = False
     squares = int(c.sum())
     out = {"bases": int(len(idx)), "which": spec.check_rule, "prefixes": int(len(o_pre)),
@@ -361,6 +376,35 @@ def serving_leg(n_jobs, limit_s, seed=0, **cfg):
     return out
 
 
+def rank_share(n_prefixes, rank, ws, scaling):
+    """Indices of the prefixes this rank counts: all of its own problem under
+    weak scaling (each rank draws its own base prefixes), an interleaved
+    share of the one common problem under strong scaling."""
+    if scaling == "strong" and ws > 1:
+        from paper_1709_02599_gb300 import shard
+        return shard.shard_indices(n_prefixes, rank, ws)
+    return np.arange(n_prefixes, dtype=np.int64)
+
+
+def agree_on_choice(choice, ws, scaling):
+    """Under strong scaling every rank must count the same problem: rank 0's
+    tuned (depth, suffix, launch) is broadcast to the others."""
+    if scaling != "strong" or ws < 2:
+        return choice
+    import torch.distributed as dist
+    box = [choice]
+    dist.broadcast_object_list(box, src=0)
+    return box[0]
+
+
+def reduce_squares(local, ws):
+    """Exact sum of the ranks' square counts (one scalar collective)."""
+    if ws < 2:
+        return int(local)
+    from paper_1709_02599_gb300 import shard
+    return shard.allreduce_total(int(local))
+
+
 def reference_arm(args):
     """The oracle, as it stands, on the host cores: each step a bounded sample
     (one diagonal's prefixes) of the same workload."""
@@ -402,6 +446,8 @@ def reference_arm(args):
 
 def run_leg(dls, spec, args, steps, stream, flush, seed, rank, ws, units=None,
             plain_per_position=True):
+    # under strong scaling every rank draws the same base prefixes
+    seed = 0 if args.scaling == "strong" else seed
     """One workload: autotune (cached), then the graph-launched batched count
     timed over `steps` steps, the plain launches, the host-buffer entry, the
     roofline and the oracle check.  Returns (leg dict, step seconds, squares
@@ -430,7 +476,12 @@ def run_leg(dls, spec, args, steps, stream, flush, seed, rank, ws, units=None,
                                "heuristic_sq}, "
                                "then %d launch shapes" % (spec.depths,
                                                           len(shapes or autotune.SHAPES) - 1)}
+    depth_sel, suffix_sel, cfg = agree_on_choice((depth_sel, suffix_sel, cfg), ws, args.scaling)
     order, pre, par = autotune.build_problem(N, FLAGS, order0, base, depth_sel, suffix_sel)
+    P_all = len(pre)
+    share = rank_share(P_all, rank, ws, args.scaling)
+    par_all = par
+    pre, par = np.ascontiguousarray(pre[share]), par[share]
     P, depth = pre.shape
     d_pre = torch.from_numpy(pre).to("cuda")
     counts = torch.empty(P, dtype=torch.uint64, device="cuda")
@@ -548,7 +599,7 @@ def run_leg(dls, spec, args, steps, stream, flush, seed, rank, ws, units=None,
     if rank == 0 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
         chk, rate, n_pre = oracle_check(spec, seed, units, depth_sel, suffix_sel, pre, par,
-                                        counts_np, threads)
+                                        counts_np, threads, share, par_all)
         leg["oracle_check"] = chk
         leg["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                                "sample": "all %d prefixes of %s, same split and fill order as "
@@ -577,11 +628,7 @@ def main():
     spec = SPECS[args.workload]
     leg, step_s, squares = run_leg(dls, spec, args, args.steps, stream, flush, seed, rank, ws,
                                    units=args.diagonals or spec.units)
-    if ws > 1:
-        from paper_1709_02599_gb300 import shard
-        squares_all = shard.allreduce_total(squares)
-    else:
-        squares_all = squares
+    squares_all = reduce_squares(squares, ws)
     value = squares_all / step_s
     e2e = leg["e2e"]
     if e2e is not None and ws > 1:
@@ -589,7 +636,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * step_s, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "scaling": args.scaling, "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": leg["config"],
         "plain": leg["plain"],
         "plain_per_position_step": leg["plain_per_position_step"],
@@ -605,8 +652,9 @@ def main():
     # the largest single-GPU configuration as a second leg: the vertically
     # symmetric order-10 workload, fewer steps (one pass is ~1 s)
     if not args.no_config4 and spec.name != "vsym10_rows2" and not args.diagonals:
-        leg4, _, _ = run_leg(dls, SPECS["vsym10_rows2"], args, min(args.steps, 5), stream, flush,
-                             seed, rank, ws, plain_per_position=False)
+        leg4, step4, squares4 = run_leg(dls, SPECS["vsym10_rows2"], args, min(args.steps, 5),
+                                        stream, flush, seed, rank, ws, plain_per_position=False)
+        leg4["value"] = reduce_squares(squares4, ws) / step4
         leg4["gpu_launches"] = leg4["steps"]
         line["workloads"] = {"vsym10_rows2": leg4}
     if rank == 0 and args.serve_jobs > 0:

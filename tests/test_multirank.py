@@ -104,3 +104,52 @@ def test_failed_rank_is_detected_not_hung(tmp_path):
     if os.path.exists(r0):
         rec = np.load(r0, allow_pickle=True)
         assert rec[0] == "error"
+
+
+def _bench_worker(rank, world, port, out_path):
+    """bench.py's rank logic for --scaling strong, the oracle standing in for
+    each rank's GPU: rank 0's choice is broadcast, each rank counts its
+    interleaved share of the one problem, the total is reduced exactly, and
+    rank 0 checks its rows of the chosen diagonals against the oracle."""
+    import datetime
+    import torch.distributed as dist
+    import bench
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=60))
+    try:
+        spec = bench.SPECS["dls8_diag64"]
+        units = 4
+        mine = (28, "heuristic_sq", {}) if rank == 0 else (31, "given", {"block_threads": 32})
+        depth, suffix, cfg = bench.agree_on_choice(mine, world, "strong")
+        o_order, pre, par = spec.oracle_sample(0, units, np.arange(units), depth, suffix)
+        share = bench.rank_share(len(pre), rank, world, "strong")
+        local, _ = oracle.count_many(spec.n, spec.flags, o_order, pre[share], threads=2)
+        total = bench.reduce_squares(int(local.sum()), world)
+        checked = None
+        if rank == 0:
+            chk, _, _ = bench.oracle_check(spec, 0, units, depth, suffix, pre[share],
+                                           par[share], local, 2, share, par)
+            checked = chk["agree"]
+        np.save(out_path % rank, np.array([depth, suffix, len(share), total, checked],
+                                          dtype=object), allow_pickle=True)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_bench_strong_scaling_rank_logic(tmp_path):
+    world = 2
+    port = _free_port()
+    out = str(tmp_path / "b%d.npy")
+    mp.start_processes(_bench_worker, args=(world, port, out), nprocs=world, join=True,
+                       start_method="spawn")
+    import bench
+    spec = bench.SPECS["dls8_diag64"]
+    o_order, pre, _ = spec.oracle_sample(0, 4, np.arange(4), 28, "heuristic_sq")
+    ref, _ = oracle.count_many(spec.n, spec.flags, o_order, pre, threads=4)
+    res = [np.load(out % r, allow_pickle=True) for r in range(world)]
+    assert all(int(r[0]) == 28 and r[1] == "heuristic_sq" for r in res)   # rank 0's choice
+    assert sum(int(r[2]) for r in res) == len(pre)
+    assert all(int(r[3]) == int(ref.sum()) for r in res)
+    assert res[0][4] is True
