@@ -385,6 +385,23 @@ typedef struct {
  * dls_release()), CUDA. */
 int dls_stream_status(void *stream, dls_count_status *out);
 
+/* Counts every prefix (as dls_count_ex) and sums weight x Count over all of
+ * them in 128 bits on the device: Algorithm 6's Total += Cnt * multiple
+ * (Section 4.3), where the weight of an item is the class size of the
+ * canonical hourglass it extends (Corollary 1), and with unit weights the
+ * plain 128-bit total.  d_weights: DEVICE, n_prefixes uint32 (caller-owned),
+ * or NULL for all 1.  d_counts: DEVICE, n_prefixes uint64 receiving the
+ * counts, or NULL to keep them in the library's work area for `stream`
+ * (grown on demand, shared with dls_count_host: the same race applies).
+ * multiply: nonzero multiplies the total by dls_multiplier(n, flags) (row 0
+ * fixed -> all squares, Section 2.2).  *total_out: HOST.  Synchronous.
+ * Errors as dls_count_ex, BAD_ARG for a NULL total_out, and the count's
+ * status (INTERNAL, TIMEOUT, ABORTED) with *total_out not written. */
+int dls_count_weighted(int n, uint32_t flags, const uint8_t *order, int order_len,
+                       const uint8_t *d_prefixes, int depth, int64_t n_prefixes,
+                       const uint32_t *d_weights, uint64_t *d_counts, int multiply,
+                       dls_u128 *total_out, const dls_launch_t *cfg, void *stream);
+
 /* ---------------------------------------------------- symmetry breaking */
 
 /* Canonical hourglasses (Section 4.2, Algorithm 5).  An hourglass design has

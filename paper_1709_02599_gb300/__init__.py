@@ -199,6 +199,34 @@ def count(n, flags, order, prefixes, counts=None, total=None, nodes=None, launch
     return counts
 
 
+def count_weighted(n, flags, order, prefixes, weights=None, counts=None, multiply=False,
+                   launch=None, stream=None):
+    """Sum of weight x Count over the prefixes, in 128 bits on the device
+    (dls_count_weighted): Algorithm 6's total when the weights are class
+    sizes; the plain total with weights=None; times the row-0 multiplier
+    with multiply=True.  prefixes: uint8 CUDA tensor [P, depth]; weights:
+    int32/uint32 CUDA tensor [P] or None; counts: uint64 CUDA tensor [P] to
+    receive the counts, or None.  Synchronous; returns a Python int."""
+    import torch
+    if prefixes.dtype != torch.uint8 or not prefixes.is_cuda or prefixes.dim() != 2:
+        raise ValueError("prefixes must be a 2-D uint8 CUDA tensor")
+    prefixes = prefixes.contiguous()
+    P, depth = prefixes.shape
+    if weights is not None:
+        weights = weights.contiguous()
+        if weights.dtype not in (torch.int32, torch.uint32) or weights.shape != (P,):
+            raise ValueError("weights must be a [P] 32-bit CUDA tensor")
+    o, op, ol = _order(order)
+    cfg = (launch or Launch()).c()
+    tot = _lib.U128()
+    _lib.check(lib().dls_count_weighted(n, flags, op, ol, _dev_ptr(prefixes) if P else None,
+                                        depth, P, _dev_ptr(weights), _dev_ptr(counts),
+                                        1 if multiply else 0, ctypes.byref(tot),
+                                        ctypes.byref(cfg), _stream_handle(stream)),
+               "dls_count_weighted")
+    return tot.value()
+
+
 def count_plain(n, flags, order, prefixes, counts=None, total=None, stream=None):
     """The plain one-thread-per-prefix launch (dls_count_plain)."""
     import torch

@@ -151,6 +151,9 @@ def load():
         "dls_count_host_noalloc": (c_int, [c_int, c_u32, u8p, c_int, vp, c_int, c_i64, vp,
                                            ctypes.POINTER(U128), ctypes.POINTER(LaunchT), vp]),
         "dls_hourglass_classes": (c_int, [c_int, c_u32, u8p, c_int, vp, c_int64_t, vp, vp]),
+        "dls_count_weighted": (c_int, [c_int, c_u32, u8p, c_int, vp, c_int, c_i64, vp, vp,
+                                       c_int, ctypes.POINTER(U128), ctypes.POINTER(LaunchT),
+                                       vp]),
         "dls_release": (None, []),
         "dls_stream_status": (c_int, [vp, ctypes.POINTER(CountStatus)]),
         "dls_server_default_cfg": (None, [ctypes.POINTER(ServerCfg)]),

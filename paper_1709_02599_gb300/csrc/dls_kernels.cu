@@ -661,6 +661,56 @@ __global__ void __launch_bounds__(512)
   if (NODES) block_reduce_add(s.nodes, p.nodes, red);
 }
 
+// --------------------------------------------------- weighted 128-bit sum --
+
+// 128-bit (hi, lo) += 64-bit x * 32-bit y
+__device__ __forceinline__ void acc_mul(unsigned long long &hi, unsigned long long &lo,
+                                        unsigned long long x, unsigned y) {
+  const unsigned long long plo = x * (unsigned long long)y;
+  const unsigned long long phi = __umul64hi(x, (unsigned long long)y);
+  lo += plo;
+  hi += phi + (lo < plo ? 1ull : 0ull);
+}
+
+__device__ __forceinline__ void acc_add(unsigned long long &hi, unsigned long long &lo,
+                                        unsigned long long ohi, unsigned long long olo) {
+  lo += olo;
+  hi += ohi + (lo < olo ? 1ull : 0ull);
+}
+
+// Sum over k of counts[k] * weights[k] (weights NULL: 1) into out[0] (low
+// 64 bits) and out[1] (high 64 bits): per-thread 128-bit sums, a warp and a
+// block reduction, then one pair of atomics per block (the carry of the low
+// word is detected from the value it replaced).
+__global__ void __launch_bounds__(256) k_weighted_sum(const unsigned long long *counts,
+                                                      const uint32_t *weights, long long n,
+                                                      unsigned long long *out) {
+  __shared__ unsigned long long rh[8];
+  __shared__ unsigned long long rl[8];
+  unsigned long long hi = 0ull, lo = 0ull;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x)
+    acc_mul(hi, lo, counts[k], weights ? weights[k] : 1u);
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long h2 = __shfl_down_sync(FULL, hi, o);
+    const unsigned long long l2 = __shfl_down_sync(FULL, lo, o);
+    acc_add(hi, lo, h2, l2);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    rh[warp] = hi;
+    rl[warp] = lo;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    hi = lo = 0ull;
+    for (unsigned w = 0; w < (blockDim.x >> 5); ++w) acc_add(hi, lo, rh[w], rl[w]);
+    const unsigned long long old = atomicAdd(out, lo);
+    if (old + lo < old) hi += 1ull;
+    if (hi) atomicAdd(out + 1, hi);
+  }
+}
+
 // ------------------------------------------------------------ host side --
 
 // What the last count on a work area launched (for its status query).
@@ -1273,6 +1323,64 @@ int dls_count_host(int n, uint32_t flags, const uint8_t *order,
     }
     *total_out = t;
   }
+  return DLS_OK;
+}
+
+int dls_count_weighted(int n, uint32_t flags, const uint8_t *order, int order_len,
+                       const uint8_t *d_prefixes, int depth, int64_t n_prefixes,
+                       const uint32_t *d_weights, uint64_t *d_counts, int multiply,
+                       dls_u128 *total_out, const dls_launch_t *cfg, void *stream) {
+  if (total_out == nullptr || n_prefixes < 0) return DLS_ERR_BAD_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Workspace *ws = nullptr;
+  int rc = get_workspace(st, &ws);
+  if (rc) return rc;
+  cudaError_t e;
+  if (d_counts == nullptr && n_prefixes > 0) {
+    // the counts go to the work area's buffer (shared with dls_count_host)
+    std::lock_guard<std::mutex> g(g_ws_mutex);
+    if (ws->d2h_count < (size_t)n_prefixes + 1) {
+      if (ws->d2h) cudaFree(ws->d2h);
+      ws->d2h = nullptr;
+      ws->d2h_count = 0;
+      e = cudaMalloc(&ws->d2h, ((size_t)n_prefixes + 1) * sizeof(unsigned long long));
+      if (e != cudaSuccess) return cuda_fail(e);
+      ws->d2h_count = (size_t)n_prefixes + 1;
+    }
+    d_counts = reinterpret_cast<uint64_t *>(ws->d2h);
+  }
+  rc = enqueue_count(n, flags, order, order_len, d_prefixes, depth, n_prefixes, d_counts,
+                     nullptr, nullptr, cfg, st);
+  if (rc) return rc;
+  // words 2-3 of the work area: the 128-bit sum
+  unsigned long long *sum = ws->scratch + 2;
+  e = cudaMemsetAsync(sum, 0, 2 * sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (n_prefixes > 0) {
+    DevInfo di;
+    rc = dev_info(&di);
+    if (rc) return rc;
+    const long long want = (n_prefixes + 255) / 256;
+    const unsigned grid = (unsigned)std::max(1ll, std::min<long long>(want, 4ll * di.sms));
+    const unsigned long long *cnt = reinterpret_cast<const unsigned long long *>(d_counts);
+    const long long np = (long long)n_prefixes;
+    k_weighted_sum<<<grid, 256, 0, st>>>(cnt, d_weights, np, sum);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  unsigned long long h[4] = {0ull, 0ull, 0ull, 0ull};  // head, status, sum lo, sum hi
+  e = cudaMemcpyAsync(h, ws->scratch, sizeof(h), cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  rc = status_code((unsigned)h[1]);
+  if (rc) return rc;
+  dls_u128 t = {h[2], h[3]};
+  if (multiply) {
+    const dls_u128 m = dls_multiplier(n, flags);
+    t = dls_mul_u64(m.lo, t);  // the multiplier is below 2^64 for every order taken
+  }
+  *total_out = t;
   return DLS_OK;
 }
 

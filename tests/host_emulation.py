@@ -137,6 +137,8 @@ class Emulated:
                     "stack_entries", "fused"]
             return 0, dict(zip(keys, map(int, lines[1].split())))
         head = lines[1].split()
+        if "hi" in head:
+            self.last_total128 = int(head[head.index("hi") + 1]) << 64 | int(head[1])
         if "status" in head:
             k = head.index("status")
             self.last_status = (int(head[k + 1]), int(head[k + 3]))

@@ -60,6 +60,10 @@ inline unsigned atomicOr(unsigned *a, unsigned v) {
   *a = old | v;
   return old;
 }
+// high 64 bits of the 128-bit product
+inline unsigned long long __umul64hi(unsigned long long a, unsigned long long b) {
+  return (unsigned long long)(((unsigned __int128)a * b) >> 64);
+}
 inline unsigned long long atomicOr(unsigned long long *a, unsigned long long v) {
   const unsigned long long old = *a;
   *a = old | v;

@@ -10,7 +10,8 @@
 //                block_threads items_per_job max_order
 //
 // ENTRY: count (dls_count_ex with node counting, then dls_stream_status),
-// host (dls_count_host), noalloc (dls_count_host_noalloc), plan
+// host (dls_count_host), noalloc (dls_count_host_noalloc), weighted
+// (dls_count_weighted with weights (k % 5) + 1 and the multiplier), plan
 // (dls_plan_create, then two dls_plan_launch and dls_plan_status), describe
 // (dls_describe_launch).  "Device" buffers are host memory here.  Output:
 // "rc R" and, when R = 0, "total T nodes N" (nodes 0 where the entry does
@@ -253,6 +254,19 @@ int main(int argc, char **argv) {
                        : dls_count_host_noalloc(n, flags, order.data(), len, pre.data(), depth,
                                                 P, counts.data(), &t, &cfg, nullptr);
     // total_out: the plain 128-bit sum of the counts
+    std::printf("rc %d\n", rc);
+    if (rc == 0) {
+      std::printf("total %llu nodes 0 hi %llu\n", (unsigned long long)t.lo,
+                  (unsigned long long)t.hi);
+      for (uint64_t c : counts) std::printf("%llu\n", (unsigned long long)c);
+    }
+  } else if (entry == "weighted") {
+    // weights (k % 5) + 1, total times the row-0 multiplier
+    std::vector<uint32_t> w((size_t)P);
+    for (int64_t k = 0; k < P; ++k) w[(size_t)k] = (uint32_t)(k % 5) + 1u;
+    dls_u128 t{0, 0};
+    const int rc = dls_count_weighted(n, flags, order.data(), len, pre.data(), depth, P,
+                                      w.data(), counts.data(), 1, &t, &cfg, nullptr);
     std::printf("rc %d\n", rc);
     if (rc == 0) {
       std::printf("total %llu nodes 0 hi %llu\n", (unsigned long long)t.lo,

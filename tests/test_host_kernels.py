@@ -203,6 +203,22 @@ def test_budget_stops_and_the_rest_resumes(dls, emulated, sh):
         assert rc == ERR_TIMEOUT, entry
 
 
+def test_weighted_total(dls, emulated):
+    """dls_count_weighted: the counts, and the sum of weight x count in 128
+    bits times the row-0 multiplier (weights (k % 5) + 1 in the driver), for
+    both kernel families; order 8's multiplier 8! takes totals past 2^64
+    when the counts are those of whole squares."""
+    for n, after, step in ((7, 14, 7), (8, 20, 2000)):
+        wl = every(gpu_cases.split(dls, n, D, after), step)
+        ref, _ = oracle.count_many(n, D, wl.oracle_order, wl.oracle_prefixes)
+        w = np.arange(len(ref)) % 5 + 1
+        expect = sum(int(c) * int(x) for c, x in zip(ref, w)) * oracle.multiplier(n, D)
+        for sh in (dict(), dict(kernel=1)):
+            rc, res = emulated.count("weighted", n, D, wl.order, wl.prefixes, **sh)
+            assert rc == 0 and (res[0] == ref).all(), (n, sh)
+            assert emulated.last_total128 == expect, (n, sh)
+
+
 def test_abort_flag(dls, emulated):
     """A set abort flag stops the count before any prefix is finished
     (DLS_ERR_ABORTED); a flag that stays clear changes nothing."""
