@@ -58,16 +58,11 @@ DIAGS, AFTER_ROW0 = 64, 20
 OPS_PER_NODE = 11
 ISSUE_LANES_PER_SM = 4 * 32      # 4 schedulers x 32 lanes, one instruction/clk
 L2_FLUSH_BYTES = 256 << 20
-# DRAM bytes (read + write) per prefix of k_snapshot on the order-8 workload,
-# per split depth: ncu captures of 16 of the 64 diagonals, squared-count
-# order after the split (depth 25: 149 590 prefixes, 4.953 MB read; depth
-# 28: 273 038 prefixes, 9.893 MB read; 0 written while the kernel ran),
-# scaled per prefix; the profile summary under profiles/ gives the commands
-# (key "k_snapshot fused": the same kernel with the fused step, captured the
-# same way at depth 25: 5.015 MB read, 0 written)
-TRAFFIC_PER_PREFIX = {("dls8_diag64", "k_snapshot", 25): 4.953088e6 / 149590,
-                      ("dls8_diag64", "k_snapshot", 28): 9.892864e6 / 273038,
-                      ("dls8_diag64", "k_snapshot fused", 25): 5.015040e6 / 149590}
+# DRAM bytes (read + write) per prefix of the batched kernel, per (workload,
+# kernel, step, fused, split depth), from an ncu capture of that build (the
+# summary under profiles/ gives the command); a kernel without a capture of
+# its current build reports traffic null
+TRAFFIC_PER_PREFIX = {}
 
 
 def parse():
@@ -569,8 +564,7 @@ def run_leg(dls, spec, args, steps, stream, flush, seed, rank, ws, units=None,
     peak_tops = sms * ISSUE_LANES_PER_SM * sm_max_mhz * 1e6 / 1e12
     achieved_tops = nodes * OPS_PER_NODE / step_s / 1e12
     # the traffic figures belong to the kernel variant they were captured on
-    kernel_id = run["kernel"] + (" fused" if run.get("fused") else "")
-    tkey = (spec.name, kernel_id, depth)
+    tkey = (spec.name, run["kernel"], run["step"], bool(run.get("fused")), depth)
     leg = {
         "value": squares / step_s, "unit": UNIT, "steps": steps,
         "ms_per_step": 1e3 * step_s,

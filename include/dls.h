@@ -298,6 +298,10 @@ typedef struct {
     int smem_bytes;       /* dynamic shared memory per block                 */
     int stack_entries;    /* snapshot entries per lane (0 otherwise)         */
     int fused;            /* 1 = the snapshot search takes the fused step    */
+    int step;             /* the search step: 0 = one entry per position,
+                             1 = snapshots with field shifts (vertical
+                             symmetry), 2 = snapshots with byte words (n <= 8
+                             without vertical symmetry)                      */
 } dls_launch_info;
 
 /* Resolves the kernel and launch shape that dls_count_ex would use for these

@@ -162,7 +162,8 @@ def describe_launch(n, flags, order, depth, n_prefixes, launch=None):
     """The kernel and launch shape dls_count_ex would use (dls_describe_launch):
     a dict with 'kernel' (k_snapshot / k_persistent / k_plain_snap / k_plain), 'words'
     ('registers' or 'shared'), 'block_threads', 'grid_blocks', 'smem_bytes',
-    'stack_entries', 'fused' (the snapshot search's fused step)."""
+    'stack_entries', 'fused' (the snapshot search's fused step), 'step' (which
+    search step runs)."""
     o, op, ol = _order(order)
     cfg = (launch or Launch()).c()
     info = _lib.LaunchInfo()
@@ -173,7 +174,7 @@ def describe_launch(n, flags, order, depth, n_prefixes, launch=None):
             "words": "registers" if info.words == 2 else "shared",
             "block_threads": info.block_threads, "grid_blocks": info.grid_blocks,
             "smem_bytes": info.smem_bytes, "stack_entries": info.stack_entries,
-            "fused": bool(info.fused)}
+            "fused": bool(info.fused), "step": _lib.STEP_NAMES[info.step]}
 
 
 def count(n, flags, order, prefixes, counts=None, total=None, nodes=None, launch=None,

@@ -25,6 +25,7 @@ RUN_SNAPSHOT = 2
 RUN_PLAIN_SNAPSHOT = 3
 RUN_NAMES = {RUN_PERSISTENT: "k_persistent", RUN_PLAIN: "k_plain", RUN_SNAPSHOT: "k_snapshot",
              RUN_PLAIN_SNAPSHOT: "k_plain_snap"}
+STEP_NAMES = {0: "per-position", 1: "snapshot, field shifts", 2: "snapshot, byte words"}
 
 OK = 0
 ERR_CAPACITY = 4
@@ -69,7 +70,8 @@ class LaunchInfo(ctypes.Structure):
                 ("grid_blocks", ctypes.c_int),
                 ("smem_bytes", ctypes.c_int),
                 ("stack_entries", ctypes.c_int),
-                ("fused", ctypes.c_int)]
+                ("fused", ctypes.c_int),
+                ("step", ctypes.c_int)]
 
 
 class CountStatus(ctypes.Structure):

@@ -452,13 +452,84 @@ __device__ bool snap_load(SnapLane &s, const KParams &p, long long item, const C
   return L == 0u;
 }
 
+// The same for a byte-word lane (orders n <= 8 without vertical symmetry):
+// the prefix is placed into the 64-bit words, which are then split into the
+// four byte words.
+template <bool VSYM, bool NODES>
+__device__ bool snap_load(BLane &s, const KParams &p, long long item, const Cell *tbl,
+                          const BRow *tb) {
+  static_assert(!VSYM, "byte words: no vertical symmetry");
+  const Geo &g = p.g;
+  s.prefix = item;
+  s.cnt = 0ull;
+  s.sp = s.bot = 0;
+  Words<true> w;
+  w.tb = nullptr;
+  w.clear(0, 0u);
+  const bool ok =
+      place_prefix<true, false>(w, g, p.prefixes + (size_t)item * (size_t)g.depth, tbl);
+  s.R0 = (uint32_t)w.R;
+  s.R1 = (uint32_t)(w.R >> 32);
+  s.C0 = (uint32_t)w.C;
+  s.C1 = (uint32_t)(w.C >> 32);
+  s.dg = w.dg;
+  if (!ok) return true;
+  if (g.depth == p.order_len) {
+    s.cnt = 1ull;
+    return true;
+  }
+  const uint32_t L = w.template cands<false>(tbl[g.depth], g);
+  if (g.depth == g.last) {
+    s.cnt = (unsigned)__popc(L);
+    if (NODES) s.nodes += (unsigned)__popc(L);
+    return true;
+  }
+  s.p = g.depth;
+  s.L = L;
+  const BRow &row = tb[g.depth];
+  s.a = row.a;
+  s.b = row.b;
+  s.c = row.c;
+  return L == 0u;
+}
+
 // In-warp work donation for snapshot lanes: each idle lane is paired with a
 // busy lane that holds a stack entry; it takes the busy lane's bottom entry
 // (the shallowest open cell: the largest untried subtree) and the busy lane
 // drops it by raising its bottom index.
+// Restores a lane's words from an entry (line words, packed word) and loads
+// the table row of its position.
 template <bool VSYM, bool DG>
-__device__ void snap_donate(SnapLane &s, bool &busy, const KParams &p, const SnapStack &st,
-                            const SnapTable &tb, int lane, unsigned B) {
+__device__ __forceinline__ void snap_take(SnapLane &s, const KParams &p, uint4 a, uint32_t wv,
+                                          const SnapTable &tb) {
+  s.w.R = ((unsigned long long)a.y << 32) | a.x;
+  s.w.C = ((unsigned long long)a.w << 32) | a.z;
+  uint32_t dg;
+  snap_unpack<VSYM>(wv, p.g.n, dg, s.p, s.L);
+  if (DG) s.w.dg = dg;
+  s.sh = tb.sh[s.p];
+  s.dm = tb.dm[s.p];
+}
+
+template <bool VSYM, bool DG>
+__device__ __forceinline__ void snap_take(BLane &s, const KParams &p, uint4 a, uint32_t wv,
+                                          const BRow *tb) {
+  s.R0 = a.x;
+  s.R1 = a.y;
+  s.C0 = a.z;
+  s.C1 = a.w;
+  uint32_t dg;
+  snap_unpack<false>(wv, p.g.n, dg, s.p, s.L);
+  if (DG) s.dg = dg;
+  const BRow &row = tb[s.p];
+  s.a = row.a;
+  s.b = row.b;
+  s.c = row.c;
+}
+
+template <bool VSYM, bool DG, class LaneT, class TableT>
+__device__ void snap_donate(LaneT &s, bool &busy, const KParams &p, const SnapStack &st,
+                            const TableT &tb, int lane, unsigned B) {
   const unsigned idle = __ballot_sync(FULL, !busy);
   if (idle == 0u || idle == FULL) return;
   const unsigned donors = __ballot_sync(FULL, busy && s.sp > s.bot);
@@ -480,15 +551,7 @@ __device__ void snap_donate(SnapLane &s, bool &busy, const KParams &p, const Sna
   const long long d_prefix = __shfl_sync(FULL, s.prefix, partner);
   if (receiver) {
     const int off = (d_bot + 1) * (int)B + (partner - lane);
-    const uint4 a = st.sa[off];
-    const uint32_t wv = st.sw[off];
-    s.w.R = ((unsigned long long)a.y << 32) | a.x;
-    s.w.C = ((unsigned long long)a.w << 32) | a.z;
-    uint32_t dg;
-    snap_unpack<VSYM>(wv, p.g.n, dg, s.p, s.L);
-    if (DG) s.w.dg = dg;
-    s.sh = tb.sh[s.p];
-    s.dm = tb.dm[s.p];
+    snap_take<VSYM, DG>(s, p, st.sa[off], st.sw[off], tb);
     s.sp = s.bot = 0;
     s.prefix = d_prefix;
     s.cnt = 0ull;
@@ -498,12 +561,38 @@ __device__ void snap_donate(SnapLane &s, bool &busy, const KParams &p, const Sna
   if (giver) s.bot++;
 }
 
-// Shared memory: [cell table: 8 bytes per position, rounded to 32 positions]
-//                [position table: 16 + 8 bytes per position, same rounding]
-//                [stack: (cap + 2) * B entries of 16 bytes, then as many of 4]
-__device__ __forceinline__ void snap_setup(const KParams &p, int diag, uint32_t *smem,
-                                           const Cell *&tbl, SnapTable &tb, SnapStack &st,
-                                           SnapLane &s, bool two_on) {
+// The two snapshot searches: register words with field shifts (vertically
+// symmetric orders; SnapLane, snap_step) and byte words (all other orders
+// n <= 8; BLane, bsnap_step).
+template <bool VSYM>
+struct SnapKind {
+  using Lane = SnapLane;
+  using Table = SnapTable;
+  template <bool NODES, bool DG, bool LA, bool FU>
+  static __device__ __forceinline__ bool step(Lane &s, const Geo &g, const SnapStack &st,
+                                              const Table &tb, unsigned B, uint32_t &ovf) {
+    return snap_step<true, NODES, DG, LA, FU>(s, g, st, tb, B, ovf);
+  }
+};
+
+template <>
+struct SnapKind<false> {
+  using Lane = BLane;
+  using Table = const BRow *;
+  template <bool NODES, bool DG, bool LA, bool FU>
+  static __device__ __forceinline__ bool step(Lane &s, const Geo &g, const SnapStack &st,
+                                              const Table &tb, unsigned B, uint32_t &ovf) {
+    return bsnap_step<NODES, DG, LA, FU>(s, g, st, tb, B, ovf);
+  }
+};
+
+// Position tables in shared memory; returns where the stacks start.
+// [cell table: 8 bytes per position, rounded to 32 positions]
+// [position table: 24 bytes per position (shifts and diagonal masks), or 48
+//  (byte-word rows), same rounding]
+__device__ __forceinline__ uint4 *snap_tables(const KParams &p, int diag, bool dgw,
+                                              uint32_t *smem, const Cell *&tbl, SnapTable &tb,
+                                              bool two_on) {
   const unsigned B = blockDim.x;
   const int rows = (p.order_len + 31) & ~31;
   Cell *t = reinterpret_cast<Cell *>(smem);
@@ -521,24 +610,40 @@ __device__ __forceinline__ void snap_setup(const KParams &p, int diag, uint32_t 
       tdm[idx] = make_uint2((uint32_t)(p.ci[n2] * p.wr), (uint32_t)(p.cj[n2] * p.wc));
     }
   }
-  uint4 *sa0 = reinterpret_cast<uint4 *>(tdm + rows);
-  st.sa = sa0 + threadIdx.x;
-  st.sw = reinterpret_cast<uint32_t *>(sa0 + (size_t)(p.snap_cap + 2) * B) + threadIdx.x;
-  st.cap = p.snap_cap;
   tbl = t;
   tb.sh = tsh;
   tb.dm = tdm;
-  s.w.tb = nullptr;
-  s.w.R = s.w.C = 0ull;
-  s.w.dg = 0u;
-  s.p = 0;
-  s.L = 0u;
-  s.sh = make_uint4(0u, 0u, 0u, 0u);
-  s.dm = make_uint2(0u, 0u);
-  s.sp = s.bot = 0;
-  s.prefix = 0;
-  s.cnt = 0ull;
-  s.nodes = 0ull;
+  return reinterpret_cast<uint4 *>(tdm + rows);
+}
+
+__device__ __forceinline__ uint4 *snap_tables(const KParams &p, int diag, bool dgw,
+                                              uint32_t *smem, const Cell *&tbl,
+                                              const BRow *&tb, bool) {
+  const unsigned B = blockDim.x;
+  const int rows = (p.order_len + 31) & ~31;
+  Cell *t = reinterpret_cast<Cell *>(smem);
+  BRow *rw = reinterpret_cast<BRow *>(smem + 2 * rows);
+  for (int idx = threadIdx.x; idx < p.order_len; idx += B) {
+    t[idx] = describe_regs(p.ci[idx], p.cj[idx], p.g.n, diag != 0, 8, 8);
+    rw[idx] = brow_make(p.g.n, diag != 0, dgw, p.ci, p.cj, idx, p.order_len);
+  }
+  tbl = t;
+  tb = rw;
+  return reinterpret_cast<uint4 *>(rw + rows);
+}
+
+// Shared memory: the position tables (snap_tables), then the stacks:
+// (cap + 2) * B entries of 16 bytes, then as many of 4.
+template <class LaneT, class TableT>
+__device__ __forceinline__ void snap_setup(const KParams &p, int diag, bool dgw,
+                                           uint32_t *smem, const Cell *&tbl, TableT &tb,
+                                           SnapStack &st, LaneT &s, bool two_on) {
+  const unsigned B = blockDim.x;
+  uint4 *sa0 = snap_tables(p, diag, dgw, smem, tbl, tb, two_on);
+  st.sa = sa0 + threadIdx.x;
+  st.sw = reinterpret_cast<uint32_t *>(sa0 + (size_t)(p.snap_cap + 2) * B) + threadIdx.x;
+  st.cap = p.snap_cap;
+  s = LaneT{};
   __syncthreads();
 }
 
@@ -551,11 +656,12 @@ __global__ void __launch_bounds__(512)
   extern __shared__ uint32_t smem[];
   __shared__ unsigned long long red[16];
   const unsigned B = blockDim.x;
+  using K = SnapKind<VSYM>;
   const Cell *tbl;
-  SnapTable tb;
+  typename K::Table tb;
   SnapStack st;
-  SnapLane s;
-  snap_setup(p, diag, smem, tbl, tb, st, s, FU);
+  typename K::Lane s;
+  snap_setup(p, diag, DG, smem, tbl, tb, st, s, FU);
   uint32_t ovf = 0u;
   unsigned long long lane_total = 0ull;
   const long long item = (long long)blockIdx.x * B + threadIdx.x;
@@ -569,7 +675,7 @@ __global__ void __launch_bounds__(512)
   unsigned stopped = 0u;
   int k = 0;
   while (__any_sync(FULL, busy)) {
-    if (busy && snap_step<VSYM, NODES, DG, false, FU>(s, p.g, st, tb, B, ovf)) {
+    if (busy && K::template step<NODES, DG, false, FU>(s, p.g, st, tb, B, ovf)) {
       busy = false;
       flush_count(s.prefix, s.cnt, p, lane_total);
     }
@@ -593,11 +699,12 @@ __global__ void __launch_bounds__(512)
   __shared__ unsigned long long red[16];
   const unsigned B = blockDim.x;
   const int lane = threadIdx.x & 31;
+  using K = SnapKind<VSYM>;
   const Cell *tbl;
-  SnapTable tb;
+  typename K::Table tb;
   SnapStack st;
-  SnapLane s;
-  snap_setup(p, diag, smem, tbl, tb, st, s, LA || FU);
+  typename K::Lane s;
+  snap_setup(p, diag, DG, smem, tbl, tb, st, s, LA || FU);
   uint32_t ovf = 0u;
 
   unsigned long long lane_total = 0ull;
@@ -631,12 +738,12 @@ __global__ void __launch_bounds__(512)
       bool fin;
       if (!stoppable) {
         do {
-          fin = snap_step<VSYM, NODES, DG, LA, FU>(s, p.g, st, tb, B, ovf);
+          fin = K::template step<NODES, DG, LA, FU>(s, p.g, st, tb, B, ovf);
         } while (!__any_sync(FULL, fin));
       } else {
         int k = 0;
         do {
-          fin = snap_step<VSYM, NODES, DG, LA, FU>(s, p.g, st, tb, B, ovf);
+          fin = K::template step<NODES, DG, LA, FU>(s, p.g, st, tb, B, ovf);
         } while (!__any_sync(FULL, fin) && ++k <= p.check_mask);
         spent += k + 1;
       }
@@ -646,7 +753,7 @@ __global__ void __launch_bounds__(512)
       }
     } else {
       for (int it = 0; it <= p.check_mask; ++it) {
-        if (busy && snap_step<VSYM, NODES, DG, LA, FU>(s, p.g, st, tb, B, ovf)) {
+        if (busy && K::template step<NODES, DG, LA, FU>(s, p.g, st, tb, B, ovf)) {
           busy = false;
           flush_count(s.prefix, s.cnt, p, lane_total);
         }
@@ -959,10 +1066,12 @@ static size_t smem_bytes(int order_len, int n, int depth, int last, int block,
   return (size_t)((order_len + 31) & ~31) * 8u + (size_t)((reg ? 0 : 2 * n) + stack) * block * 4u;
 }
 
-// Snapshot kernel: the cell table and the position table (8 + 24 bytes per
-// position), then 20 bytes per entry slot and lane (cap + 2 slots).
-static size_t smem_bytes_snapshot(int order_len, int entries, int block) {
-  return (size_t)((order_len + 31) & ~31) * 32u + (size_t)(entries + 2) * block * 20u;
+// Snapshot kernels: the cell table and the position table (8 + 24 bytes per
+// position with vertical symmetry, 8 + 48 with byte words), then 20 bytes per
+// entry slot and lane (cap + 2 slots).
+static size_t smem_bytes_snapshot(int order_len, int entries, int block, bool vsym) {
+  return (size_t)((order_len + 31) & ~31) * (vsym ? 32u : 56u) +
+         (size_t)(entries + 2) * block * 20u;
 }
 
 // A resolved launch: the parameter block, the kernel and its shape.
@@ -1047,7 +1156,7 @@ static int prepare_launch(int n, uint32_t flags, const uint8_t *order, int order
   // by default, an explicit block size whose snapshot stacks do not fit
   // falls back to the per-position stack (a fifth of the bytes per entry)
   if (snap && sh.stack == 0 && !default_block &&
-      smem_bytes_snapshot(order_len, kp.snap_cap, sh.block) + static_smem > di.smem_optin) {
+      smem_bytes_snapshot(order_len, kp.snap_cap, sh.block, vsym) + static_smem > di.smem_optin) {
     snap = false;
     kp.snap_cap = 0;
   }
@@ -1067,7 +1176,7 @@ static int prepare_launch(int n, uint32_t flags, const uint8_t *order, int order
   pr->fn = snap ? pick_snapshot(plain, vsym, d_nodes != nullptr, dgw, la, fu)
                 : pick_kernel(sh.kernel, reg, vsym, d_nodes != nullptr, sh.lanes_log2 > 0);
   auto smem_for = [&](int block) {
-    return snap ? smem_bytes_snapshot(order_len, kp.snap_cap, block)
+    return snap ? smem_bytes_snapshot(order_len, kp.snap_cap, block, vsym)
                 : smem_bytes(order_len, n, depth, order_len - 1, block, reg);
   };
   size_t smem = smem_for(sh.block);
@@ -1232,6 +1341,8 @@ int dls_describe_launch(int n, uint32_t flags, const uint8_t *order, int order_l
   out->smem_bytes = (int)pr.smem;
   out->stack_entries = pr.kp.snap_cap;
   out->fused = pr.fused ? 1 : 0;
+  const bool snapshot = pr.run == DLS_RUN_SNAPSHOT || pr.run == DLS_RUN_PLAIN_SNAPSHOT;
+  out->step = !snapshot ? 0 : ((flags & DLS_VSYM) ? 1 : 2);
   return DLS_OK;
 }
 

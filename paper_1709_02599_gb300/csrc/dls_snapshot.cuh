@@ -238,4 +238,143 @@ __device__ __forceinline__ bool snap_step(SnapLane &s, const Geo &g, const SnapS
   return dead && !keep && !has;
 }
 
+// ------------------------------------------------------------ byte words --
+//
+// Orders n <= 8 without vertical symmetry keep every row word and every
+// column word in one byte: rows 0-3 are the bytes of R0 and rows 4-7 those
+// of R1, columns 0-3 of C0 and 4-7 of C1.  A cell's admissible values are
+// then two byte permutes (one per word pair, picking the cell's row byte and
+// column byte) and one three-input logic operation; a value is placed with
+// four multiply-adds, one per word, by the multipliers 2^(8k) or 0 of the
+// cell's row and column (the bit placed is always clear, so adding it sets
+// it).  The multiply-adds run on the FMA pipe, leaving the integer ALU --
+// the unit the search is bound by -- the rest of the step.  The stack and its
+// entries are those of the search above: R0, R1, C0, C1 as one 16-byte word,
+// and the packed word (diagonal words, position, untried candidates).
+
+// Position table row for order position p (48 bytes):
+//   a: multipliers that place a value at p (row into R0 / R1, column into
+//      C0 / C1);
+//   b: the same for p + 1 (the fused step), or, with diagonal words, the
+//      diagonal masks of p and of p + 1 (as Cell::y) in b.x and b.y;
+//   c: byte selectors of the row and the column of p + 1, then of p + 2
+//      (the lookahead and the fused step read p + 2).
+// Positions past the last repeat the last cell; no step uses them.
+struct BRow {
+  uint4 a, b, c;
+};
+
+__host__ __device__ inline uint32_t byte_mult(int k, int half) {
+  return (k >> 2) == half ? (1u << (8 * (k & 3))) : 0u;
+}
+
+__host__ __device__ inline BRow brow_make(int n, bool diag, bool dgw, const uint8_t *ci,
+                                          const uint8_t *cj, int p, int len) {
+  const int q = p + 1 < len ? p + 1 : len - 1;
+  const int q2 = p + 2 < len ? p + 2 : len - 1;
+  BRow r;
+  r.a = make_uint4(byte_mult(ci[p], 0), byte_mult(ci[p], 1), byte_mult(cj[p], 0),
+                   byte_mult(cj[p], 1));
+  if (dgw) {
+    const Cell c0 = describe_regs(ci[p], cj[p], n, diag, 8, 8);
+    const Cell c1 = describe_regs(ci[q], cj[q], n, diag, 8, 8);
+    r.b = make_uint4(c0.y, c1.y, 0u, 0u);
+  } else {
+    r.b = make_uint4(byte_mult(ci[q], 0), byte_mult(ci[q], 1), byte_mult(cj[q], 0),
+                     byte_mult(cj[q], 1));
+  }
+  r.c = make_uint4(ci[q], cj[q], ci[q2], cj[q2]);
+  return r;
+}
+
+// Per-lane state of the byte-word search.
+struct BLane {
+  uint32_t R0, R1, C0, C1;   // row and column bytes of the current path
+  uint32_t dg;               // diagonal words (as Words::dg)
+  int p;                     // position whose candidates L are being tried
+  uint32_t L;                // untried candidates at p
+  uint4 a, b, c;             // table row of p
+  int sp, bot;               // live entries [bot, sp)
+  long long prefix;
+  unsigned long long cnt;
+  unsigned long long nodes;
+};
+
+// Admissible values at the cell whose byte selectors are (sr, sc).
+__device__ __forceinline__ uint32_t bcands(uint32_t R0, uint32_t R1, uint32_t C0, uint32_t C1,
+                                           uint32_t sr, uint32_t sc, uint32_t all) {
+  return all & ~(__byte_perm(R0, R1, sr) | __byte_perm(C0, C1, sc));
+}
+
+// One search iteration of the byte-word search; the same moves as snap_step
+// (see there), returns true when the lane's work is finished.
+template <bool NODES, bool DG, bool LA = false, bool FU = false>
+__device__ __forceinline__ bool bsnap_step(BLane &s, const Geo &g, const SnapStack &st,
+                                           const BRow *tb, unsigned B, uint32_t &ovf) {
+  static_assert(!LA || !DG, "lookahead: no diagonal words");
+  static_assert(!FU || (!DG && !LA), "fused step: no diagonal words, no lookahead");
+  const uint32_t nv = s.L & (0u - s.L);
+  const uint32_t Lr = s.L ^ nv;
+  const bool keep = Lr != 0u;
+  const bool has = s.sp > s.bot;
+  int q = s.p + 1;  // <= last: a lane never stands on the last cell
+  const uint32_t R0 = s.R0, R1 = s.R1, C0 = s.C0, C1 = s.C1, dg0 = s.dg;
+  uint32_t r0 = nv * s.a.x + R0, r1 = nv * s.a.y + R1;
+  uint32_t c0 = nv * s.a.z + C0, c1 = nv * s.a.w + C1;
+  uint32_t L1 = bcands(r0, r1, c0, c1, s.c.x, s.c.y, g.all);
+  uint32_t dg = dg0;
+  if (DG) {
+    dg += (nv * 0x10001u) & s.b.x;
+    const uint32_t t = dg & s.b.y;
+    L1 &= ~(t | (t >> 16));
+  }
+  if (NODES) s.nodes++;
+  if (FU) {
+    // one candidate at q (q not the last cell): place it too
+    const bool f = q != g.last && L1 != 0u && (L1 & (L1 - 1u)) == 0u;
+    const uint32_t d2 = f ? L1 : 0u;
+    r0 = d2 * s.b.x + r0;
+    r1 = d2 * s.b.y + r1;
+    c0 = d2 * s.b.z + c0;
+    c1 = d2 * s.b.w + c1;
+    const uint32_t L2 = bcands(r0, r1, c0, c1, s.c.z, s.c.w, g.all);
+    if (NODES) s.nodes += f ? 1u : 0u;
+    L1 = f ? L2 : L1;
+    q = f ? q + 1 : q;
+  }
+  const bool leaf = q == g.last;
+  const unsigned leaves = leaf ? (unsigned)__popc(L1) : 0u;
+  s.cnt += leaves;
+  if (NODES) s.nodes += leaves;
+  bool dead = leaf || L1 == 0u;
+  if (LA) dead = dead || bcands(r0, r1, c0, c1, s.c.z, s.c.w, g.all) == 0u;
+  // the state before placing nv goes to the first free slot (a push keeps
+  // it); the entry a dead end resumes is read back (see snap_step)
+  st.sa[(s.sp + 1) * (int)B] = make_uint4(R0, R1, C0, C1);
+  st.sw[(s.sp + 1) * (int)B] = snap_pack<false>(DG ? dg0 : 0u, s.p, Lr);
+  const int rd = (keep || s.sp <= s.bot) ? s.sp + 1 : s.sp;
+  const uint4 ea = st.sa[rd * (int)B];
+  const uint32_t ew = st.sw[rd * (int)B];
+  const bool push = keep && !dead;
+  const bool pop = dead && !keep && has;
+  ovf |= (push && s.sp >= st.cap) ? 1u : 0u;
+  uint32_t edg, eL;
+  int ep;
+  snap_unpack<false>(ew, g.n, edg, ep, eL);
+  s.R0 = dead ? ea.x : r0;
+  s.R1 = dead ? ea.y : r1;
+  s.C0 = dead ? ea.z : c0;
+  s.C1 = dead ? ea.w : c1;
+  if (DG) s.dg = dead ? edg : dg;
+  s.L = dead ? eL : L1;
+  s.p = dead ? ep : q;
+  s.sp = min(s.sp + (push ? 1 : 0) - (pop ? 1 : 0), st.cap);
+  // table row of the new position, for the next iteration
+  const BRow &row = tb[s.p];
+  s.a = row.a;
+  s.b = row.b;
+  s.c = row.c;
+  return dead && !keep && !has;
+}
+
 }  // namespace dls

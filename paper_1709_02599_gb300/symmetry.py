@@ -5,8 +5,8 @@
 
 Every hourglass (row 0, both diagonals, last row) is enumerated by the prefix
 split, dls_hourglass_classes keeps the canonical ones with their class sizes
-(GPU), dls_count counts the completions of the canonical ones (GPU), and the
-total is the sum of class size x completions (Corollary 1).
+(GPU), and dls_count_weighted counts the completions of the canonical ones
+and sums class size x completions in 128 bits (GPU; Corollary 1).
 
 For orders whose hourglasses do not fit in memory at once (order 9 has
 1.49e9), count_symmetry_broken_resumable does the same in workunits.  A
@@ -19,8 +19,8 @@ import ctypes
 
 import numpy as np
 
-from . import (_lib, lib, count as dls_count, extend_prefixes, fill_order, order_complete,
-               DIAGONAL, VSYM, ORDER_HOURGLASS, ORDER_HEURISTIC, Launch)
+from . import (_lib, lib, count as dls_count, count_weighted, extend_prefixes, fill_order,
+               order_complete, DIAGONAL, VSYM, ORDER_HOURGLASS, ORDER_HEURISTIC, Launch)
 
 
 def hourglass_len(n, vsym=False):
@@ -76,13 +76,15 @@ def count_symmetry_broken(n, flags=DIAGONAL, launch=None, min_items=1 << 20):
         items, par = extend_prefixes(n, flags, order, items, depth + 1)
         parent = parent[par]
         depth += 1
-    counts = dls_count(n, flags, order, torch.from_numpy(items).cuda(), launch=launch)
-    torch.cuda.synchronize()
+    # Algorithm 6's Total += Cnt * multiple in the library: each item weighs
+    # the class size of its representative, the weighted sum is taken in 128
+    # bits on the device (dls_count_weighted)
+    d_items = torch.from_numpy(items).cuda()
+    weights = torch.from_numpy(sz[parent].astype(np.int32)).cuda()
+    counts = torch.empty(len(items), dtype=torch.uint64, device="cuda")
+    total = count_weighted(n, flags, order, d_items, weights=weights, counts=counts,
+                           launch=launch)
     ct = counts.cpu().numpy()
-    per_rep = np.zeros(len(reps), dtype=object)
-    for r, c in zip(parent, ct):
-        per_rep[r] += int(c)
-    total = sum(int(s) * int(c) for s, c in zip(sz, per_rep))
     return {"total": total, "hourglasses": int(len(hg)), "classes": int(len(canon)),
             "class_size_sum": int(sizes.sum().item()), "max_class": int(sz.max()) if len(sz) else 0,
             "squares_counted": int(ct.sum()), "items": int(len(items)), "split_depth": depth,

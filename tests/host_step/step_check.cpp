@@ -1,13 +1,15 @@
-// step_check.cpp -- runs the kernels' per-lane search steps (snap_step of
+// step_check.cpp -- runs the kernels' per-lane search steps (bsnap_step and snap_step of
 // dls_snapshot.cuh, dfs_step of dls_search.cuh, compiled for the host
 // through shim.h) on one lane per work item, with no warp and no donation,
 // for tests/test_host_step.py.
 //
 //   step_check n flags mode order.bin prefixes.bin depth cap [lanes_log2 split_pos]
 //
-// mode, the snapshot step: 0 = plain (diagonal words when a cell after the
-// prefix lies on a diagonal), 1 = lookahead, 2 = fused step (1 and 2 only
-// without diagonal words and without vertical symmetry; exit 2 otherwise).
+// mode, the snapshot step (the byte-word step without vertical symmetry,
+// the field-shift step with it): 0 = plain (diagonal words when a cell
+// after the prefix lies on a diagonal), 1 = lookahead, 2 = fused step (1 and
+// 2 only without diagonal words and without vertical symmetry; exit 2
+// otherwise).
 // mode, the per-position step (one stack entry per position): 10 = words in
 // registers (exit 2 where they do not fit), 11 = words in the shared-memory
 // layout, 12 = as 11 with vertical symmetry taken at run time (the serving
@@ -40,6 +42,21 @@ struct Run {
   uint32_t ovf = 0u;
   int badpos = 0;
 };
+
+// The byte-word step (orders n <= 8 without vertical symmetry).
+template <bool DG, bool LA, bool FU>
+bool bsearch(BLane &s, const Geo &g, const SnapStack &st, const BRow *tb, int len, Run &run) {
+  for (;;) {
+    ++run.iters;
+    const bool fin = bsnap_step<true, DG, LA, FU>(s, g, st, tb, 1u, run.ovf);
+    if (s.p < 0 || s.p >= len || s.sp < 0 || s.sp > st.cap) {
+      ++run.badpos;
+      return false;
+    }
+    run.maxsp = std::max(run.maxsp, s.sp);
+    if (fin) return true;
+  }
+}
 
 template <bool VSYM, bool DG, bool LA, bool FU>
 bool search(SnapLane &s, const Geo &g, const SnapStack &st, const SnapTable &tb, int len,
@@ -233,6 +250,13 @@ int main(int argc, char **argv) {
     }
   }
   const SnapTable tb{tsh.data(), tdm.data()};
+  std::vector<uint8_t> ci(len), cj(len);
+  for (int t = 0; t < len; ++t) {
+    ci[t] = ob[2 * t];
+    cj[t] = ob[2 * t + 1];
+  }
+  std::vector<BRow> brows(len);
+  for (int t = 0; t < len; ++t) brows[t] = brow_make(n, diag, dg, ci.data(), cj.data(), t, len);
   Geo g;
   g.n = n;
   g.all = (1u << n) - 1u;
@@ -262,6 +286,34 @@ int main(int argc, char **argv) {
       const uint32_t L = vsym ? s.w.cands<true>(tbl[depth], g) : s.w.cands<false>(tbl[depth], g);
       if (depth == g.last) {
         cnt = nodes = (unsigned)__popc(L);
+      } else if (L != 0u && !vsym) {
+        // byte words: the kernels' search for every order without symmetry
+        BLane b{};
+        b.R0 = (uint32_t)s.w.R;
+        b.R1 = (uint32_t)(s.w.R >> 32);
+        b.C0 = (uint32_t)s.w.C;
+        b.C1 = (uint32_t)(s.w.C >> 32);
+        b.dg = s.w.dg;
+        b.p = depth;
+        b.L = L;
+        b.a = brows[depth].a;
+        b.b = brows[depth].b;
+        b.c = brows[depth].c;
+        bool done;
+        if (mode == 1)
+          done = bsearch<false, true, false>(b, g, st, brows.data(), len, run);
+        else if (mode == 2)
+          done = bsearch<false, false, true>(b, g, st, brows.data(), len, run);
+        else
+          done = dg ? bsearch<true, false, false>(b, g, st, brows.data(), len, run)
+                    : bsearch<false, false, false>(b, g, st, brows.data(), len, run);
+        if (!done) {
+          std::fprintf(stderr, "iters %llu maxsp %d overflow %u badpos %d\n", run.iters,
+                       run.maxsp, run.ovf, run.badpos);
+          return 3;
+        }
+        cnt = b.cnt;
+        nodes = b.nodes;
       } else if (L != 0u) {
         s.p = depth;
         s.L = L;

@@ -342,6 +342,15 @@ def test_paper_order8_total(dls, golden):
     wl = gpu_cases.split(dls, 8, D, 14)
     c = _gpu_counts(dls, 8, D, wl.order, wl.prefixes)
     assert int(c.sum(dtype=np.uint64)) == golden["dls8_row0_fixed"]
+    # dls_count_weighted: the same count times the row-0 multiplier 8!, and
+    # with every weight 2^32 - 1 a weighted total past 2^64, both in 128 bits
+    d_pre = torch.from_numpy(wl.prefixes).cuda()
+    total = dls.count_weighted(8, D, wl.order, d_pre, multiply=True)
+    assert total == golden["dls8_row0_fixed"] * 40320
+    # (int32 -1 is the 32-bit pattern 2^32 - 1; the library reads uint32)
+    w = torch.full((len(wl.prefixes),), -1, dtype=torch.int32, device="cuda")
+    big = dls.count_weighted(8, D, wl.order, d_pre, weights=w)
+    assert big == golden["dls8_row0_fixed"] * 0xFFFFFFFF and big >= 1 << 64
 
 
 @pytest.mark.slow
