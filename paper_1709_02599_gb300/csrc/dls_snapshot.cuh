@@ -306,8 +306,68 @@ __device__ __forceinline__ uint32_t bcands(uint32_t R0, uint32_t R1, uint32_t C0
   return all & ~(__byte_perm(R0, R1, sr) | __byte_perm(C0, C1, sc));
 }
 
-// One search iteration of the byte-word search; the same moves as snap_step
-// (see there), returns true when the lane's work is finished.
+// Shared-memory accesses under a predicate.  On the GPU they are single
+// predicated instructions (a C++ `if` around them would become a branch,
+// and the lanes of a warp would split); a lane whose predicate is off makes
+// no access and its registers keep their values.
+#ifdef __CUDA_ARCH__
+// (the base's shared-window address is loop-invariant and computed once)
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void st_shared_if(bool c, uint4 *base, int k, uint4 v) {
+  asm volatile(
+      "{\n .reg .pred q;\n setp.ne.u32 q, %0, 0;\n"
+      " @q st.shared.v4.u32 [%1], {%2, %3, %4, %5};\n}\n" ::"r"((uint32_t)c),
+      "r"(smem_addr(base) + (uint32_t)k * 16u), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+      : "memory");
+}
+__device__ __forceinline__ void st_shared_if(bool c, uint32_t *base, int k, uint32_t v) {
+  asm volatile(
+      "{\n .reg .pred q;\n setp.ne.u32 q, %0, 0;\n"
+      " @q st.shared.u32 [%1], %2;\n}\n" ::"r"((uint32_t)c),
+      "r"(smem_addr(base) + (uint32_t)k * 4u), "r"(v)
+      : "memory");
+}
+__device__ __forceinline__ void ld_shared_if(bool c, const uint4 *base, int k, uint4 &v) {
+  asm volatile(
+      "{\n .reg .pred q;\n setp.ne.u32 q, %4, 0;\n"
+      " @q ld.shared.v4.u32 {%0, %1, %2, %3}, [%5];\n}\n"
+      : "+r"(v.x), "+r"(v.y), "+r"(v.z), "+r"(v.w)
+      : "r"((uint32_t)c), "r"(smem_addr(base) + (uint32_t)k * 16u)
+      : "memory");
+}
+__device__ __forceinline__ void ld_shared_if(bool c, const uint32_t *base, int k, uint32_t &v) {
+  asm volatile(
+      "{\n .reg .pred q;\n setp.ne.u32 q, %1, 0;\n"
+      " @q ld.shared.u32 %0, [%2];\n}\n"
+      : "+r"(v)
+      : "r"((uint32_t)c), "r"(smem_addr(base) + (uint32_t)k * 4u)
+      : "memory");
+}
+#else
+inline void st_shared_if(bool c, uint4 *base, int k, uint4 v) {
+  if (c) base[k] = v;
+}
+inline void st_shared_if(bool c, uint32_t *base, int k, uint32_t v) {
+  if (c) base[k] = v;
+}
+inline void ld_shared_if(bool c, const uint4 *base, int k, uint4 &v) {
+  if (c) v = base[k];
+}
+inline void ld_shared_if(bool c, const uint32_t *base, int k, uint32_t &v) {
+  if (c) v = base[k];
+}
+#endif
+
+// One search iteration of the byte-word search: the moves of snap_step (see
+// there), with the stack and table traffic cut to what each lane needs.
+// Only a push writes its entry (the state before placing nv); only a move
+// back to an older cell reads one, loaded over the registers that hold the
+// state before the placement -- so a dead end with candidates left at p
+// resumes from those registers, and one select per register picks the new
+// state; only a move to another position reads a table row.  Returns true
+// when the lane's work is finished (then it stays on p with no candidate).
 template <bool NODES, bool DG, bool LA = false, bool FU = false>
 __device__ __forceinline__ bool bsnap_step(BLane &s, const Geo &g, const SnapStack &st,
                                            const BRow *tb, unsigned B, uint32_t &ovf) {
@@ -318,9 +378,10 @@ __device__ __forceinline__ bool bsnap_step(BLane &s, const Geo &g, const SnapSta
   const bool keep = Lr != 0u;
   const bool has = s.sp > s.bot;
   int q = s.p + 1;  // <= last: a lane never stands on the last cell
-  const uint32_t R0 = s.R0, R1 = s.R1, C0 = s.C0, C1 = s.C1, dg0 = s.dg;
-  uint32_t r0 = nv * s.a.x + R0, r1 = nv * s.a.y + R1;
-  uint32_t c0 = nv * s.a.z + C0, c1 = nv * s.a.w + C1;
+  const uint32_t dg0 = s.dg;
+  uint4 e = make_uint4(s.R0, s.R1, s.C0, s.C1);  // the state before placing nv
+  uint32_t r0 = nv * s.a.x + e.x, r1 = nv * s.a.y + e.y;
+  uint32_t c0 = nv * s.a.z + e.z, c1 = nv * s.a.w + e.w;
   uint32_t L1 = bcands(r0, r1, c0, c1, s.c.x, s.c.y, g.all);
   uint32_t dg = dg0;
   if (DG) {
@@ -348,32 +409,34 @@ __device__ __forceinline__ bool bsnap_step(BLane &s, const Geo &g, const SnapSta
   if (NODES) s.nodes += leaves;
   bool dead = leaf || L1 == 0u;
   if (LA) dead = dead || bcands(r0, r1, c0, c1, s.c.z, s.c.w, g.all) == 0u;
-  // the state before placing nv goes to the first free slot (a push keeps
-  // it); the entry a dead end resumes is read back (see snap_step)
-  st.sa[(s.sp + 1) * (int)B] = make_uint4(R0, R1, C0, C1);
-  st.sw[(s.sp + 1) * (int)B] = snap_pack<false>(DG ? dg0 : 0u, s.p, Lr);
-  const int rd = (keep || s.sp <= s.bot) ? s.sp + 1 : s.sp;
-  const uint4 ea = st.sa[rd * (int)B];
-  const uint32_t ew = st.sw[rd * (int)B];
   const bool push = keep && !dead;
   const bool pop = dead && !keep && has;
   ovf |= (push && s.sp >= st.cap) ? 1u : 0u;
+  uint32_t ew = snap_pack<false>(DG ? dg0 : 0u, s.p, Lr);
+  // entry e lives in slot e + 1; a full stack pushes into the spare slot
+  // cap + 1, which the index clamp below never makes live
+  st_shared_if(push, st.sa, (s.sp + 1) * (int)B, e);
+  st_shared_if(push, st.sw, (s.sp + 1) * (int)B, ew);
+  ld_shared_if(pop, st.sa, s.sp * (int)B, e);
+  ld_shared_if(pop, st.sw, s.sp * (int)B, ew);
   uint32_t edg, eL;
   int ep;
   snap_unpack<false>(ew, g.n, edg, ep, eL);
-  s.R0 = dead ? ea.x : r0;
-  s.R1 = dead ? ea.y : r1;
-  s.C0 = dead ? ea.z : c0;
-  s.C1 = dead ? ea.w : c1;
+  s.R0 = dead ? e.x : r0;
+  s.R1 = dead ? e.y : r1;
+  s.C0 = dead ? e.z : c0;
+  s.C1 = dead ? e.w : c1;
   if (DG) s.dg = dead ? edg : dg;
   s.L = dead ? eL : L1;
-  s.p = dead ? ep : q;
+  const int np = dead ? ep : q;
+  const bool moved = np != s.p;
+  s.p = np;
   s.sp = min(s.sp + (push ? 1 : 0) - (pop ? 1 : 0), st.cap);
   // table row of the new position, for the next iteration
-  const BRow &row = tb[s.p];
-  s.a = row.a;
-  s.b = row.b;
-  s.c = row.c;
+  const uint4 *rows = reinterpret_cast<const uint4 *>(tb);
+  ld_shared_if(moved, rows, 3 * s.p, s.a);
+  ld_shared_if(moved, rows, 3 * s.p + 1, s.b);
+  ld_shared_if(moved, rows, 3 * s.p + 2, s.c);
   return dead && !keep && !has;
 }
 
