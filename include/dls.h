@@ -257,6 +257,10 @@ typedef struct {
     int64_t budget;       /* stop early after this many search iterations per
                              lane (the lanes of a warp step together; 0 = no
                              limit) -- see "Stopping early" below          */
+    int stack_cap;        /* snapshot entries per lane: 0 = the bound that no
+                             search can exceed (default); a smaller value
+                             leaves more lanes resident -- see "Stack cap"
+                             below                                          */
     const volatile int *abort_flag; /* NULL, or a word the kernel polls (device
                              memory, or host memory the GPU can read, e.g.
                              pinned and mapped): once it reads nonzero, the
@@ -278,6 +282,20 @@ typedef struct {
  * total (d_total) is then partial.  No wait in the kernel depends on the
  * flag: a warp only reads it. */
 #define DLS_UNFINISHED (1ull << 63)
+
+/* Stack cap (dls_launch_t.stack_cap).  The snapshot search's stack has as
+ * many entries per lane as the order has positions after the prefix whose
+ * cell is not forced by a line -- a bound no search can exceed -- but real
+ * searches stay far below it (order 8, split 25 cells into the order: bound
+ * 25, deepest stack 19, and 0.15 % of the prefixes deeper than 16).  A
+ * smaller cap leaves more lanes resident.  A lane whose stack would outgrow
+ * the cap finishes its prefix at once and marks it; a second pass of the
+ * same kernel, with the full bound, then counts the marked prefixes again
+ * from zero (its idle lanes share their searches through donation), and the
+ * total is summed from the counts.  Counts stay exact; both passes are
+ * enqueued on the stream (and captured by plans).  The cap applies only with
+ * per-prefix counts (d_counts), without a node count, a budget or an abort
+ * flag; otherwise the bound is kept. */
 
 /* What a dls_count_ex call with this shape runs. */
 typedef enum {
@@ -305,7 +323,8 @@ typedef struct {
 } dls_launch_info;
 
 /* Resolves the kernel and launch shape that dls_count_ex would use for these
- * arguments (same validation and errors), without enqueueing anything.
+ * arguments, with per-prefix counts and no node count (same validation and
+ * errors), without enqueueing anything.
  * Queries the current CUDA device (occupancy).  out: HOST, caller-owned. */
 int dls_describe_launch(int n, uint32_t flags, const uint8_t *order,
                         int order_len, int depth, int64_t n_prefixes,

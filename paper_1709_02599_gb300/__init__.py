@@ -39,12 +39,13 @@ class Launch:
     fuse: int = 0
     budget: int = 0        # search iterations per lane before stopping (0 = none)
     abort_flag: int = 0    # address of an int the kernel polls (0 = none)
+    stack_cap: int = 0     # snapshot entries per lane (0 = the bound)
 
     def c(self):
         return _lib.LaunchT(self.kernel, self.block_threads, self.blocks_per_sm,
                             self.lanes_per_prefix, self.split_pos, self.donate,
                             self.check_every, self.words, self.stack, self.lookahead,
-                            self.fuse, self.budget, self.abort_flag or None)
+                            self.fuse, self.budget, self.stack_cap, self.abort_flag or None)
 
 
 def lib():

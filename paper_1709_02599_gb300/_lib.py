@@ -60,6 +60,7 @@ class LaunchT(ctypes.Structure):
                 ("lookahead", ctypes.c_int),
                 ("fuse", ctypes.c_int),
                 ("budget", ctypes.c_int64),
+                ("stack_cap", ctypes.c_int),
                 ("abort_flag", ctypes.c_void_p)]
 
 

@@ -54,6 +54,10 @@ namespace dls {
 constexpr unsigned ST_OVERFLOW = 1u;  // a snapshot stack would have overflowed
 constexpr unsigned ST_TIMEOUT = 2u;   // stopped early: iteration budget spent
 constexpr unsigned ST_ABORTED = 4u;   // stopped early: abort flag seen
+constexpr unsigned ST_DEFERRED = 8u;  // a capped stack deferred prefixes to the recount pass
+// Count mark of a prefix deferred by a capped stack (counted again, from 0,
+// by the recount pass; never left in a count returned to the caller).
+constexpr unsigned long long RECOUNT = 1ull << 62;
 // iterations between two reads of a count's abort flag (a read of mapped
 // host memory takes microseconds)
 constexpr long long POLL_EVERY = 4096;
@@ -80,6 +84,8 @@ struct KParams {
   int snap_cap;               // snapshot stack entries per lane
   long long budget;           // search iterations per lane before stopping (0: none)
   const volatile int *abort_flag;  // polled; nonzero stops the count (NULL: none)
+  int defer;                  // a stack overflow defers the prefix to the recount pass
+  int recount;                // the recount pass: only deferred prefixes are searched
   uint8_t ci[DLS_MAX_CELLS];
   uint8_t cj[DLS_MAX_CELLS];
 };
@@ -120,6 +126,7 @@ __device__ bool load_item(Lane<REG> &s, const KParams &p, long long item,
 __device__ __forceinline__ void flush_count(long long prefix, unsigned long long cnt,
                                             const KParams &p,
                                             unsigned long long &lane_total) {
+  if (prefix < 0) return;  // a prefix the recount pass skips
   lane_total += cnt;
   if (p.counts != nullptr) {
     if (p.count_store)
@@ -127,6 +134,39 @@ __device__ __forceinline__ void flush_count(long long prefix, unsigned long long
     else if (cnt)
       atomicAdd(p.counts + prefix, cnt);
   }
+}
+
+// A finished item of a snapshot search: counted, unless the lane's stack
+// overflowed during it -- then, with a capped stack, the prefix is marked for
+// the recount pass (which searches it again with the full bound); without a
+// cap (where the bound excludes an overflow) the count's status reports it.
+__device__ __forceinline__ void finish_snapshot_item(long long prefix, unsigned long long cnt,
+                                                     const KParams &p, uint32_t &ovf,
+                                                     unsigned long long &lane_total) {
+  if (!ovf) {
+    flush_count(prefix, cnt, p, lane_total);
+    return;
+  }
+  ovf = 0u;
+  if (p.defer && prefix >= 0) {
+    if (p.count_store)
+      p.counts[prefix] = RECOUNT;
+    else
+      atomicOr(p.counts + prefix, RECOUNT);
+    atomicOr(reinterpret_cast<unsigned *>(p.queue + 1), ST_DEFERRED);
+  } else {
+    atomicOr(reinterpret_cast<unsigned *>(p.queue + 1), ST_OVERFLOW);
+  }
+}
+
+// The recount pass takes only the prefixes the first pass deferred (and
+// clears their count); any other one is skipped (prefix -1: nothing is
+// stored for it).  Returns true for a skipped one.
+__device__ __forceinline__ bool recount_skip(const KParams &p, long long item) {
+  if (!p.recount) return false;
+  if ((p.counts[item] & RECOUNT) == 0ull) return true;
+  p.counts[item] = 0ull;
+  return false;
 }
 
 // Stopping early.  `spent` = search iterations the warp has made (the same
@@ -429,9 +469,10 @@ template <bool VSYM, bool NODES>
 __device__ bool snap_load(SnapLane &s, const KParams &p, long long item, const Cell *tbl,
                           const SnapTable &tb) {
   const Geo &g = p.g;
-  s.prefix = item;
   s.cnt = 0ull;
   s.sp = s.bot = 0;
+  s.prefix = recount_skip(p, item) ? -1 : item;
+  if (s.prefix < 0) return true;
   s.w.clear(0, 0u);
   if (!place_prefix<true, VSYM>(s.w, g, p.prefixes + (size_t)item * (size_t)g.depth, tbl))
     return true;
@@ -460,9 +501,10 @@ __device__ bool snap_load(BLane &s, const KParams &p, long long item, const Cell
                           const BRow *tb) {
   static_assert(!VSYM, "byte words: no vertical symmetry");
   const Geo &g = p.g;
-  s.prefix = item;
   s.cnt = 0ull;
   s.sp = s.bot = 0;
+  s.prefix = recount_skip(p, item) ? -1 : item;
+  if (s.prefix < 0) return true;
   Words<true> w;
   w.tb = nullptr;
   w.clear(0, 0u);
@@ -668,7 +710,7 @@ __global__ void __launch_bounds__(512)
   bool busy = false;
   if (item < p.n_items) {
     busy = !snap_load<VSYM, NODES>(s, p, item, tbl, tb);
-    if (!busy) flush_count(s.prefix, s.cnt, p, lane_total);
+    if (!busy) finish_snapshot_item(s.prefix, s.cnt, p, ovf, lane_total);
   }
   const bool stoppable = p.budget > 0 || p.abort_flag != nullptr;
   long long spent = 0, next_poll = 0;
@@ -677,7 +719,7 @@ __global__ void __launch_bounds__(512)
   while (__any_sync(FULL, busy)) {
     if (busy && K::template step<NODES, DG, false, FU>(s, p.g, st, tb, B, ovf)) {
       busy = false;
-      flush_count(s.prefix, s.cnt, p, lane_total);
+      finish_snapshot_item(s.prefix, s.cnt, p, ovf, lane_total);
     }
     if (stoppable && ++k > p.check_mask) {
       spent += k;
@@ -687,7 +729,6 @@ __global__ void __launch_bounds__(512)
     }
   }
   if (stopped) stop_warp(p, stopped, busy, s.prefix, s.cnt, false, threadIdx.x & 31);
-  if (ovf) raise_status(p.queue, ST_OVERFLOW);
   block_reduce_add(lane_total, p.total, red);
   if (NODES) block_reduce_add(s.nodes, p.nodes, red);
 }
@@ -725,7 +766,7 @@ __global__ void __launch_bounds__(512)
         const long long item = (long long)base + __popc(idle & ((1u << lane) - 1u));
         if (item < p.n_items) {
           busy = !snap_load<VSYM, NODES>(s, p, item, tbl, tb);
-          if (!busy) flush_count(s.prefix, s.cnt, p, lane_total);
+          if (!busy) finish_snapshot_item(s.prefix, s.cnt, p, ovf, lane_total);
         }
       }
       if ((long long)(base + (unsigned long long)nidle) >= p.n_items) qdone = true;
@@ -749,13 +790,13 @@ __global__ void __launch_bounds__(512)
       }
       if (fin) {
         busy = false;
-        flush_count(s.prefix, s.cnt, p, lane_total);
+        finish_snapshot_item(s.prefix, s.cnt, p, ovf, lane_total);
       }
     } else {
       for (int it = 0; it <= p.check_mask; ++it) {
         if (busy && K::template step<NODES, DG, LA, FU>(s, p.g, st, tb, B, ovf)) {
           busy = false;
-          flush_count(s.prefix, s.cnt, p, lane_total);
+          finish_snapshot_item(s.prefix, s.cnt, p, ovf, lane_total);
         }
       }
       spent += p.check_mask + 1;
@@ -763,7 +804,6 @@ __global__ void __launch_bounds__(512)
     }
   }
   if (stopped) stop_warp(p, stopped, busy, s.prefix, s.cnt, true, lane);
-  if (ovf) raise_status(p.queue, ST_OVERFLOW);
   block_reduce_add(lane_total, p.total, red);
   if (NODES) block_reduce_add(s.nodes, p.nodes, red);
 }
@@ -909,6 +949,7 @@ struct Shape {
   int lookahead;
   int fuse;   // -1 off, 0 where it applies, 1 on
   long long budget;
+  int stack_cap;
   const volatile int *abort_flag;
 };
 
@@ -951,6 +992,8 @@ static int resolve_shape(const dls_launch_t *cfg, int depth, int last,
   if (c.budget < 0) return DLS_ERR_BAD_ARG;
   sh->budget = c.budget;
   sh->abort_flag = c.abort_flag;
+  if (c.stack_cap < 0) return DLS_ERR_BAD_ARG;
+  sh->stack_cap = c.stack_cap;
   return DLS_OK;
 }
 
@@ -1089,6 +1132,15 @@ struct Prepared {
   size_t smem = 0;
   bool store = false;
   bool fused = false;  // snapshot search with the fused step
+  int bound = 0;       // snapshot entries no search can exceed
+  // a capped stack: the recount pass (same kernel, full bound, deferred
+  // prefixes only) and the total summed from the counts afterwards
+  bool recount = false;
+  KParams kp2;
+  int block2 = 0;
+  unsigned grid2 = 0;
+  size_t smem2 = 0;
+  uint64_t *total_out = nullptr;
 };
 
 // Validates the arguments and resolves the kernel and its launch shape
@@ -1147,6 +1199,18 @@ static int prepare_launch(int n, uint32_t flags, const uint8_t *order, int order
   if (sh.stack == 2 && !snap_ok) return DLS_ERR_BAD_ARG;
   bool snap = snap_ok && sh.stack != 1;
   kp.snap_cap = snap ? std::max(1, snapshot_entries(info, n, flags, depth)) : 0;
+  pr->bound = kp.snap_cap;
+  // a stack cap below the bound needs per-prefix counts to defer to (and no
+  // node count, budget or abort flag); otherwise the bound stays
+  const bool can_defer = d_counts != nullptr && d_nodes == nullptr && sh.budget == 0 &&
+                         sh.abort_flag == nullptr;
+  if (snap && sh.stack_cap > 0 && sh.stack_cap < kp.snap_cap && can_defer) {
+    kp.snap_cap = sh.stack_cap;
+    pr->recount = true;
+    kp.defer = 1;
+    pr->total_out = d_total;
+    kp.total = nullptr;  // summed from the counts after the recount pass
+  }
   DevInfo di;
   rc = dev_info(&di);
   if (rc) return rc;
@@ -1192,23 +1256,65 @@ static int prepare_launch(int n, uint32_t flags, const uint8_t *order, int order
   cudaError_t e = cudaFuncSetAttribute(pr->fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return cuda_fail(e);
-  if (sh.kernel == DLS_KERNEL_PLAIN) {
-    long long g = (kp.n_items + sh.block - 1) / sh.block;
-    if (g > 0x7fffffffll) return DLS_ERR_BAD_ARG;
-    pr->grid = (unsigned)g;
-  } else {
+  auto grid_for = [&](int block, size_t sm, unsigned *grid) -> int {
+    if (sh.kernel == DLS_KERNEL_PLAIN) {
+      long long g = (kp.n_items + block - 1) / block;
+      if (g > 0x7fffffffll) return DLS_ERR_BAD_ARG;
+      *grid = (unsigned)g;
+      return DLS_OK;
+    }
     int per_sm = sh.blocks_per_sm;
     if (per_sm == 0) {
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pr->fn, sh.block, smem);
-      if (e != cudaSuccess) return cuda_fail(e);
+      cudaError_t e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pr->fn, block, sm);
+      if (e2 != cudaSuccess) return cuda_fail(e2);
       if (per_sm < 1) return DLS_ERR_NO_MEMORY;
     }
     long long want = (long long)di.sms * per_sm;
     long long need = (kp.n_items + 31) / 32;  // warps with at least one item
-    long long blocks_needed = (need * 32 + sh.block - 1) / sh.block;
-    pr->grid = (unsigned)std::max(1ll, std::min(want, blocks_needed));
+    long long blocks_needed = (need * 32 + block - 1) / block;
+    *grid = (unsigned)std::max(1ll, std::min(want, blocks_needed));
+    return DLS_OK;
+  };
+  rc = grid_for(sh.block, smem, &pr->grid);
+  if (rc) return rc;
+  if (pr->recount) {
+    // the recount pass: the full bound, a smaller block where its stacks
+    // need it; it takes only the deferred prefixes
+    pr->kp2 = kp;
+    pr->kp2.snap_cap = pr->bound;
+    pr->kp2.defer = 0;
+    pr->kp2.recount = 1;
+    int b2 = sh.block;
+    size_t sm2 = smem_bytes_snapshot(order_len, pr->bound, b2, vsym);
+    while (sm2 + static_smem > di.smem_optin && b2 > 32) {
+      b2 /= 2;
+      sm2 = smem_bytes_snapshot(order_len, pr->bound, b2, vsym);
+    }
+    if (sm2 + static_smem > di.smem_optin) return DLS_ERR_NO_MEMORY;
+    if (sm2 > smem) {
+      e = cudaFuncSetAttribute(pr->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+      if (e != cudaSuccess) return cuda_fail(e);
+    }
+    pr->block2 = b2;
+    pr->smem2 = sm2;
+    const int saved = sh.blocks_per_sm;
+    sh.blocks_per_sm = 0;  // the occupancy of the recount pass's own shape
+    rc = grid_for(b2, sm2, &pr->grid2);
+    sh.blocks_per_sm = saved;
+    if (rc) return rc;
   }
   return DLS_OK;
+}
+
+// Sum of n counts into *total (64 bits; the total of one count call).
+__global__ void __launch_bounds__(256) k_sum_counts(const unsigned long long *counts,
+                                                    long long n, unsigned long long *total) {
+  __shared__ unsigned long long red[8];
+  unsigned long long v = 0ull;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x)
+    v += counts[k];
+  block_reduce_add(v, total, red);
 }
 
 // Validates, fills the parameter block and enqueues the whole pass on
@@ -1263,6 +1369,28 @@ static int enqueue_count(int n, uint32_t flags, const uint8_t *order,
   void *args[] = {&pr.kp, (void *)&pr.diag};
   e = cudaLaunchKernel(pr.fn, dim3(pr.grid), dim3(pr.block), args, pr.smem, stream);
   if (e != cudaSuccess) return cuda_fail(e);
+  if (pr.recount) {
+    // the recount pass over the deferred prefixes, from a fresh queue head
+    pr.kp2.queue = scratch;
+    e = cudaMemsetAsync(scratch, 0, sizeof(unsigned long long), stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    void *args2[] = {&pr.kp2, (void *)&pr.diag};
+    e = cudaLaunchKernel(pr.fn, dim3(pr.grid2), dim3(pr.block2), args2, pr.smem2, stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (pr.total_out) {
+      DevInfo di;
+      rc = dev_info(&di);
+      if (rc) return rc;
+      const long long np = (long long)n_prefixes;
+      const unsigned gs = (unsigned)std::max(1ll, std::min<long long>((np + 255) / 256,
+                                                                      4ll * di.sms));
+      unsigned long long *tot = reinterpret_cast<unsigned long long *>(pr.total_out);
+      const unsigned long long *cnt = reinterpret_cast<const unsigned long long *>(d_counts);
+      k_sum_counts<<<gs, 256, 0, stream>>>(cnt, np, tot);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return cuda_fail(e);
+    }
+  }
   return DLS_OK;
 }
 
@@ -1330,8 +1458,11 @@ int dls_describe_launch(int n, uint32_t flags, const uint8_t *order, int order_l
                         int depth, int64_t n_prefixes, const dls_launch_t *cfg,
                         dls_launch_info *out) {
   if (out == nullptr) return DLS_ERR_BAD_ARG;
+  // as a count with per-prefix counts and no node count would launch (the
+  // pointer only enables the stack cap; nothing is launched)
+  static uint64_t no_counts;
   Prepared pr;
-  int rc = prepare_launch(n, flags, order, order_len, nullptr, depth, n_prefixes, nullptr,
+  int rc = prepare_launch(n, flags, order, order_len, nullptr, depth, n_prefixes, &no_counts,
                           nullptr, nullptr, cfg, &pr);
   if (rc) return rc;
   out->run = pr.run;

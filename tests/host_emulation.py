@@ -27,7 +27,8 @@ CSRC = os.path.join(ROOT, "paper_1709_02599_gb300", "csrc")
 HK = os.path.join(HERE, "host_kernels")
 SOURCES = ["dls_kernels.cu", "dls_serve.cu", "dls_symmetry.cu", "dls_noalloc.cu"]
 FIELDS = ["kernel", "block_threads", "blocks_per_sm", "lanes_per_prefix", "split_pos",
-          "donate", "check_every", "words", "stack", "lookahead", "fuse", "budget", "abort"]
+          "donate", "check_every", "words", "stack", "lookahead", "fuse", "budget", "abort",
+          "stack_cap"]
 
 _SHARED = re.compile(r"__shared__\s+([A-Za-z_][\w ]*?)\s+(\w+)\[(\d+)\];")
 _LAUNCH = re.compile(r"(\w+)<<<([^;]*?)>>>\(([^;]*)\);")

@@ -4,7 +4,7 @@
 //
 //   kernel_check ENTRY n flags order.bin prefixes.bin depth
 //                kernel block blocks_per_sm lanes split_pos donate check_every
-//                words stack lookahead fuse budget abort
+//                words stack lookahead fuse budget abort stack_cap
 //   kernel_check classes n flags order.bin hourglasses.bin len
 //   kernel_check serve jobs.txt mode max_jobs arena_bytes chunk_bytes budget
 //                block_threads items_per_job max_order
@@ -195,10 +195,10 @@ int run_serve(int argc, char **argv) {
 int main(int argc, char **argv) {
   if (argc >= 2 && std::string(argv[1]) == "classes") return run_classes(argc, argv);
   if (argc >= 2 && std::string(argv[1]) == "serve") return run_serve(argc, argv);
-  if (argc != 20) {
+  if (argc != 21) {
     std::fprintf(stderr, "usage: kernel_check ENTRY n flags order.bin prefixes.bin depth "
                          "kernel block blocks_per_sm lanes split_pos donate check_every "
-                         "words stack lookahead fuse budget abort\n");
+                         "words stack lookahead fuse budget abort stack_cap\n");
     return 1;
   }
   const std::string entry = argv[1];
@@ -225,6 +225,7 @@ int main(int argc, char **argv) {
   const int abort_mode = std::atoi(argv[19]);
   abort_word = abort_mode == 1 ? 1 : 0;
   cfg.abort_flag = abort_mode ? &abort_word : nullptr;
+  cfg.stack_cap = std::atoi(argv[20]);
   const int len = (int)order.size() / 2;
   const int64_t P = depth ? (int64_t)pre.size() / depth : 1;
   if (pre.empty()) pre.push_back(0);  // a valid pointer for depth 0

@@ -539,3 +539,45 @@ def test_budget_and_abort_flag_on_the_gpu(dls):
         assert status == expect
         if expect == 0:
             assert started == P and (c.cpu().numpy() == ref).all()
+
+
+@pytest.mark.parametrize("depth", [25, 28])
+def test_stack_cap_on_the_benchmark_workload(dls, depth):
+    """The order-8 workload with the snapshot stack capped below its bound
+    (entries 16 and 12, against 25 and 23): the lanes that would outgrow the
+    cap defer their prefix, the recount pass counts those again, and the
+    counts of 4 seed-chosen diagonals are the oracle's; every count and the
+    total equal those of the uncapped launch, through plans too."""
+    import dls_inputs
+    from paper_1709_02599_gb300 import autotune
+    n = 8
+    order0 = dls.fill_order(n, D)
+    ident = np.arange(n, dtype=np.uint8)[None]
+    diags, _ = dls.extend_prefixes(n, D, order0, ident, n + (n - 1))
+    picks = dls_inputs.choose(len(diags), 64, 0)
+    order, pre, par = autotune.build_problem(n, D, order0, diags[picks], depth, "heuristic_sq")
+    o_order = orders.heuristic_complete(n, orders.md_ad_rows(n)[:depth], squares=True)
+    o_diags, _ = oracle.extend(n, D, orders.md_ad_rows(n), np.array([orders.identity(n)],
+                                                                        np.uint8), n + (n - 1))
+    o_pre, o_par = oracle.extend(n, D, o_order, o_diags[picks], depth)
+    assert (o_pre == pre).all()
+    sel = np.isin(par, dls_inputs.choose(64, 4, seed=3))
+    ref, _ = oracle.count_many(n, D, o_order, o_pre[sel], threads=THREADS)
+    d_pre = torch.from_numpy(pre).cuda()
+    full = _gpu_counts(dls, n, D, order, pre)
+    for cap in (16, 12):
+        for launch in (dls.Launch(stack_cap=cap), dls.Launch(stack_cap=cap, block_threads=64),
+                       dls.Launch(kernel=dls.KERNEL_PLAIN, stack_cap=cap)):
+            assert dls.describe_launch(n, D, order, depth, len(pre), launch)["stack_entries"] == cap
+            c = _gpu_counts(dls, n, D, order, pre, launch)
+            assert (c == full).all(), launch
+            assert (c[sel] == ref).all()
+            counts = torch.empty(len(pre), dtype=torch.uint64, device="cuda")
+            total = torch.empty(1, dtype=torch.uint64, device="cuda")
+            plan = dls.Plan(n, D, order, d_pre, counts, total, launch)
+            plan.launch()
+            plan.launch()
+            assert plan.status() == (0, len(pre))
+            assert (counts.cpu().numpy() == full).all()
+            assert int(total.cpu().numpy()[0]) == int(full.sum())
+            plan.close()

@@ -218,6 +218,33 @@ def test_weighted_total(dls, emulated):
             assert emulated.last_total128 == expect, (n, sh)
 
 
+@pytest.mark.parametrize("n,after,step", [(7, 14, 7), (6, 5, 1)])
+def test_stack_cap_defers_and_recounts(dls, emulated, n, after, step):
+    """A stack cap far below the bound: lanes that would outgrow it defer
+    their prefix, the recount pass counts those again with the full bound,
+    and every count and the total are the oracle's (plans, both host-buffer
+    entries, the weighted total; the batched and the plain snapshot
+    kernels).  describe reports the cap."""
+    wl = every(gpu_cases.split(dls, n, D, after), step)
+    ref, _ = oracle.count_many(n, D, wl.oracle_order, wl.oracle_prefixes)
+    P = len(ref)
+    for sh in (dict(stack_cap=2), dict(stack_cap=1, block_threads=32),
+               dict(kernel=1, stack_cap=2)):
+        rc, info = emulated.count("describe", n, D, wl.order, wl.prefixes, **sh)
+        assert rc == 0 and info["stack_entries"] == sh["stack_cap"], sh
+        rc, res = emulated.count("plan", n, D, wl.order, wl.prefixes, **sh)
+        assert rc == 0 and emulated.last_status == (0, P), sh
+        assert (res[0] == ref).all() and res[1] == int(ref.sum()), sh
+        for entry in ("host", "noalloc"):
+            rc, res = emulated.count(entry, n, D, wl.order, wl.prefixes, **sh)
+            assert rc == 0 and (res[0] == ref).all(), (entry, sh)
+        rc, res = emulated.count("weighted", n, D, wl.order, wl.prefixes, **sh)
+        w = np.arange(P) % 5 + 1
+        assert rc == 0 and (res[0] == ref).all()
+        assert emulated.last_total128 == sum(int(c) * int(x) for c, x in zip(ref, w)) * \
+            oracle.multiplier(n, D)
+
+
 def test_abort_flag(dls, emulated):
     """A set abort flag stops the count before any prefix is finished
     (DLS_ERR_ABORTED); a flag that stays clear changes nothing."""
