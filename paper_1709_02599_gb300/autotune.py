@@ -1,5 +1,6 @@
 """Autotuner for the batched count: split depth, fill order after the prefix,
-lanes per prefix, placement of the row/column words and block size.
+lanes per prefix, placement of the row/column words, block size and the
+snapshot stack's cap.
 
 Every trial counts the same squares: the base prefixes are extended to the
 candidate split depth with the same leading cells, and only the cells after
@@ -28,6 +29,9 @@ SHAPES = [
     {},
     {"block_threads": 64},
     {"block_threads": 256},
+    {"stack_cap": 17, "block_threads": 64},
+    {"stack_cap": 15, "block_threads": 64},
+    {"stack_cap": 17},
     {"fuse": -1},
     {"fuse": -1, "block_threads": 64},
     {"lookahead": 1},
