@@ -220,9 +220,11 @@ typedef struct {
                              abort flag (power of two, default 64)           */
     int words;            /* where a lane keeps its row and column words:
                              0 = registers when they fit (n <= 8, or even
-                             n <= 10 with DLS_VSYM), else shared memory;
-                             1 = shared memory; 2 = registers (BAD_ARG if
-                             they do not fit)                                */
+                             n <= 10 with DLS_VSYM, or the snapshot search's
+                             wide words for n = 9 with at most 8 rows after
+                             the prefix), else shared memory; 1 = shared
+                             memory; 2 = registers (BAD_ARG if they do not
+                             fit)                                            */
     int stack;            /* the search's stack --
                              1 = one entry per order position (Algorithm 4's
                              L and LS per cell; backing out of a cell is one
@@ -319,7 +321,9 @@ typedef struct {
     int step;             /* the search step: 0 = one entry per position,
                              1 = snapshots with field shifts (vertical
                              symmetry), 2 = snapshots with byte words (n <= 8
-                             without vertical symmetry)                      */
+                             without vertical symmetry), 3 = snapshots with
+                             wide words (n = 9: values 0-7 in byte slots,
+                             value 8 a bit per line)                         */
 } dls_launch_info;
 
 /* Resolves the kernel and launch shape that dls_count_ex would use for these

@@ -25,7 +25,8 @@ RUN_SNAPSHOT = 2
 RUN_PLAIN_SNAPSHOT = 3
 RUN_NAMES = {RUN_PERSISTENT: "k_persistent", RUN_PLAIN: "k_plain", RUN_SNAPSHOT: "k_snapshot",
              RUN_PLAIN_SNAPSHOT: "k_plain_snap"}
-STEP_NAMES = {0: "per-position", 1: "snapshot, field shifts", 2: "snapshot, byte words"}
+STEP_NAMES = {0: "per-position", 1: "snapshot, field shifts", 2: "snapshot, byte words",
+              3: "snapshot, wide words"}
 
 OK = 0
 ERR_CAPACITY = 4

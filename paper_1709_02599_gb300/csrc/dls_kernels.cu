@@ -86,6 +86,9 @@ struct KParams {
   const volatile int *abort_flag;  // polled; nonzero stops the count (NULL: none)
   int defer;                  // a stack overflow defers the prefix to the recount pass
   int recount;                // the recount pass: only deferred prefixes are searched
+  int diag_words;             // DLS_DIAGONAL (the wide load checks the diagonals)
+  int8_t rslot[DLS_MAX_N];    // wide words: byte slot of each row / column (-1: none)
+  int8_t cslot[DLS_MAX_N];
   uint8_t ci[DLS_MAX_CELLS];
   uint8_t cj[DLS_MAX_CELLS];
 };
@@ -535,6 +538,78 @@ __device__ bool snap_load(BLane &s, const KParams &p, long long item, const Cell
   return L == 0u;
 }
 
+// The same for a wide-word lane (order 9): the prefix is checked and placed
+// with plain line masks, which are then written into the row and column
+// slots and the value-8 word.
+template <bool VSYM, bool NODES>
+__device__ bool snap_load(WLane &s, const KParams &p, long long item, const Cell *,
+                          const WRow *tb) {
+  static_assert(!VSYM, "wide words: no vertical symmetry");
+  const Geo &g = p.g;
+  const int n = g.n;
+  s.cnt = 0ull;
+  s.sp = s.bot = 0;
+  s.prefix = recount_skip(p, item) ? -1 : item;
+  if (s.prefix < 0) return true;
+  uint32_t rows[DLS_MAX_N], cols[DLS_MAX_N];
+  for (int k = 0; k < n; ++k) rows[k] = cols[k] = 0u;
+  uint32_t md = 0u, ad = 0u;
+  const uint8_t *rec = p.prefixes + (size_t)item * (size_t)g.depth;
+  bool ok = true;
+  for (int t = 0; t < g.depth && ok; ++t) {
+    const int i = p.ci[t], j = p.cj[t];
+    const uint32_t v = rec[t];
+    const uint32_t b = v < (uint32_t)n ? (1u << v) : 0u;
+    const bool on_md = p.diag_words && i == j, on_ad = p.diag_words && i + j == n - 1;
+    const uint32_t used = rows[i] | cols[j] | (on_md ? md : 0u) | (on_ad ? ad : 0u);
+    ok = b != 0u && (used & b) == 0u;
+    rows[i] |= b;
+    cols[j] |= b;
+    md |= on_md ? b : 0u;
+    ad |= on_ad ? b : 0u;
+  }
+  uint32_t R0 = 0u, R1 = 0u, C0 = 0u, C1 = 0u, C2 = 0u, V8 = 0u;
+  for (int k = 0; k < n; ++k) {
+    const int rs = p.rslot[k], cs = p.cslot[k];
+    const uint32_t rb = rows[k] & 0xffu, cb = cols[k] & 0xffu;
+    if (rs >= 0) {
+      R0 |= rb * byte_mult(rs, 0);
+      R1 |= rb * byte_mult(rs, 1);
+    }
+    if (cs >= 0) {
+      C0 |= cb * wide_col_mult(cs, 0);
+      C1 |= cb * wide_col_mult(cs, 1);
+      C2 |= cb * wide_col_mult(cs, 2);
+    }
+    V8 |= ((rows[k] >> 8) & 1u) << k;
+    V8 |= ((cols[k] >> 8) & 1u) << (16 + k);
+  }
+  s.R0 = R0;
+  s.R1 = R1;
+  s.C0 = C0;
+  s.C1 = C1;
+  s.C2 = C2;
+  s.V8 = V8;
+  s.dg = md | (ad << 16);
+  if (!ok) return true;
+  if (g.depth == p.order_len) {
+    s.cnt = 1ull;
+    return true;
+  }
+  const int i = p.ci[g.depth], j = p.cj[g.depth];
+  const bool on_md = p.diag_words && i == j, on_ad = p.diag_words && i + j == n - 1;
+  const uint32_t L = g.all & ~(rows[i] | cols[j] | (on_md ? md : 0u) | (on_ad ? ad : 0u));
+  if (g.depth == g.last) {
+    s.cnt = (unsigned)__popc(L);
+    if (NODES) s.nodes += (unsigned)__popc(L);
+    return true;
+  }
+  s.p = g.depth;
+  s.L = L;
+  s.r = tb[g.depth];
+  return L == 0u;
+}
+
 // In-warp work donation for snapshot lanes: each idle lane is paired with a
 // busy lane that holds a stack entry; it takes the busy lane's bottom entry
 // (the shallowest open cell: the largest untried subtree) and the busy lane
@@ -569,6 +644,35 @@ __device__ __forceinline__ void snap_take(BLane &s, const KParams &p, uint4 a, u
   s.c = row.c;
 }
 
+// A wide-word entry: R0, R1, C0, C1 in sa, then (C2, V8, diagonal words,
+// position | untried candidates << 16) in the stack's second array.
+template <bool VSYM, bool DG>
+__device__ __forceinline__ void snap_take(WLane &s, const KParams &, uint4 a, uint4 b,
+                                          const WRow *tb) {
+  s.R0 = a.x;
+  s.R1 = a.y;
+  s.C0 = a.z;
+  s.C1 = a.w;
+  s.C2 = b.x;
+  s.V8 = b.y;
+  if (DG) s.dg = b.z;
+  s.p = (int)(b.w & 0xffffu);
+  s.L = b.w >> 16;
+  s.r = tb[s.p];
+}
+
+// The second word of entry `off` (a 32-bit packed word, or 16 bytes for
+// wide words).
+__device__ __forceinline__ uint32_t entry_word(const SnapLane &, const SnapStack &st, int off) {
+  return st.sw[off];
+}
+__device__ __forceinline__ uint32_t entry_word(const BLane &, const SnapStack &st, int off) {
+  return st.sw[off];
+}
+__device__ __forceinline__ uint4 entry_word(const WLane &, const SnapStack &st, int off) {
+  return reinterpret_cast<const uint4 *>(st.sw)[off];
+}
+
 template <bool VSYM, bool DG, class LaneT, class TableT>
 __device__ void snap_donate(LaneT &s, bool &busy, const KParams &p, const SnapStack &st,
                             const TableT &tb, int lane, unsigned B) {
@@ -593,7 +697,7 @@ __device__ void snap_donate(LaneT &s, bool &busy, const KParams &p, const SnapSt
   const long long d_prefix = __shfl_sync(FULL, s.prefix, partner);
   if (receiver) {
     const int off = (d_bot + 1) * (int)B + (partner - lane);
-    snap_take<VSYM, DG>(s, p, st.sa[off], st.sw[off], tb);
+    snap_take<VSYM, DG>(s, p, st.sa[off], entry_word(s, st, off), tb);
     s.sp = s.bot = 0;
     s.prefix = d_prefix;
     s.cnt = 0ull;
@@ -603,13 +707,29 @@ __device__ void snap_donate(LaneT &s, bool &busy, const KParams &p, const SnapSt
   if (giver) s.bot++;
 }
 
-// The two snapshot searches: register words with field shifts (vertically
-// symmetric orders; SnapLane, snap_step) and byte words (all other orders
-// n <= 8; BLane, bsnap_step).
-template <bool VSYM>
+// The three snapshot searches: byte words (orders n <= 8 without vertical
+// symmetry; BLane, bsnap_step), register words with field shifts (vertically
+// symmetric orders; SnapLane, snap_step) and wide words (order 9; WLane,
+// wsnap_step).  W2 = 4-byte words in the second part of an entry.
+constexpr int KIND_BYTE = 0, KIND_SHIFT = 1, KIND_WIDE = 2;
+
+template <int KIND>
 struct SnapKind {
+  using Lane = BLane;
+  using Table = const BRow *;
+  static constexpr int W2 = 1;
+  template <bool NODES, bool DG, bool LA, bool FU>
+  static __device__ __forceinline__ bool step(Lane &s, const Geo &g, const SnapStack &st,
+                                              const Table &tb, unsigned B, uint32_t &ovf) {
+    return bsnap_step<NODES, DG, LA, FU>(s, g, st, tb, B, ovf);
+  }
+};
+
+template <>
+struct SnapKind<KIND_SHIFT> {
   using Lane = SnapLane;
   using Table = SnapTable;
+  static constexpr int W2 = 1;
   template <bool NODES, bool DG, bool LA, bool FU>
   static __device__ __forceinline__ bool step(Lane &s, const Geo &g, const SnapStack &st,
                                               const Table &tb, unsigned B, uint32_t &ovf) {
@@ -618,14 +738,20 @@ struct SnapKind {
 };
 
 template <>
-struct SnapKind<false> {
-  using Lane = BLane;
-  using Table = const BRow *;
+struct SnapKind<KIND_WIDE> {
+  using Lane = WLane;
+  using Table = const WRow *;
+  static constexpr int W2 = 4;
   template <bool NODES, bool DG, bool LA, bool FU>
   static __device__ __forceinline__ bool step(Lane &s, const Geo &g, const SnapStack &st,
                                               const Table &tb, unsigned B, uint32_t &ovf) {
-    return bsnap_step<NODES, DG, LA, FU>(s, g, st, tb, B, ovf);
+    return wsnap_step<NODES, DG, LA, FU>(s, g, st, tb, B, ovf);
   }
+};
+
+template <bool VSYM, bool WIDE>
+struct SnapKindOf {
+  static constexpr int value = VSYM ? KIND_SHIFT : (WIDE ? KIND_WIDE : KIND_BYTE);
 };
 
 // Position tables in shared memory; returns where the stacks start.
@@ -674,16 +800,37 @@ __device__ __forceinline__ uint4 *snap_tables(const KParams &p, int diag, bool d
   return reinterpret_cast<uint4 *>(rw + rows);
 }
 
+__device__ __forceinline__ uint4 *snap_tables(const KParams &p, int diag, bool dgw,
+                                              uint32_t *smem, const Cell *&tbl,
+                                              const WRow *&tb, bool) {
+  const unsigned B = blockDim.x;
+  const int rows = (p.order_len + 31) & ~31;
+  Cell *t = reinterpret_cast<Cell *>(smem);
+  WRow *rw = reinterpret_cast<WRow *>(smem + 2 * rows);
+  int rs[DLS_MAX_N], cs[DLS_MAX_N];
+  for (int k = 0; k < DLS_MAX_N; ++k) {
+    rs[k] = p.rslot[k];
+    cs[k] = p.cslot[k];
+  }
+  for (int idx = threadIdx.x; idx < p.order_len; idx += B) {
+    t[idx] = describe_regs(p.ci[idx], p.cj[idx], p.g.n, diag != 0, 8, 8);
+    rw[idx] = wrow_make(p.g.n, diag != 0, dgw, p.ci, p.cj, idx, p.order_len, rs, cs);
+  }
+  tbl = t;
+  tb = rw;
+  return reinterpret_cast<uint4 *>(rw + rows);
+}
+
 // Shared memory: the position tables (snap_tables), then the stacks:
-// (cap + 2) * B entries of 16 bytes, then as many of 4.
-template <class LaneT, class TableT>
+// (cap + 2) * B entries of 16 bytes, then as many of 4 * W2.
+template <int W2, class LaneT, class TableT>
 __device__ __forceinline__ void snap_setup(const KParams &p, int diag, bool dgw,
                                            uint32_t *smem, const Cell *&tbl, TableT &tb,
                                            SnapStack &st, LaneT &s, bool two_on) {
   const unsigned B = blockDim.x;
   uint4 *sa0 = snap_tables(p, diag, dgw, smem, tbl, tb, two_on);
   st.sa = sa0 + threadIdx.x;
-  st.sw = reinterpret_cast<uint32_t *>(sa0 + (size_t)(p.snap_cap + 2) * B) + threadIdx.x;
+  st.sw = reinterpret_cast<uint32_t *>(sa0 + (size_t)(p.snap_cap + 2) * B) + threadIdx.x * W2;
   st.cap = p.snap_cap;
   s = LaneT{};
   __syncthreads();
@@ -692,18 +839,18 @@ __device__ __forceinline__ void snap_setup(const KParams &p, int diag, bool dgw,
 // The plain launch with the snapshot search: one thread per prefix, no
 // queue, no donation (the baseline the batched kernel is measured against,
 // with the same search step).
-template <bool VSYM, bool NODES, bool DG, bool FU>
+template <bool VSYM, bool NODES, bool DG, bool FU, bool WIDE = false>
 __global__ void __launch_bounds__(512)
     k_plain_snap(const __grid_constant__ KParams p, int diag) {
   extern __shared__ uint32_t smem[];
   __shared__ unsigned long long red[16];
   const unsigned B = blockDim.x;
-  using K = SnapKind<VSYM>;
+  using K = SnapKind<SnapKindOf<VSYM, WIDE>::value>;
   const Cell *tbl;
   typename K::Table tb;
   SnapStack st;
   typename K::Lane s;
-  snap_setup(p, diag, DG, smem, tbl, tb, st, s, FU);
+  snap_setup<K::W2>(p, diag, DG, smem, tbl, tb, st, s, FU);
   uint32_t ovf = 0u;
   unsigned long long lane_total = 0ull;
   const long long item = (long long)blockIdx.x * B + threadIdx.x;
@@ -733,19 +880,19 @@ __global__ void __launch_bounds__(512)
   if (NODES) block_reduce_add(s.nodes, p.nodes, red);
 }
 
-template <bool VSYM, bool NODES, bool DG, bool LA, bool FU>
+template <bool VSYM, bool NODES, bool DG, bool LA, bool FU, bool WIDE = false>
 __global__ void __launch_bounds__(512)
     k_snapshot(const __grid_constant__ KParams p, int diag) {
   extern __shared__ uint32_t smem[];
   __shared__ unsigned long long red[16];
   const unsigned B = blockDim.x;
   const int lane = threadIdx.x & 31;
-  using K = SnapKind<VSYM>;
+  using K = SnapKind<SnapKindOf<VSYM, WIDE>::value>;
   const Cell *tbl;
   typename K::Table tb;
   SnapStack st;
   typename K::Lane s;
-  snap_setup(p, diag, DG, smem, tbl, tb, st, s, LA || FU);
+  snap_setup<K::W2>(p, diag, DG, smem, tbl, tb, st, s, LA || FU);
   uint32_t ovf = 0u;
 
   unsigned long long lane_total = 0ull;
@@ -1053,31 +1200,42 @@ static const void *pick_kernel(int kind, bool reg, bool vsym, bool nodes, bool s
   return reg ? pick2<true>(kind, vsym, nodes, split) : pick2<false>(kind, vsym, nodes, split);
 }
 
-template <bool VSYM, bool NODES, bool DG>
+template <bool VSYM, bool NODES, bool DG, bool WIDE>
 static const void *snapshot_ptr(bool plain) {
-  return plain ? (const void *)k_plain_snap<VSYM, NODES, DG, false>
-               : (const void *)k_snapshot<VSYM, NODES, DG, false, false>;
+  return plain ? (const void *)k_plain_snap<VSYM, NODES, DG, false, WIDE>
+               : (const void *)k_snapshot<VSYM, NODES, DG, false, false, WIDE>;
 }
 
-template <bool VSYM>
+template <bool VSYM, bool WIDE>
 static const void *pick_snapshot2(bool plain, bool nodes, bool dg) {
-  if (dg) return nodes ? snapshot_ptr<VSYM, true, true>(plain)
-                       : snapshot_ptr<VSYM, false, true>(plain);
-  return nodes ? snapshot_ptr<VSYM, true, false>(plain) : snapshot_ptr<VSYM, false, false>(plain);
+  if (dg) return nodes ? snapshot_ptr<VSYM, true, true, WIDE>(plain)
+                       : snapshot_ptr<VSYM, false, true, WIDE>(plain);
+  return nodes ? snapshot_ptr<VSYM, true, false, WIDE>(plain)
+               : snapshot_ptr<VSYM, false, false, WIDE>(plain);
+}
+
+// the fused step or the lookahead (no diagonal words, no vertical symmetry)
+template <bool WIDE>
+static const void *pick_snapshot_fl(bool plain, bool nodes, bool la) {
+  if (!la && plain) return nodes ? (const void *)k_plain_snap<false, true, false, true, WIDE>
+                                 : (const void *)k_plain_snap<false, false, false, true, WIDE>;
+  if (!la) return nodes ? (const void *)k_snapshot<false, true, false, false, true, WIDE>
+                        : (const void *)k_snapshot<false, false, false, false, true, WIDE>;
+  return nodes ? (const void *)k_snapshot<false, true, false, true, false, WIDE>
+               : (const void *)k_snapshot<false, false, false, true, false, WIDE>;
 }
 
 // dg: some cell at or after the prefix depth lies on a diagonal (the
 // diagonal words change during the search); la: the persistent kernel with
 // the lookahead; fu: the fused step (both: no diagonal words, no vertical
-// symmetry only)
-static const void *pick_snapshot(bool plain, bool vsym, bool nodes, bool dg, bool la, bool fu) {
-  if (fu && plain) return nodes ? (const void *)k_plain_snap<false, true, false, true>
-                                : (const void *)k_plain_snap<false, false, false, true>;
-  if (fu) return nodes ? (const void *)k_snapshot<false, true, false, false, true>
-                       : (const void *)k_snapshot<false, false, false, false, true>;
-  if (la) return nodes ? (const void *)k_snapshot<false, true, false, true, false>
-                       : (const void *)k_snapshot<false, false, false, true, false>;
-  return vsym ? pick_snapshot2<true>(plain, nodes, dg) : pick_snapshot2<false>(plain, nodes, dg);
+// symmetry only); wide: the wide-word search of order 9
+static const void *pick_snapshot(bool plain, bool vsym, bool wide, bool nodes, bool dg, bool la,
+                                 bool fu) {
+  if (fu || la) return wide ? pick_snapshot_fl<true>(plain, nodes, la)
+                            : pick_snapshot_fl<false>(plain, nodes, la);
+  if (vsym) return pick_snapshot2<true, false>(plain, nodes, dg);
+  return wide ? pick_snapshot2<false, true>(plain, nodes, dg)
+              : pick_snapshot2<false, false>(plain, nodes, dg);
 }
 
 static bool diagonal_cells_after(const OrderInfo &info, int n, uint32_t flags, int depth) {
@@ -1110,11 +1268,14 @@ static size_t smem_bytes(int order_len, int n, int depth, int last, int block,
 }
 
 // Snapshot kernels: the cell table and the position table (8 + 24 bytes per
-// position with vertical symmetry, 8 + 48 with byte words), then 20 bytes per
-// entry slot and lane (cap + 2 slots).
-static size_t smem_bytes_snapshot(int order_len, int entries, int block, bool vsym) {
-  return (size_t)((order_len + 31) & ~31) * (vsym ? 32u : 56u) +
-         (size_t)(entries + 2) * block * 20u;
+// position with vertical symmetry, 8 + 48 with byte words, 8 + 80 with wide
+// words), then 20 bytes (32 with wide words) per entry slot and lane (cap + 2
+// slots).
+static size_t smem_bytes_snapshot(int order_len, int entries, int block, bool vsym,
+                                  bool wide = false) {
+  const size_t row = vsym ? 32u : (wide ? 88u : 56u);
+  return (size_t)((order_len + 31) & ~31) * row +
+         (size_t)(entries + 2) * block * (wide ? 32u : 20u);
 }
 
 // A resolved launch: the parameter block, the kernel and its shape.
@@ -1132,6 +1293,7 @@ struct Prepared {
   size_t smem = 0;
   bool store = false;
   bool fused = false;  // snapshot search with the fused step
+  bool wide = false;   // the wide-word search (order 9)
   int bound = 0;       // snapshot entries no search can exceed
   // a capped stack: the recount pass (same kernel, full bound, deferred
   // prefixes only) and the total summed from the counts afterwards
@@ -1190,12 +1352,22 @@ static int prepare_launch(int n, uint32_t flags, const uint8_t *order, int order
   int wr = 0, wc = 0;
   bool reg = words_fit_registers(n, vsym, &wr, &wc);
   if (sh.words == 1) reg = false;
-  if (sh.words == 2 && !reg) return DLS_ERR_BAD_ARG;
   kp.wr = wr;
   kp.wc = wc;
   // the snapshot search: register words, one lane per prefix; order
-  // positions must fit its packed entry
-  const bool snap_ok = reg && sh.lanes_log2 == 0 && order_len <= (vsym ? 64 : 256);
+  // positions must fit its packed entry.  Order 9 without vertical symmetry
+  // takes the wide words when at most 8 rows have cells after the prefix.
+  int rs9[DLS_MAX_N], cs9[DLS_MAX_N];
+  const bool wide = !vsym && n == 9 && sh.lanes_log2 == 0 && sh.words != 1 &&
+                    wide_slots(n, info.i, info.j, order_len, depth, rs9, cs9);
+  if (wide) {
+    for (int k = 0; k < DLS_MAX_N; ++k) {
+      kp.rslot[k] = (int8_t)(k < n ? rs9[k] : -1);
+      kp.cslot[k] = (int8_t)(k < n ? cs9[k] : -1);
+    }
+  }
+  kp.diag_words = (flags & DLS_DIAGONAL) ? 1 : 0;
+  const bool snap_ok = (reg || wide) && sh.lanes_log2 == 0 && order_len <= (vsym ? 64 : 256);
   if (sh.stack == 2 && !snap_ok) return DLS_ERR_BAD_ARG;
   bool snap = snap_ok && sh.stack != 1;
   kp.snap_cap = snap ? std::max(1, snapshot_entries(info, n, flags, depth)) : 0;
@@ -1220,10 +1392,13 @@ static int prepare_launch(int n, uint32_t flags, const uint8_t *order, int order
   // by default, an explicit block size whose snapshot stacks do not fit
   // falls back to the per-position stack (a fifth of the bytes per entry)
   if (snap && sh.stack == 0 && !default_block &&
-      smem_bytes_snapshot(order_len, kp.snap_cap, sh.block, vsym) + static_smem > di.smem_optin) {
+      smem_bytes_snapshot(order_len, kp.snap_cap, sh.block, vsym, wide) + static_smem >
+          di.smem_optin) {
     snap = false;
     kp.snap_cap = 0;
   }
+  // words in registers: the 64-bit fields, or the wide words of a snapshot
+  if (sh.words == 2 && !reg && !(snap && wide)) return DLS_ERR_BAD_ARG;
   pr->reg = reg;
   const bool plain = sh.kernel == DLS_KERNEL_PLAIN;
   pr->run = snap ? (plain ? DLS_RUN_PLAIN_SNAPSHOT : DLS_RUN_SNAPSHOT)
@@ -1237,10 +1412,11 @@ static int prepare_launch(int n, uint32_t flags, const uint8_t *order, int order
   if (sh.fuse == 1 && !fu_fits) return DLS_ERR_BAD_ARG;
   const bool fu = fu_fits && (sh.fuse == 1 || (sh.fuse == 0 && kFuseByDefault));
   pr->fused = fu;
-  pr->fn = snap ? pick_snapshot(plain, vsym, d_nodes != nullptr, dgw, la, fu)
+  pr->wide = snap && wide;
+  pr->fn = snap ? pick_snapshot(plain, vsym, pr->wide, d_nodes != nullptr, dgw, la, fu)
                 : pick_kernel(sh.kernel, reg, vsym, d_nodes != nullptr, sh.lanes_log2 > 0);
   auto smem_for = [&](int block) {
-    return snap ? smem_bytes_snapshot(order_len, kp.snap_cap, block, vsym)
+    return snap ? smem_bytes_snapshot(order_len, kp.snap_cap, block, vsym, pr->wide)
                 : smem_bytes(order_len, n, depth, order_len - 1, block, reg);
   };
   size_t smem = smem_for(sh.block);
@@ -1285,10 +1461,10 @@ static int prepare_launch(int n, uint32_t flags, const uint8_t *order, int order
     pr->kp2.defer = 0;
     pr->kp2.recount = 1;
     int b2 = sh.block;
-    size_t sm2 = smem_bytes_snapshot(order_len, pr->bound, b2, vsym);
+    size_t sm2 = smem_bytes_snapshot(order_len, pr->bound, b2, vsym, pr->wide);
     while (sm2 + static_smem > di.smem_optin && b2 > 32) {
       b2 /= 2;
-      sm2 = smem_bytes_snapshot(order_len, pr->bound, b2, vsym);
+      sm2 = smem_bytes_snapshot(order_len, pr->bound, b2, vsym, pr->wide);
     }
     if (sm2 + static_smem > di.smem_optin) return DLS_ERR_NO_MEMORY;
     if (sm2 > smem) {
@@ -1466,14 +1642,14 @@ int dls_describe_launch(int n, uint32_t flags, const uint8_t *order, int order_l
                           nullptr, nullptr, cfg, &pr);
   if (rc) return rc;
   out->run = pr.run;
-  out->words = pr.reg ? 2 : 1;
+  out->words = (pr.reg || pr.wide) ? 2 : 1;
   out->block_threads = pr.block;
   out->grid_blocks = (int)pr.grid;
   out->smem_bytes = (int)pr.smem;
   out->stack_entries = pr.kp.snap_cap;
   out->fused = pr.fused ? 1 : 0;
   const bool snapshot = pr.run == DLS_RUN_SNAPSHOT || pr.run == DLS_RUN_PLAIN_SNAPSHOT;
-  out->step = !snapshot ? 0 : ((flags & DLS_VSYM) ? 1 : 2);
+  out->step = !snapshot ? 0 : ((flags & DLS_VSYM) ? 1 : (pr.wide ? 3 : 2));
   return DLS_OK;
 }
 

@@ -440,4 +440,188 @@ __device__ __forceinline__ bool bsnap_step(BLane &s, const Geo &g, const SnapSta
   return dead && !keep && !has;
 }
 
+// ------------------------------------------------------------ wide words --
+//
+// Order 9 without vertical symmetry: the values 0-7 of a line keep their
+// byte (as with byte words) and the value 8 a bit of its own.
+//   row bytes:    the rows that have cells after the prefix get slots 0-7,
+//                 slot k is byte k of {R1:R0} (at most 8 such rows);
+//   column bytes: slot s of a column is byte s of C0 (s < 4), byte s - 4 of
+//                 C1 (4 <= s < 7) or byte s - 7 of C2 (s = 7, 8); byte 3 of
+//                 C1 and bytes 2-3 of C2 stay 0, so two byte permutes reach
+//                 any column (the other one picks a zero byte);
+//   value 8:      V8 bit i = row i holds 8, bit 16 + j = column j holds 8.
+// A cell's admissible values: ~(row byte | column bytes) for 0-7 in one
+// three-input logic op (the second permute fills bytes 1-3 with ones so the
+// result keeps only byte 0), and bit 8 set when V8 has neither the cell's
+// row bit nor its column bit (mask m8).  A value is placed by multiply-adds:
+// its low byte into R0, R1, C0, C1, C2 by the cell's multipliers (2^(8k) or
+// 0), its bit 8 into V8 by m8.  An entry is 32 bytes: R0, R1, C0, C1, then
+// C2, V8, the diagonal words and (position | untried candidates << 16).
+
+// Position table row for order position p (80 bytes):
+//   a  = byte multipliers of p (R0, R1, C0, C1);
+//   a2 = (C2 multiplier of p, m8 of p, diagonal mask of p, and the diagonal
+//        mask of p + 1 with diagonal words, else the C2 multiplier of p + 1);
+//   b  = byte multipliers of p + 1 (the fused step);
+//   c  = (row selector, column selectors A and B, m8) of p + 1;
+//   c2 = the same for p + 2.
+struct WRow {
+  uint4 a, a2, b, c, c2;
+};
+
+// Slot maps of an order after its prefix: rslot[i] (-1: row i has no cell
+// after the prefix), cslot[j].  Returns false if more than 8 rows do.
+__host__ __device__ inline bool wide_slots(int n, const uint8_t *ci, const uint8_t *cj, int len,
+                                           int depth, int *rslot, int *cslot) {
+  for (int k = 0; k < n; ++k) rslot[k] = cslot[k] = -1;
+  int nr = 0, nc = 0;
+  for (int t = depth; t < len; ++t) {
+    if (rslot[ci[t]] < 0) rslot[ci[t]] = nr++;
+    if (cslot[cj[t]] < 0) cslot[cj[t]] = nc++;
+  }
+  return nr <= 8 && nc <= 9;
+}
+
+__host__ __device__ inline uint32_t wide_row_sel(int rs) { return rs < 0 ? 0u : (uint32_t)rs; }
+__host__ __device__ inline uint32_t wide_col_sel_a(int cs) {
+  return (cs >= 0 && cs < 7) ? (uint32_t)cs : 7u;
+}
+__host__ __device__ inline uint32_t wide_col_sel_b(int cs) {
+  return (cs >= 7) ? (0x7650u | (uint32_t)(cs - 7)) : 0x7654u;
+}
+__host__ __device__ inline uint32_t wide_col_mult(int cs, int word) {
+  if (cs < 0) return 0u;
+  const int w = cs < 4 ? 0 : (cs < 7 ? 1 : 2);
+  const int b = cs < 4 ? cs : (cs < 7 ? cs - 4 : cs - 7);
+  return w == word ? (1u << (8 * b)) : 0u;
+}
+
+__host__ __device__ inline WRow wrow_make(int n, bool diag, bool dgw, const uint8_t *ci,
+                                          const uint8_t *cj, int p, int len, const int *rslot,
+                                          const int *cslot) {
+  const int q = p + 1 < len ? p + 1 : len - 1;
+  const int q2 = p + 2 < len ? p + 2 : len - 1;
+  auto m8 = [&](int t) { return (1u << ci[t]) | (1u << (16 + cj[t])); };
+  auto sel = [&](int t) {
+    return make_uint4(wide_row_sel(rslot[ci[t]]), wide_col_sel_a(cslot[cj[t]]),
+                      wide_col_sel_b(cslot[cj[t]]), m8(t));
+  };
+  auto bytes = [&](int t) {
+    const int rs = rslot[ci[t]], cs = cslot[cj[t]];
+    return make_uint4(rs >= 0 ? byte_mult(rs, 0) : 0u, rs >= 0 ? byte_mult(rs, 1) : 0u,
+                      wide_col_mult(cs, 0), wide_col_mult(cs, 1));
+  };
+  WRow r;
+  r.a = bytes(p);
+  const Cell d0 = describe_regs(ci[p], cj[p], n, diag, 8, 8);
+  const Cell d1 = describe_regs(ci[q], cj[q], n, diag, 8, 8);
+  r.a2 = make_uint4(wide_col_mult(cslot[cj[p]], 2), m8(p), dgw ? d0.y : 0u,
+                    dgw ? d1.y : wide_col_mult(cslot[cj[q]], 2));
+  r.b = bytes(q);
+  r.c = sel(q);
+  r.c2 = sel(q2);
+  return r;
+}
+
+// Per-lane state of the wide-word search.
+struct WLane {
+  uint32_t R0, R1, C0, C1, C2, V8;
+  uint32_t dg;
+  int p;
+  uint32_t L;
+  WRow r;                    // table row of p
+  int sp, bot;
+  long long prefix;
+  unsigned long long cnt;
+  unsigned long long nodes;
+};
+
+// Admissible values at a cell with selectors / mask c = (row, column A,
+// column B, m8).
+__device__ __forceinline__ uint32_t wcands(uint32_t R0, uint32_t R1, uint32_t C0, uint32_t C1,
+                                           uint32_t C2, uint32_t V8, uint4 c) {
+  const uint32_t lo = ~(__byte_perm(R0, R1, c.x) | __byte_perm(C0, C1, c.y) |
+                        __byte_perm(C2, 0xffffff00u, c.z));
+  return lo | ((V8 & c.w) == 0u ? 0x100u : 0u);
+}
+
+// The wide-word search iteration: the moves of snap_step / bsnap_step, with
+// the same predicated stack and table traffic as bsnap_step.
+template <bool NODES, bool DG, bool LA = false, bool FU = false>
+__device__ __forceinline__ bool wsnap_step(WLane &s, const Geo &g, const SnapStack &st,
+                                           const WRow *tb, unsigned B, uint32_t &ovf) {
+  static_assert(!LA || !DG, "lookahead: no diagonal words");
+  static_assert(!FU || (!DG && !LA), "fused step: no diagonal words, no lookahead");
+  const uint32_t nv = s.L & (0u - s.L);
+  const uint32_t Lr = s.L ^ nv;
+  const bool keep = Lr != 0u;
+  const bool has = s.sp > s.bot;
+  int q = s.p + 1;  // <= last: a lane never stands on the last cell
+  uint4 e = make_uint4(s.R0, s.R1, s.C0, s.C1);  // the state before placing nv
+  uint4 e2 = make_uint4(s.C2, s.V8, s.dg, (uint32_t)s.p | (Lr << 16));
+  const uint32_t lo = nv & 0xffu, hi = nv >> 8;
+  uint32_t r0 = lo * s.r.a.x + e.x, r1 = lo * s.r.a.y + e.y;
+  uint32_t c0 = lo * s.r.a.z + e.z, c1 = lo * s.r.a.w + e.w;
+  uint32_t c2 = lo * s.r.a2.x + e2.x, v8 = hi * s.r.a2.y + e2.y;
+  uint32_t L1 = wcands(r0, r1, c0, c1, c2, v8, s.r.c);  // bits 0-8 only
+  uint32_t dg = e2.z;
+  if (DG) {
+    dg += (nv * 0x10001u) & s.r.a2.z;
+    const uint32_t t = dg & s.r.a2.w;
+    L1 &= ~(t | (t >> 16));
+  }
+  if (NODES) s.nodes++;
+  if (FU) {
+    const bool f = q != g.last && L1 != 0u && (L1 & (L1 - 1u)) == 0u;
+    const uint32_t d2 = f ? L1 : 0u;
+    const uint32_t lo2 = d2 & 0xffu, hi2 = d2 >> 8;
+    r0 = lo2 * s.r.b.x + r0;
+    r1 = lo2 * s.r.b.y + r1;
+    c0 = lo2 * s.r.b.z + c0;
+    c1 = lo2 * s.r.b.w + c1;
+    c2 = lo2 * s.r.a2.w + c2;
+    v8 = hi2 * s.r.c.w + v8;
+    const uint32_t L2 = wcands(r0, r1, c0, c1, c2, v8, s.r.c2);
+    if (NODES) s.nodes += f ? 1u : 0u;
+    L1 = f ? L2 : L1;
+    q = f ? q + 1 : q;
+  }
+  const bool leaf = q == g.last;
+  const unsigned leaves = leaf ? (unsigned)__popc(L1) : 0u;
+  s.cnt += leaves;
+  if (NODES) s.nodes += leaves;
+  bool dead = leaf || L1 == 0u;
+  if (LA) dead = dead || wcands(r0, r1, c0, c1, c2, v8, s.r.c2) == 0u;
+  const bool push = keep && !dead;
+  const bool pop = dead && !keep && has;
+  ovf |= (push && s.sp >= st.cap) ? 1u : 0u;
+  // entries: R0, R1, C0, C1 in sa; C2, V8, diagonal words, packed in sb
+  // (the stack's second array of 16-byte slots)
+  uint4 *sb = reinterpret_cast<uint4 *>(st.sw);
+  st_shared_if(push, st.sa, (s.sp + 1) * (int)B, e);
+  st_shared_if(push, sb, (s.sp + 1) * (int)B, e2);
+  ld_shared_if(pop, st.sa, s.sp * (int)B, e);
+  ld_shared_if(pop, sb, s.sp * (int)B, e2);
+  s.R0 = dead ? e.x : r0;
+  s.R1 = dead ? e.y : r1;
+  s.C0 = dead ? e.z : c0;
+  s.C1 = dead ? e.w : c1;
+  s.C2 = dead ? e2.x : c2;
+  s.V8 = dead ? e2.y : v8;
+  if (DG) s.dg = dead ? e2.z : dg;
+  s.L = dead ? (e2.w >> 16) : L1;
+  const int np = dead ? (int)(e2.w & 0xffffu) : q;
+  const bool moved = np != s.p;
+  s.p = np;
+  s.sp = min(s.sp + (push ? 1 : 0) - (pop ? 1 : 0), st.cap);
+  const uint4 *rows = reinterpret_cast<const uint4 *>(tb);
+  ld_shared_if(moved, rows, 5 * s.p, s.r.a);
+  ld_shared_if(moved, rows, 5 * s.p + 1, s.r.a2);
+  ld_shared_if(moved, rows, 5 * s.p + 2, s.r.b);
+  ld_shared_if(moved, rows, 5 * s.p + 3, s.r.c);
+  ld_shared_if(moved, rows, 5 * s.p + 4, s.r.c2);
+  return dead && !keep && !has;
+}
+
 }  // namespace dls

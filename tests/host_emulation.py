@@ -135,7 +135,7 @@ class Emulated:
             return rc, None
         if entry == "describe":
             keys = ["run", "words", "block_threads", "grid_blocks", "smem_bytes",
-                    "stack_entries", "fused"]
+                    "stack_entries", "fused", "step"]
             return 0, dict(zip(keys, map(int, lines[1].split())))
         head = lines[1].split()
         if "hi" in head:

@@ -16,7 +16,7 @@
 // (dls_describe_launch).  "Device" buffers are host memory here.  Output:
 // "rc R" and, when R = 0, "total T nodes N" (nodes 0 where the entry does
 // not count them; count and plan add "status S started K") and one count per
-// prefix; describe prints "run W block grid smem entries fused" instead.
+// prefix; describe prints "run W block grid smem entries fused step" instead.
 //
 // classes: dls_hourglass_classes over `len`-byte hourglass records; prints
 // "rc R" and one class size per record.
@@ -235,8 +235,8 @@ int main(int argc, char **argv) {
     const int rc = dls_describe_launch(n, flags, order.data(), len, depth, P, &cfg, &info);
     std::printf("rc %d\n", rc);
     if (rc == 0)
-      std::printf("%d %d %d %d %d %d %d\n", info.run, info.words, info.block_threads,
-                  info.grid_blocks, info.smem_bytes, info.stack_entries, info.fused);
+      std::printf("%d %d %d %d %d %d %d %d\n", info.run, info.words, info.block_threads,
+                  info.grid_blocks, info.smem_bytes, info.stack_entries, info.fused, info.step);
     return 0;
   }
   std::vector<uint64_t> counts((size_t)P, 0xdeadbeefull);

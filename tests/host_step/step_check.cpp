@@ -58,6 +58,119 @@ bool bsearch(BLane &s, const Geo &g, const SnapStack &st, const BRow *tb, int le
   }
 }
 
+// The wide-word step (order 9 without vertical symmetry).
+template <bool DG, bool LA, bool FU>
+bool wsearch(WLane &s, const Geo &g, const SnapStack &st, const WRow *tb, int len, Run &run) {
+  for (;;) {
+    ++run.iters;
+    const bool fin = wsnap_step<true, DG, LA, FU>(s, g, st, tb, 1u, run.ovf);
+    if (s.p < 0 || s.p >= len || s.sp < 0 || s.sp > st.cap) {
+      ++run.badpos;
+      return false;
+    }
+    run.maxsp = std::max(run.maxsp, s.sp);
+    if (fin) return true;
+  }
+}
+
+// Wide-word runs: each prefix placed with plain line masks, written into the
+// slots as the kernel's load does, then searched.
+int run_wide(int n, uint32_t flags, int mode, const std::vector<uint8_t> &ob,
+             const std::vector<uint8_t> &pre, int depth, int cap) {
+  const bool diag = (flags & 1u) != 0;
+  const int len = (int)ob.size() / 2;
+  std::vector<uint8_t> ci(len), cj(len);
+  for (int t = 0; t < len; ++t) {
+    ci[t] = ob[2 * t];
+    cj[t] = ob[2 * t + 1];
+  }
+  int rs[DLS_MAX_N], cs[DLS_MAX_N];
+  if (!wide_slots(n, ci.data(), cj.data(), len, depth, rs, cs)) return 2;
+  bool dg = false;
+  for (int t = depth; t < len; ++t)
+    if (diag && (ci[t] == cj[t] || ci[t] + cj[t] == n - 1)) dg = true;
+  if ((mode == 1 || mode == 2) && dg) return 2;
+  std::vector<WRow> rows(len);
+  for (int t = 0; t < len; ++t)
+    rows[t] = wrow_make(n, diag, dg, ci.data(), cj.data(), t, len, rs, cs);
+  Geo g;
+  g.n = n;
+  g.all = (1u << n) - 1u;
+  g.pairmask = 0u;
+  g.depth = depth;
+  g.last = len - 1;
+  g.vsmask = 0u;
+  std::vector<uint4> sa((size_t)cap + 2, make_uint4(~0u, ~0u, ~0u, ~0u));
+  std::vector<uint4> sb((size_t)cap + 2, make_uint4(~0u, ~0u, ~0u, ~0u));
+  const SnapStack st{sa.data(), reinterpret_cast<uint32_t *>(sb.data()), cap};
+  const long long P = depth ? (long long)pre.size() / depth : 1;
+  Run run;
+  for (long long k = 0; k < P; ++k) {
+    const uint8_t *rec = pre.data() + (size_t)k * (size_t)depth;
+    uint32_t rw[DLS_MAX_N] = {0}, cl[DLS_MAX_N] = {0}, md = 0u, ad = 0u;
+    bool ok = true;
+    for (int t = 0; t < depth && ok; ++t) {
+      const int i = ci[t], j = cj[t];
+      const uint32_t b = rec[t] < n ? (1u << rec[t]) : 0u;
+      const bool om = diag && i == j, oa = diag && i + j == n - 1;
+      ok = b != 0u && ((rw[i] | cl[j] | (om ? md : 0u) | (oa ? ad : 0u)) & b) == 0u;
+      rw[i] |= b;
+      cl[j] |= b;
+      md |= om ? b : 0u;
+      ad |= oa ? b : 0u;
+    }
+    unsigned long long cnt = 0, nodes = 0;
+    if (ok && depth == len) {
+      cnt = 1;
+    } else if (ok) {
+      const int i = ci[depth], j = cj[depth];
+      const bool om = diag && i == j, oa = diag && i + j == n - 1;
+      const uint32_t L = g.all & ~(rw[i] | cl[j] | (om ? md : 0u) | (oa ? ad : 0u));
+      if (depth == g.last) {
+        cnt = nodes = (unsigned)__popc(L);
+      } else if (L != 0u) {
+        WLane w{};
+        for (int x = 0; x < n; ++x) {
+          if (rs[x] >= 0) {
+            w.R0 |= (rw[x] & 0xffu) * byte_mult(rs[x], 0);
+            w.R1 |= (rw[x] & 0xffu) * byte_mult(rs[x], 1);
+          }
+          if (cs[x] >= 0) {
+            w.C0 |= (cl[x] & 0xffu) * wide_col_mult(cs[x], 0);
+            w.C1 |= (cl[x] & 0xffu) * wide_col_mult(cs[x], 1);
+            w.C2 |= (cl[x] & 0xffu) * wide_col_mult(cs[x], 2);
+          }
+          w.V8 |= ((rw[x] >> 8) & 1u) << x;
+          w.V8 |= ((cl[x] >> 8) & 1u) << (16 + x);
+        }
+        w.dg = md | (ad << 16);
+        w.p = depth;
+        w.L = L;
+        w.r = rows[depth];
+        bool done;
+        if (mode == 1)
+          done = wsearch<false, true, false>(w, g, st, rows.data(), len, run);
+        else if (mode == 2)
+          done = wsearch<false, false, true>(w, g, st, rows.data(), len, run);
+        else
+          done = dg ? wsearch<true, false, false>(w, g, st, rows.data(), len, run)
+                    : wsearch<false, false, false>(w, g, st, rows.data(), len, run);
+        if (!done) {
+          std::fprintf(stderr, "iters %llu maxsp %d overflow %u badpos %d\n", run.iters,
+                       run.maxsp, run.ovf, run.badpos);
+          return 3;
+        }
+        cnt = w.cnt;
+        nodes = w.nodes;
+      }
+    }
+    std::printf("%llu %llu\n", cnt, nodes);
+  }
+  std::fprintf(stderr, "iters %llu maxsp %d overflow %u badpos %d\n", run.iters, run.maxsp,
+               run.ovf, run.badpos);
+  return 0;
+}
+
 template <bool VSYM, bool DG, bool LA, bool FU>
 bool search(SnapLane &s, const Geo &g, const SnapStack &st, const SnapTable &tb, int len,
             Run &run) {
@@ -235,6 +348,7 @@ int main(int argc, char **argv) {
   }
   if ((mode == 1 || mode == 2) && (dg || vsym)) return 2;
   if (pos) return run_pos(n, flags, mode, ob, pre, depth, sp);
+  if (!vsym && n == 9) return run_wide(n, flags, mode, ob, pre, depth, cap);
 
   std::vector<Cell> tbl(len);
   std::vector<uint4> tsh(len);

@@ -124,7 +124,8 @@ def test_larger_orders_from_sampled_partial_squares(dls, n, flags, rows):
 
 def test_snapshot_stack_refused_where_it_does_not_apply(dls):
     """The snapshot search needs register words and one lane per prefix."""
-    t9 = torch.from_numpy(np.arange(9, dtype=np.uint8)[None]).cuda()
+    # order 9 with every row after the prefix (no row 0): no wide words
+    t9 = torch.from_numpy(np.zeros((1, 0), dtype=np.uint8)).cuda()
     t8 = torch.from_numpy(np.arange(8, dtype=np.uint8)[None]).cuda()
     for n, t, sh in ((9, t9, dict(stack=2)), (8, t8, dict(stack=2, words=1)),
                      (8, t8, dict(stack=2, lanes_per_prefix=2)),
@@ -146,10 +147,12 @@ def test_describe_launch_names_the_kernel(dls):
     assert dls.describe_launch(8, D, o8, 15, 1000,
                                dls.Launch(kernel=dls.KERNEL_PLAIN, stack=1))["kernel"] == "k_plain"
     d9 = dls.describe_launch(9, D, o9, 17, 1000)
+    assert d9["kernel"] == "k_snapshot" and d9["step"] == "snapshot, wide words"
+    d9 = dls.describe_launch(9, D, o9, 5, 1000)  # rows 0-8 all searched
     assert d9["kernel"] == "k_persistent" and d9["words"] == "shared"
     assert dls.describe_launch(8, D, o8, 15, 0)["grid_blocks"] == 0
     with pytest.raises(dls.DlsError):
-        dls.describe_launch(9, D, o9, 17, 10, dls.Launch(stack=2))
+        dls.describe_launch(9, D, o9, 5, 10, dls.Launch(stack=2))
 
 
 def test_lookahead_where_it_applies(dls):
@@ -581,3 +584,46 @@ def test_stack_cap_on_the_benchmark_workload(dls, depth):
             assert (counts.cpu().numpy() == full).all()
             assert int(total.cpu().numpy()[0]) == int(full.sum())
             plan.close()
+
+
+@pytest.mark.parametrize("flags", [D, 0])
+def test_order9_wide_words(dls, flags):
+    """Order 9 on the wide-word snapshot search: random partial squares with
+    4 rows filled (5 for ordinary squares), extended through the rest of both
+    diagonals with the diagonal flag, so that every step runs (diagonal
+    words, the fused step, the lookahead), plus a capped stack (deferred
+    prefixes recounted) and the plain launch, against the oracle."""
+    import dls_inputs
+    rows = 4 if flags & D else 5
+    order = dls.fill_order(9, flags, first_rows=rows)
+    o_order = orders.md_ad_rows(9, first_rows=rows)
+    depth = rows * 9
+    pre, o_pre = [], []
+    for k in range(8):
+        draws = dls_inputs.draws(1 << 14, seed=9 * 100 + rows + 50, stream=k)
+        a, _ = dls.sample_prefix(9, flags, order, depth, draws)
+        b, _ = oracle.sample_prefix(9, flags, o_order, depth, draws)
+        if b is None:
+            continue
+        pre.append(a)
+        o_pre.append(b)
+    pre, o_pre = np.array(pre), np.array(o_pre)
+    assert (pre == o_pre).all()
+    cases = [(pre, o_pre, depth)]
+    if flags & D:
+        diag = sum(1 for i, j in o_order[depth:] if i == j or i + j == 8)
+        p2, _ = dls.extend_prefixes(9, flags, order, pre, depth + diag)
+        o2, _ = oracle.extend(9, flags, o_order, o_pre, depth + diag)
+        assert (p2 == o2).all() and len(p2) > 0
+        cases.append((p2, o2, depth + diag))
+    for p, op, d in cases:
+        ref, _ = oracle.count_many(9, flags, o_order, op, threads=THREADS)
+        shapes = [dict(), dict(kernel=dls.KERNEL_PLAIN), dict(stack_cap=4),
+                  dict(block_threads=32, check_every=1)]
+        if d > depth:
+            shapes += [dict(fuse=-1), dict(lookahead=1), dict(stack_cap=3, block_threads=64)]
+        for sh in shapes:
+            info = dls.describe_launch(9, flags, order, d, len(p), dls.Launch(**sh))
+            assert info["step"] == "snapshot, wide words", (sh, info)
+            c = _gpu_counts(dls, 9, flags, order, p, dls.Launch(**sh))
+            assert (c == ref).all(), (d, sh)

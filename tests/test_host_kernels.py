@@ -276,16 +276,22 @@ def test_describe_launch_and_argument_errors(dls, emulated):
     assert rc == 0 and d["run"] == 3
     rc, d = emulated.count("describe", 8, D, o8, p8, stack=1)
     assert rc == 0 and d["run"] == 0 and d["stack_entries"] == 0
+    # order 9: the wide words where at most 8 rows have cells after the
+    # prefix (row 0 inside it), else the per-position search
     o9 = dls.fill_order(9, D)
     rc, d = emulated.count("describe", 9, D, o9, np.zeros((10, 17), np.uint8))
+    assert rc == 0 and d["run"] == 2 and d["words"] == 2 and d["step"] == 3
+    rc, d = emulated.count("describe", 9, D, o9, np.zeros((10, 5), np.uint8))
+    assert rc == 0 and d["run"] == 0 and d["words"] == 1
+    rc, d = emulated.count("describe", 9, D, o9, np.zeros((10, 17), np.uint8), words=1)
     assert rc == 0 and d["run"] == 0 and d["words"] == 1
     for n, order, depth, sh in (
-            (9, o9, 17, dict(stack=2)), (8, o8, 15, dict(stack=2, words=1)),
+            (9, o9, 5, dict(stack=2)), (8, o8, 15, dict(stack=2, words=1)),
             (8, o8, 15, dict(stack=2, lanes_per_prefix=2)), (8, o8, 15, dict(stack=3)),
             (8, o8, 15, dict(fuse=1)), (8, o8, 15, dict(lookahead=1)),
             (8, o8, 28, dict(fuse=1, lookahead=1)), (8, o8, 28, dict(fuse=2)),
             (8, o8, 15, dict(block_threads=48)), (8, o8, 15, dict(lanes_per_prefix=3)),
-            (9, o9, 17, dict(words=2)), (8, o8, 15, dict(check_every=3))):
+            (9, o9, 17, dict(words=2, stack=1)), (8, o8, 15, dict(check_every=3))):
         rc, _ = emulated.count("count", n, D, order, np.zeros((4, depth), np.uint8), **sh)
         assert rc == ERR_BAD_ARG, (n, depth, sh)
 

@@ -133,6 +133,28 @@ def test_step_on_partial_orders(dls, step_check, tmp_path, n, k, depth):
     check_workload(step_check, tmp_path, wl, n, 0)
 
 
+@pytest.mark.parametrize("flags", [D, 0])
+def test_wide_step_on_order9(dls, step_check, tmp_path, flags):
+    """Order 9 (the wide words: values 0-7 in byte slots, value 8 a bit of
+    its own) on random partial squares: 4 and 5 rows filled (5 and 6 for
+    ordinary squares; with the diagonal flag the diagonals are searched),
+    and 4 rows plus the rest of both diagonals (every step mode: plain,
+    lookahead, fused)."""
+    for rows in ((4, 5) if flags & D else (5, 6)):
+        wl = gpu_cases.sampled_rows(dls, 9, flags, rows, count=4)
+        check_workload(step_check, tmp_path, wl, 9, flags)
+    if flags & D:
+        wl = gpu_cases.sampled_rows(dls, 9, D, 4, count=4)
+        # the diagonal cells of rows 4-8 follow the filled rows in the order
+        diag = sum(1 for i, j in wl.oracle_order[wl.depth:] if i == j or i + j == 8)
+        depth = wl.depth + diag
+        pre, _ = dls.extend_prefixes(9, D, wl.order, wl.prefixes, depth)
+        o_pre, _ = oracle.extend(9, D, wl.oracle_order, wl.oracle_prefixes, depth)
+        wl2 = gpu_cases.Workload(9, D, wl.order, pre, wl.oracle_order, o_pre, depth=depth)
+        iters = check_workload(step_check, tmp_path, wl2, 9, D)
+        assert set(iters) == {0, 1, 2}
+
+
 def test_step_on_one_diagonal_of_the_order8_workload(dls, step_check, tmp_path):
     """One of the 64 diagonal fillings of the order-8 benchmark workload,
     split at depth 25 with the squared-count order after the split (the
