@@ -234,11 +234,16 @@ def test_snapshot_stack_deep_orders(dls):
 
 
 def test_register_words_refused_when_they_do_not_fit(dls):
+    # order 9: register words only as the snapshot search's wide words, which
+    # need at most 8 rows after the prefix; refused with the per-position
+    # stack and with every row after the prefix
     order = dls.fill_order(9, D)
     t = torch.from_numpy(np.arange(9, dtype=np.uint8)[None]).cuda()
-    with pytest.raises(dls.DlsError) as e:
-        dls.count(9, D, order, t, launch=dls.Launch(words=2))
-    assert e.value.code == 3
+    t0 = torch.from_numpy(np.zeros((1, 0), np.uint8)).cuda()
+    for tt, sh in ((t, dict(words=2, stack=1)), (t0, dict(words=2))):
+        with pytest.raises(dls.DlsError) as e:
+            dls.count(9, D, order, tt, launch=dls.Launch(**sh))
+        assert e.value.code == 3
 
 
 def test_node_counts_match_oracle(dls):
