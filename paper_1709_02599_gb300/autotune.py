@@ -32,6 +32,7 @@ SHAPES = [
     {"stack_cap": 17, "block_threads": 64},
     {"stack_cap": 15, "block_threads": 64},
     {"stack_cap": 17},
+    {"stack_cap": 20},
     {"fuse": -1},
     {"fuse": -1, "block_threads": 64},
     {"lookahead": 1},
