@@ -259,8 +259,10 @@ typedef struct {
     int64_t budget;       /* stop early after this many search iterations per
                              lane (the lanes of a warp step together; 0 = no
                              limit) -- see "Stopping early" below          */
-    int stack_cap;        /* snapshot entries per lane: 0 = the bound that no
-                             search can exceed (default); a smaller value
+    int stack_cap;        /* snapshot entries per lane: 0 = the default --
+                             the bound that no search can exceed, or for the
+                             wide words of order 9 (32-byte entries) a cap
+                             of 20 where a cap applies; a smaller value
                              leaves more lanes resident -- see "Stack cap"
                              below                                          */
     const volatile int *abort_flag; /* NULL, or a word the kernel polls (device

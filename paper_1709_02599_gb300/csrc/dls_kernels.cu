@@ -1281,6 +1281,8 @@ static size_t smem_bytes_snapshot(int order_len, int entries, int block, bool vs
 // A resolved launch: the parameter block, the kernel and its shape.
 // dls_launch_t.fuse = 0 takes the fused step where it applies.
 static constexpr bool kFuseByDefault = true;
+// dls_launch_t.stack_cap = 0 with wide words (order 9) takes this cap.
+static constexpr int kWideDefaultCap = 20;
 
 struct Prepared {
   KParams kp;
@@ -1376,8 +1378,13 @@ static int prepare_launch(int n, uint32_t flags, const uint8_t *order, int order
   // node count, budget or abort flag); otherwise the bound stays
   const bool can_defer = d_counts != nullptr && d_nodes == nullptr && sh.budget == 0 &&
                          sh.abort_flag == nullptr;
-  if (snap && sh.stack_cap > 0 && sh.stack_cap < kp.snap_cap && can_defer) {
-    kp.snap_cap = sh.stack_cap;
+  // the wide words' 32-byte entries leave one block of 128 lanes per SM at
+  // the full bound of a typical order-9 split; by default they take a cap
+  // of kWideDefaultCap entries (two blocks: 5.3e9 against 3.7e9 squares/s
+  // on canonical order-9 hourglasses split 4 cells deeper)
+  const int cap_asked = sh.stack_cap > 0 ? sh.stack_cap : (wide ? kWideDefaultCap : 0);
+  if (snap && cap_asked > 0 && cap_asked < kp.snap_cap && can_defer) {
+    kp.snap_cap = cap_asked;
     pr->recount = true;
     kp.defer = 1;
     pr->total_out = d_total;
