@@ -261,10 +261,10 @@ typedef struct {
                              limit) -- see "Stopping early" below          */
     int stack_cap;        /* snapshot entries per lane: 0 = the default --
                              the bound that no search can exceed, or for the
-                             wide words of order 9 (32-byte entries) a cap
-                             of 20 where a cap applies; a smaller value
-                             leaves more lanes resident -- see "Stack cap"
-                             below                                          */
+                             wide words of order 9 (32-byte entries) the
+                             largest cap with which two blocks fit an SM,
+                             where a cap applies; a smaller value leaves
+                             more lanes resident -- see "Stack cap" below   */
     const volatile int *abort_flag; /* NULL, or a word the kernel polls (device
                              memory, or host memory the GPU can read, e.g.
                              pinned and mapped): once it reads nonzero, the

@@ -1051,6 +1051,7 @@ static int get_workspace(cudaStream_t stream, Workspace **out) {
 struct DevInfo {
   int sms = 0;
   size_t smem_optin = 0;
+  size_t smem_per_sm = 0;
 };
 
 static int dev_info(DevInfo *d) {
@@ -1070,6 +1071,9 @@ static int dev_info(DevInfo *d) {
     e = cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return cuda_fail(e);
     di.smem_optin = (size_t)v;
+    e = cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    di.smem_per_sm = (size_t)v;
     it = cache.emplace(dev, di).first;
   }
   *d = it->second;
@@ -1281,8 +1285,6 @@ static size_t smem_bytes_snapshot(int order_len, int entries, int block, bool vs
 // A resolved launch: the parameter block, the kernel and its shape.
 // dls_launch_t.fuse = 0 takes the fused step where it applies.
 static constexpr bool kFuseByDefault = true;
-// dls_launch_t.stack_cap = 0 with wide words (order 9) takes this cap.
-static constexpr int kWideDefaultCap = 20;
 
 struct Prepared {
   KParams kp;
@@ -1378,11 +1380,25 @@ static int prepare_launch(int n, uint32_t flags, const uint8_t *order, int order
   // node count, budget or abort flag); otherwise the bound stays
   const bool can_defer = d_counts != nullptr && d_nodes == nullptr && sh.budget == 0 &&
                          sh.abort_flag == nullptr;
+  DevInfo di;
+  rc = dev_info(&di);
+  if (rc) return rc;
+  // static shared memory of the kernels: the 16-entry reduction buffer
+  const size_t static_smem = 16 * sizeof(unsigned long long);
   // the wide words' 32-byte entries leave one block of 128 lanes per SM at
-  // the full bound of a typical order-9 split; by default they take a cap
-  // of kWideDefaultCap entries (two blocks: 5.3e9 against 3.7e9 squares/s
-  // on canonical order-9 hourglasses split 4 cells deeper)
-  const int cap_asked = sh.stack_cap > 0 ? sh.stack_cap : (wide ? kWideDefaultCap : 0);
+  // the full bound of a typical order-9 split; by default they take the
+  // largest cap with which two blocks fit (canonical order-9 hourglasses
+  // split 4 cells deeper: bound 31, 1 block, 3.7e9 squares/s; cap 20, 5.2e9;
+  // cap 24, 5.6e9)
+  int cap_asked = sh.stack_cap;
+  if (cap_asked == 0 && wide && snap) {
+    const int blk = sh.block;
+    cap_asked = kp.snap_cap;
+    while (cap_asked > 1 &&
+           2 * (smem_bytes_snapshot(order_len, cap_asked, blk, false, true) + static_smem +
+                1024) > di.smem_per_sm)
+      --cap_asked;
+  }
   if (snap && cap_asked > 0 && cap_asked < kp.snap_cap && can_defer) {
     kp.snap_cap = cap_asked;
     pr->recount = true;
@@ -1390,11 +1406,6 @@ static int prepare_launch(int n, uint32_t flags, const uint8_t *order, int order
     pr->total_out = d_total;
     kp.total = nullptr;  // summed from the counts after the recount pass
   }
-  DevInfo di;
-  rc = dev_info(&di);
-  if (rc) return rc;
-  // static shared memory of the kernels: the 16-entry reduction buffer
-  const size_t static_smem = 16 * sizeof(unsigned long long);
   const bool default_block = cfg == nullptr || cfg->block_threads == 0;
   // by default, an explicit block size whose snapshot stacks do not fit
   // falls back to the per-position stack (a fifth of the bytes per entry)

@@ -136,6 +136,7 @@ enum cudaMemcpyKind {
 };
 enum cudaDeviceAttr {
   cudaDevAttrMultiProcessorCount = 16,
+  cudaDevAttrMaxSharedMemoryPerMultiprocessor = 81,
   cudaDevAttrMaxSharedMemoryPerBlockOptin = 97
 };
 enum cudaFuncAttribute { cudaFuncAttributeMaxDynamicSharedMemorySize = 8 };

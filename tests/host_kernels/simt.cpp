@@ -255,9 +255,10 @@ cudaError_t cudaGetDevice(int *dev) {
 }
 cudaError_t cudaSetDevice(int) { return cudaSuccess; }
 cudaError_t cudaDeviceGetAttribute(int *v, cudaDeviceAttr a, int) {
-  // two multiprocessors, so that grids have a few blocks; GB300's opt-in
-  // shared memory per block
-  *v = a == cudaDevAttrMultiProcessorCount ? 2 : 232448;
+  // two multiprocessors, so that grids have a few blocks; GB300's shared
+  // memory: 227 KB per block (opt-in), 228 KB per SM
+  *v = a == cudaDevAttrMultiProcessorCount ? 2
+       : a == cudaDevAttrMaxSharedMemoryPerMultiprocessor ? 233472 : 232448;
   return cudaSuccess;
 }
 cudaError_t cudaFuncSetAttribute(const void *, cudaFuncAttribute, int) { return cudaSuccess; }
