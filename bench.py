@@ -583,6 +583,8 @@ def run_leg(dls, spec, args, steps, stream, flush, seed, rank, ws, units=None,
                    "n": N, "flags": "diagonal" + (", vertically symmetric" if FLAGS & 2 else ""),
                    "row0": "identity", spec.unit_name.replace(" ", "_"): units, "seed": "rank",
                    "split_depth": int(depth_sel), "suffix_order": suffix_sel,
+                   "order_cells": int(len(order)),
+                   "tail_dropped": int(N * (N // 2 if FLAGS & 2 else N) - len(order)),
                    "prefixes": int(P), "squares_per_step": squares, "nodes_per_step": nodes,
                    "kernel": run["kernel"] + " (CUDA graph)", "launch": cfg, "resolved": run,
                    "autotune": tuned,

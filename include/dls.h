@@ -135,6 +135,33 @@ int dls_fill_order(int n, uint32_t flags, int kind, int first_rows,
 int dls_order_complete(int n, uint32_t flags, const uint8_t *order, int keep,
                        int kind, uint8_t *ij_out, int cap, int *len_out);
 
+/* Shortens a fill order that lists every cell of the square, without
+ * changing any count.  First, of the order's last `window` cells (none
+ * before position `keep`), those on the row of the last cell move to the
+ * end, in their order; or those on its column, whichever leaves the longer
+ * run below.  Then the run of cells at the end that lie on that one line
+ * and on neither diagonal (with DLS_DIAGONAL) is dropped, leaving at least
+ * one cell after `keep`.
+ * Why the count stays: once every other cell is filled, each dropped cell
+ * is the last open cell of its column (of its row, for a column run), so
+ * its value is the one that column lacks (Section 2.4.1 computes such a
+ * value directly).  Counting each value's occurrences in the full rows and
+ * columns shows that these values are exactly the values the run's line
+ * lacks, each once; no diagonal is involved.  So every filling of the kept
+ * cells has exactly one completion, and a count over the shortened order
+ * -- which counts fillings of its cells -- equals the count over the full
+ * order.  The cells before `keep` (a prefix) keep their places, so
+ * prefixes made with either order are the same.  The search gets shorter
+ * by the dropped cells, and moving the line's cells within the window
+ * lets more of them drop (window 0: only the run already at the end).
+ * An order with DLS_VSYM, or one that does not list every cell (a partial
+ * order, whose count is of partial squares), is copied unchanged.
+ * Writes up to `cap` (i,j) pairs to ij_out and their number to *len_out.
+ * Host memory, caller-owned.  Errors: as dls_fill_order, BAD_ORDER for a bad
+ * order, BAD_ARG for keep outside [0, order_len] or window < 0. */
+int dls_order_trim(int n, uint32_t flags, const uint8_t *order, int order_len,
+                   int keep, int window, uint8_t *ij_out, int cap, int *len_out);
+
 /* The prefix split of Section 5.2: every valid assignment of the first
  * `depth` order cells that extends one of the n_base base prefixes (each
  * base_depth bytes), base prefixes in turn, each one's extensions in

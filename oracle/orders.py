@@ -164,3 +164,51 @@ def heuristic_complete(n, kept, diagonal=True, vsym=False, squares=False):
                         best, cell = v, (i, j)
         assign(cell, True)
     return out
+
+
+def trim_tail(n, order, keep, window=6, diagonal=True, vsym=False):
+    """The order shortened so that every count stays the same.
+
+    Why a final run may go: say the last k cells of a full order all lie in
+    row r, none on a diagonal.  Fill every other cell validly.  Then each of
+    the k cells is the only empty cell of its column, so its value is the
+    one value that column lacks (Section 2.4.1 computes such a last value
+    directly).  Take a value v.  The n-1 other rows are full, so v fills n-1
+    cells there, plus one in row r unless row r lacks v; the n-k columns
+    without an empty cell hold v once each; so the k columns of the run hold
+    v (n-1) + [r has v] - (n-k) times, and (k-1) + [r has v] of them have it:
+    exactly one of them lacks v when row r lacks v, none when it has it.
+    The forced values are therefore the k values row r lacks, each once, and
+    no diagonal constrains those cells: the filling completes in exactly one
+    way.  A count over the first len-k cells (which counts fillings of
+    them) equals the count over the whole order.  Columns instead of rows:
+    the same with the roles swapped.
+
+    The rule: take the cells of the last cell's row among the last `window`
+    cells (none of the first `keep`), move them to the end keeping their
+    order, and count the run at the end that lies on that row and on neither
+    diagonal; the same with the last cell's column; keep the line with the
+    longer run (the row on a tie, nothing if both are empty) and drop its
+    run, leaving at least one cell after the first `keep`.  Only for an
+    order that lists every cell of a square without vertical symmetry;
+    anything else is returned as it is."""
+    order = [tuple(map(int, c)) for c in order]
+    if vsym or len(order) != n * n or len(order) <= keep + 1:
+        return order
+    start = max(keep, len(order) - window)
+    best, best_k = order, 0
+    for axis in (0, 1):
+        line = order[-1][axis]
+        on = [c for c in order[start:] if c[axis] == line]
+        off = [c for c in order[start:] if c[axis] != line]
+        cand = order[:start] + off + on
+        k = 0
+        for c in reversed(cand):
+            if c[axis] != line or k == len(order) - keep - 1:
+                break
+            if diagonal and (c[0] == c[1] or c[0] + c[1] == n - 1):
+                break
+            k += 1
+        if k > best_k:
+            best, best_k = cand, k
+    return best[:len(best) - best_k]

@@ -86,6 +86,26 @@ def order_complete(n, flags, order, keep, kind=ORDER_HEURISTIC):
     return buf[:ln.value].copy()
 
 
+TAIL_WINDOW = 6
+
+
+def order_trim(n, flags, order, keep, window=TAIL_WINDOW):
+    """``order`` shortened without changing any count (dls_order_trim): the
+    cells of the last cell's row or column among the last ``window`` cells
+    move to the end, then the run of that line's off-diagonal cells at the
+    end is dropped -- each of them is the last open cell of its column (row)
+    and the values these force are exactly those the line lacks.  The first
+    ``keep`` cells stay in place.  Orders with vertical symmetry and partial
+    orders come back unchanged."""
+    L = lib()
+    o, op, ol = _order(order)
+    buf = np.zeros((DLS_MAX_N * DLS_MAX_N, 2), np.uint8)
+    ln = ctypes.c_int(0)
+    _lib.check(L.dls_order_trim(n, flags, op, ol, keep, window, buf.ctypes.data_as(_lib.u8p),
+                                DLS_MAX_N * DLS_MAX_N, ctypes.byref(ln)), "dls_order_trim")
+    return buf[:ln.value].copy()
+
+
 def extend_prefixes(n, flags, order, base, depth):
     """All valid assignments of the first ``depth`` order cells extending
     the rows of ``base`` (uint8 [B, base_depth]).  Returns (uint8 [M, depth],

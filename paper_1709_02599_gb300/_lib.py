@@ -133,6 +133,8 @@ def load():
                                    ctypes.POINTER(c_int)]),
         "dls_order_complete": (c_int, [c_int, c_u32, u8p, c_int, c_int, u8p, c_int,
                                        ctypes.POINTER(c_int)]),
+        "dls_order_trim": (c_int, [c_int, c_u32, u8p, c_int, c_int, c_int, u8p, c_int,
+                                   ctypes.POINTER(c_int)]),
         "dls_extend_prefixes": (c_int, [c_int, c_u32, u8p, c_int, u8p, c_int, c_i64,
                                         c_int, u8p, c_i64, i64p, i64p]),
         "dls_sample_prefix": (c_int, [c_int, c_u32, u8p, c_int, c_int, u32p, c_i64,

@@ -5,7 +5,8 @@ snapshot stack's cap.
 Every trial counts the same squares: the base prefixes are extended to the
 candidate split depth with the same leading cells, and only the cells after
 the split are reordered (counts do not depend on their order; Section 2.3
-shows the search size does).  A trial is timed as a CUDA-graph launch
+shows the search size does), and every order is shortened by dls_order_trim
+(a final run of cells forced by their columns or rows is dropped).  A trial is timed as a CUDA-graph launch
 (dls_plan_*) with CUDA events; all trials must report the same total.
 
     best = tune(n, flags, order, base, depths=[...])
@@ -21,8 +22,8 @@ import time
 import numpy as np
 
 from . import (Launch, Plan, ORDER_HEURISTIC, ORDER_HEURISTIC_SQ, ORDER_MD_AD_ROWS,
-               KERNEL_PERSISTENT,
-               extend_prefixes, order_complete)
+               KERNEL_PERSISTENT, TAIL_WINDOW,
+               extend_prefixes, order_complete, order_trim)
 
 SUFFIXES = {"given": None, "heuristic": ORDER_HEURISTIC, "heuristic_sq": ORDER_HEURISTIC_SQ}
 SHAPES = [
@@ -49,7 +50,7 @@ _CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "aut
 
 def _key(n, flags, order, base, depths, suffixes, shapes, dev):
     h = hashlib.sha1()
-    h.update(repr((n, flags, list(depths), list(suffixes), shapes, dev)).encode())
+    h.update(repr((n, flags, list(depths), list(suffixes), shapes, dev, TAIL_WINDOW)).encode())
     h.update(np.ascontiguousarray(order, dtype=np.uint8).tobytes())
     b = np.ascontiguousarray(base, dtype=np.uint8)
     h.update(repr(b.shape).encode())
@@ -73,11 +74,15 @@ def _save_cache(c):
     os.replace(tmp, _CACHE)
 
 
-def build_problem(n, flags, order, base, depth, suffix):
-    """(full order, prefixes) for one split depth and suffix rule."""
+def build_problem(n, flags, order, base, depth, suffix, window=TAIL_WINDOW):
+    """(order, prefixes, parents) for one split depth and suffix rule.  The
+    order is then shortened by dls_order_trim (window None: not), which
+    leaves every count and the prefixes as they are."""
     order = np.ascontiguousarray(order, dtype=np.uint8).reshape(-1, 2)
     if SUFFIXES[suffix] is not None:
         order = order_complete(n, flags, order, depth, SUFFIXES[suffix])
+    if window is not None:
+        order = order_trim(n, flags, order, depth, window)
     pre, par = extend_prefixes(n, flags, order, base, depth)
     return order, pre, par
 

@@ -225,6 +225,25 @@ double estimate_nodes(const OrderInfo &info, const uint8_t *prefix, int depth, u
   return probes > 0 ? sum / probes : 0.0;
 }
 
+// ------------------------------------------------------ order trimming --
+
+// Cells at the end of `cells` that share coordinate `axis` (0 row, 1 column)
+// with the last cell and lie on no diagonal (with the diagonal flag), at
+// most `most`.
+static int tail_run(const std::vector<std::pair<int, int>> &cells, int axis, int n,
+                    bool diag, int most) {
+  if (cells.empty()) return 0;
+  const auto key = [axis](const std::pair<int, int> &c) { return axis ? c.second : c.first; };
+  const int line = key(cells.back());
+  int k = 0;
+  for (auto it = cells.rbegin(); it != cells.rend() && k < most; ++it) {
+    if (key(*it) != line) break;
+    if (diag && (it->first == it->second || it->first + it->second == n - 1)) break;
+    ++k;
+  }
+  return k;
+}
+
 }  // namespace dls
 
 using namespace dls;
@@ -326,6 +345,52 @@ int dls_order_complete(int n, uint32_t flags, const uint8_t *order, int keep,
       for (int j = 0; j < w; ++j) add(i, j);
   } else {
     return DLS_ERR_BAD_ARG;
+  }
+  *len_out = (int)cells.size();
+  if ((int)cells.size() > cap) return DLS_ERR_CAPACITY;
+  for (size_t t = 0; t < cells.size(); ++t) {
+    ij_out[2 * t] = (uint8_t)cells[t].first;
+    ij_out[2 * t + 1] = (uint8_t)cells[t].second;
+  }
+  return DLS_OK;
+}
+
+int dls_order_trim(int n, uint32_t flags, const uint8_t *order, int order_len, int keep,
+                   int window, uint8_t *ij_out, int cap, int *len_out) {
+  if (n < 1 || n > DLS_MAX_N) return DLS_ERR_INVALID_N;
+  if (len_out == nullptr || cap < 0 || (cap > 0 && ij_out == nullptr) || window < 0)
+    return DLS_ERR_BAD_ARG;
+  OrderInfo info;
+  int rc = validate_order(n, flags, order, order_len, &info);
+  if (rc) return rc;
+  if (keep < 0 || keep > order_len) return DLS_ERR_BAD_ARG;
+  std::vector<std::pair<int, int>> cells;
+  for (int t = 0; t < order_len; ++t) cells.push_back({info.i[t], info.j[t]});
+  const bool diag = (flags & DLS_DIAGONAL) != 0;
+  if (!(flags & DLS_VSYM) && order_len == n * n && order_len > keep + 1) {
+    const int most = order_len - keep - 1;  // one cell after keep stays
+    const int start = std::max(keep, order_len - window);
+    std::vector<std::pair<int, int>> best;
+    int best_k = 0;  // nothing to drop: the order stays as it is
+    for (int axis = 0; axis < 2; ++axis) {
+      // the window's cells on the last cell's line move to the end
+      const int line = axis ? cells.back().second : cells.back().first;
+      std::vector<std::pair<int, int>> moved(cells.begin(), cells.begin() + start), on;
+      for (int t = start; t < order_len; ++t) {
+        const int c = axis ? cells[t].second : cells[t].first;
+        (c == line ? on : moved).push_back(cells[t]);
+      }
+      moved.insert(moved.end(), on.begin(), on.end());
+      const int k = tail_run(moved, axis, n, diag, most);
+      if (k > best_k) {
+        best_k = k;
+        best.swap(moved);
+      }
+    }
+    if (best_k > 0) {
+      best.resize(best.size() - (size_t)best_k);
+      cells.swap(best);
+    }
   }
   *len_out = (int)cells.size();
   if ((int)cells.size() > cap) return DLS_ERR_CAPACITY;

@@ -26,7 +26,7 @@ work and picks extensions.
 import numpy as np
 
 from . import (DIAGONAL, ORDER_HEURISTIC, ORDER_ROW_MAJOR, count, extend_prefixes,
-               fill_order, order_complete)
+               fill_order, order_complete, order_trim)
 
 
 def _first_cells(n, flags):
@@ -119,7 +119,8 @@ def estimate(n, flags, k, ranks, order_k=None, start_depth=None, min_items=1 << 
     """Section 5.3's estimate from the partial squares selected by `ranks`.
 
     order_k: the first k cells (default: row-major, as in Section 5.3); the
-    completion counts use the Section 2.3 order for the remaining cells.
+    completion counts use the Section 2.3 order for the remaining cells,
+    shortened by dls_order_trim.
     Returns a dict: 'n_k' (exact N^k), 'samples' (the k-cell prefixes),
     'completions' (uint64 per sample), 'mean', 'estimate', 'stderr'."""
     flags = int(flags)
@@ -127,7 +128,8 @@ def estimate(n, flags, k, ranks, order_k=None, start_depth=None, min_items=1 << 
         order_k = fill_order(n, flags, ORDER_ROW_MAJOR)[:k]
     order_k = np.ascontiguousarray(order_k, dtype=np.uint8).reshape(-1, 2)
     samples, n_k = select_by_rank(n, flags, order_k, ranks, start_depth, launch=launch)
-    full = order_complete(n, flags, order_k, len(order_k), ORDER_HEURISTIC)
+    full = order_trim(n, flags, order_complete(n, flags, order_k, len(order_k), ORDER_HEURISTIC),
+                      len(order_k))
     comp = counts_split(n, flags, full, samples, min_items=min_items, launch=launch)
     vals = [int(v) for v in comp]
     m = len(vals)

@@ -20,7 +20,8 @@ import ctypes
 import numpy as np
 
 from . import (_lib, lib, count as dls_count, count_weighted, extend_prefixes, fill_order,
-               order_complete, DIAGONAL, VSYM, ORDER_HOURGLASS, ORDER_HEURISTIC, Launch)
+               order_complete, order_trim, DIAGONAL, VSYM, ORDER_HOURGLASS, ORDER_HEURISTIC,
+               Launch)
 
 
 def hourglass_len(n, vsym=False):
@@ -58,9 +59,7 @@ def count_symmetry_broken(n, flags=DIAGONAL, launch=None, min_items=1 << 20):
     hourglasses.  Returns a dict with the total and the class statistics."""
     import torch
     vsym = bool(flags & VSYM)
-    k = hourglass_len(n, vsym)
-    order = fill_order(n, flags, ORDER_HOURGLASS)
-    order = order_complete(n, flags, order, k, ORDER_HEURISTIC)
+    order, k = hourglass_order(n, flags)
     ident = np.arange(n // 2 if vsym else n, dtype=np.uint8)[None]
     hg, _ = extend_prefixes(n, flags, order, ident, k)
     d_hg = torch.from_numpy(hg).cuda()
@@ -94,11 +93,13 @@ def count_symmetry_broken(n, flags=DIAGONAL, launch=None, min_items=1 << 20):
 def hourglass_order(n, flags):
     """The hourglass cells (row 0, main diagonal, anti-diagonal, last row;
     left half with vertical symmetry) followed by the other cells in the
-    Section 2.3 order.  Returns (order, number of hourglass cells)."""
+    Section 2.3 order, shortened by dls_order_trim (the counts stay the
+    same).  Returns (order, number of hourglass cells)."""
     vsym = bool(flags & VSYM)
     k = hourglass_len(n, vsym)
     order = fill_order(n, flags, ORDER_HOURGLASS)
-    return order_complete(n, flags, order, k, ORDER_HEURISTIC), k
+    order = order_complete(n, flags, order, k, ORDER_HEURISTIC)
+    return order_trim(n, flags, order, k), k
 
 
 def weighted_counter(n, flags, order, k, classes_fn=None, count_fn=None, min_items=1 << 20,

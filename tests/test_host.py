@@ -201,6 +201,38 @@ def test_argument_errors(dls):
     assert e.value.code == 3
 
 
+def test_order_trim_matches_oracle(dls):
+    """dls_order_trim against the oracle's trim_tail (written separately
+    from the same rule) on seeded random and structured orders, every keep
+    and window kind; partial and symmetric orders come back unchanged."""
+    rng = np.random.default_rng(7)
+    dropped = 0
+    for trial in range(600):
+        n = int(rng.integers(2, 11))
+        flags = D if rng.random() < 0.7 else 0
+        if trial % 3 == 0:
+            order = orders.heuristic_complete(n, orders.row0(n), squares=bool(trial % 2))
+        else:
+            cells = [(i, j) for i in range(n) for j in range(n)]
+            order = [cells[k] for k in rng.permutation(len(cells))]
+        keep = int(rng.integers(0, len(order) + 1))
+        window = int(rng.choice([0, 1, 4, 6, 9, 200]))
+        got = [tuple(map(int, c)) for c in dls.order_trim(n, flags, order, keep, window)]
+        want = orders.trim_tail(n, order, keep, window, diagonal=bool(flags))
+        assert got == want, (n, flags, keep, window)
+        dropped += len(order) - len(got)
+    assert dropped > 600
+    part = orders.md_ad_rows(7)[:40]
+    assert [tuple(c) for c in dls.order_trim(7, D, part, 7)] == part
+    vs = orders.md_ad_rows(8, vsym=True)
+    assert [tuple(c) for c in dls.order_trim(8, D | V, vs, 4)] == vs
+    from paper_1709_02599_gb300._lib import DlsError
+    for keep, window in ((-1, 6), (65, 6), (8, -1)):
+        with pytest.raises(DlsError) as e:
+            dls.order_trim(8, D, orders.md_ad_rows(8), keep, window)
+        assert e.value.code == 3
+
+
 def test_fig1_workunit_decomposition(dls, golden):
     """Section 5.2: the order-9 search is cut into workunits by the values of
     the first 10 cells of the Fig. 1 order after row 0.  The library and the

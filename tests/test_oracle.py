@@ -197,3 +197,88 @@ def test_nodes_count_accepted_placements():
     sq = brute.squares(n, True, row0=list(range(n)))
     full = [int(sq[0][i][j]) for (i, j) in order]
     assert oracle.count(n, D, order, full) == (1, 0)
+
+
+# ------------------------------------------------------------ trim_tail --
+# A final run of one line's off-diagonal cells can be dropped from a full
+# order without changing any count (each of them is the last open cell of
+# its column, and the values these force are those the line lacks).  Pinned
+# on known totals and on brute force; and the two conditions of the rule
+# (one line, no diagonal) each matter.
+
+LATIN_ROW0_FIXED = {4: 24, 5: 1344, 6: 1128960}   # Latin squares 576, 161280,
+# 812851200 of orders 4-6 (OEIS A002860), divided by the n! first rows
+
+
+def _orders_to_trim(n, seed, shuffled=8):
+    rng = np.random.default_rng(seed)
+    out = [orders.md_ad_rows(n), orders.row_major(n), orders.hourglass(n),
+           orders.heuristic_complete(n, orders.row0(n)),
+           orders.heuristic_complete(n, orders.row0(n), squares=True)]
+    rest = [(i, j) for i in range(1, n) for j in range(n)]
+    for _ in range(shuffled):
+        out.append(orders.row0(n) + [rest[k] for k in rng.permutation(len(rest))])
+    return out
+
+
+@pytest.mark.parametrize("n", [4, 5, 6])
+def test_trimmed_orders_keep_the_known_totals(golden, n):
+    dropped = 0
+    # (ordinary squares of order 6 take the oracle minutes: orders 4 and 5)
+    for flags in ((D, 0) if n < 6 else (D,)):
+        for order in _orders_to_trim(n, n, 8 if n < 6 else 3):
+            for window in (0, 3, 6, 100):
+                t = orders.trim_tail(n, order, n, window, diagonal=bool(flags))
+                assert t[:n] == order[:n] and set(t) <= set(order) and len(t) > n
+                dropped += len(order) - len(t)
+                got = oracle.count(n, flags, t, orders.identity(n))[0]
+                if flags:
+                    assert got * oracle.multiplier(n, D) == golden["dls_total_%d" % n]
+                else:
+                    assert got == LATIN_ROW0_FIXED[n]
+    assert dropped > 0
+
+
+@pytest.mark.parametrize("n", [4, 5])
+def test_trimmed_orders_per_prefix_by_brute_force(n):
+    # brute force lists whole squares; each prefix of the trimmed order
+    # must have as many completions as squares agree with it on those cells
+    sq = np.array(brute.squares(n, diagonal=True, row0=list(range(n))))
+    for order in _orders_to_trim(n, 10 + n):
+        t = orders.trim_tail(n, order, n, 100)
+        depth = n + 3
+        pre, _ = oracle.extend(n, D, t, np.array([orders.identity(n)], np.uint8), depth)
+        c, _ = oracle.count_many(n, D, t, pre)
+        cells = t[:depth]
+        for p, k in zip(pre, c):
+            match = np.all([sq[:, i, j] == p[q] for q, (i, j) in enumerate(cells)], axis=0)
+            assert int(match.sum()) == int(k)
+
+
+def test_trim_needs_one_line_and_no_diagonal():
+    n = 6
+    ref = _full_count(n, D)
+    # row-major ends with row 5, whose end cell (5, 5) lies on the main
+    # diagonal: the rule drops nothing, and dropping the row anyway (its
+    # diagonal cells unchecked) changes the count
+    rm = orders.row_major(n)
+    assert orders.trim_tail(n, rm, n, 0) == rm
+    assert oracle.count(n, D, rm[:-6], orders.identity(n))[0] != ref
+    # without the diagonal rule the four inner cells of row 5 may go ...
+    inner = [c for c in rm if c not in [(5, 1), (5, 2), (5, 3), (5, 4)]] + \
+        [(5, 1), (5, 2), (5, 3), (5, 4)]
+    t = orders.trim_tail(n, inner, n, 0)
+    assert t == inner[:-4] and oracle.count(n, D, t, orders.identity(n))[0] == ref
+    # ... but a final run on two lines may not: (5, 4) is forced by its
+    # column and (4, 3) by its column only once (5, 3) is placed
+    two = [c for c in rm if c not in [(4, 3), (5, 3), (5, 4)]] + [(5, 3), (4, 3), (5, 4)]
+    assert oracle.count(n, D, two, orders.identity(n))[0] == ref
+    assert oracle.count(n, D, two[:-2], orders.identity(n))[0] != ref
+
+
+def test_trim_leaves_partial_and_symmetric_orders():
+    n = 6
+    part = orders.md_ad_rows(n)[:30]
+    assert orders.trim_tail(n, part, n) == part
+    vs = orders.md_ad_rows(n, vsym=True)
+    assert orders.trim_tail(n, vs, 3, diagonal=True, vsym=True) == vs
