@@ -154,8 +154,15 @@ int dls_order_complete(int n, uint32_t flags, const uint8_t *order, int keep,
  * prefixes made with either order are the same.  The search gets shorter
  * by the dropped cells, and moving the line's cells within the window
  * lets more of them drop (window 0: only the run already at the end).
- * An order with DLS_VSYM, or one that does not list every cell (a partial
- * order, whose count is of partial squares), is copied unchanged.
+ * With DLS_VSYM (left-half cells; Section 5.4) only a row's run drops: each
+ * cell is still the last open cell of its column, and since every full row
+ * holds one value of each pair {v, N-1-v} in its left half and every left
+ * column holds both, the forced values give the run's row one value of
+ * each pair it lacks and none of a pair it has; a column's last left cell
+ * is not forced (either value of a pair may fit).  An order that does not
+ * list every cell (every left-half cell with DLS_VSYM; a partial order,
+ * whose count is of partial squares), or DLS_VSYM with odd N, is copied
+ * unchanged.
  * Writes up to `cap` (i,j) pairs to ij_out and their number to *len_out.
  * Host memory, caller-owned.  Errors: as dls_fill_order, BAD_ORDER for a bad
  * order, BAD_ARG for keep outside [0, order_len] or window < 0. */

@@ -190,14 +190,28 @@ def trim_tail(n, order, keep, window=6, diagonal=True, vsym=False):
     diagonal; the same with the last cell's column; keep the line with the
     longer run (the row on a tie, nothing if both are empty) and drop its
     run, leaving at least one cell after the first `keep`.  Only for an
-    order that lists every cell of a square without vertical symmetry;
-    anything else is returned as it is."""
+    order that lists every cell (every left-half cell with vertical
+    symmetry); anything else is returned as it is.
+
+    Vertical symmetry (Section 5.4: the order lists the left half, the right
+    half is A[i][N-1-j] = N-1-A[i][j]): a row is valid when its left half
+    holds one value of each pair {v, N-1-v}, a column when it holds every
+    value.  A row's run still consists of columns' last open cells.  Take a
+    pair P: the N-1 full rows hold one P value each in their left halves,
+    the N/2 left columns two each (both values), so the left half lacks
+    N - (N-1) - a = 1 - a of them, where a (0 or 1) is the number of P
+    values the run's row already holds -- all in the run's columns, at most
+    one per column.  So the run's row receives one value of each pair it
+    lacks and none of a pair it has: valid, and again unique.  A column's
+    run does not work here: a row's last left cell may take either value of
+    its missing pair, so it is not forced."""
     order = [tuple(map(int, c)) for c in order]
-    if vsym or len(order) != n * n or len(order) <= keep + 1:
+    w = n // 2 if vsym else n
+    if (vsym and n % 2) or len(order) != n * w or len(order) <= keep + 1:
         return order
     start = max(keep, len(order) - window)
     best, best_k = order, 0
-    for axis in (0, 1):
+    for axis in ((0,) if vsym else (0, 1)):
         line = order[-1][axis]
         on = [c for c in order[start:] if c[axis] == line]
         off = [c for c in order[start:] if c[axis] != line]

@@ -367,12 +367,16 @@ int dls_order_trim(int n, uint32_t flags, const uint8_t *order, int order_len, i
   std::vector<std::pair<int, int>> cells;
   for (int t = 0; t < order_len; ++t) cells.push_back({info.i[t], info.j[t]});
   const bool diag = (flags & DLS_DIAGONAL) != 0;
-  if (!(flags & DLS_VSYM) && order_len == n * n && order_len > keep + 1) {
+  const bool vsym = (flags & DLS_VSYM) != 0;
+  const int w = vsym ? n / 2 : n;
+  if (!(vsym && n % 2) && order_len == n * w && order_len > keep + 1) {
     const int most = order_len - keep - 1;  // one cell after keep stays
     const int start = std::max(keep, order_len - window);
     std::vector<std::pair<int, int>> best;
     int best_k = 0;  // nothing to drop: the order stays as it is
-    for (int axis = 0; axis < 2; ++axis) {
+    // with vertical symmetry a row's last left cell is not forced (two
+    // values of a symmetric pair may fit), so only row runs go
+    for (int axis = 0; axis < (vsym ? 1 : 2); ++axis) {
       // the window's cells on the last cell's line move to the end
       const int line = axis ? cells.back().second : cells.back().first;
       std::vector<std::pair<int, int>> moved(cells.begin(), cells.begin() + start), on;

@@ -24,10 +24,12 @@ class Workload:
         assert (prefixes == oracle_prefixes).all()
 
 
-def split(dls, n, flags, after_row0, first_rows=1, kind=None):
+def split(dls, n, flags, after_row0, first_rows=1, kind=None, trim=False):
     """Row 0 identity, every valid prefix `after_row0` cells past row 0.
     kind: None = main diagonal, anti-diagonal, rows; dls.ORDER_ROW_MAJOR;
-    dls.ORDER_HEURISTIC (the Section 2.3 order after row 0)."""
+    dls.ORDER_HEURISTIC (the Section 2.3 order after row 0).  trim: both
+    orders shortened after the prefix (dls_order_trim on the library's side,
+    the oracle's trim_tail on the oracle's)."""
     vs = bool(flags & V)
     if kind is None:
         order = dls.fill_order(n, flags, first_rows=first_rows)
@@ -41,6 +43,10 @@ def split(dls, n, flags, after_row0, first_rows=1, kind=None):
         o_order = orders.heuristic_complete(n, orders.row0(n, vs), bool(flags & D), vs)
     w = len(orders.identity(n, vs))
     depth = min(len(o_order), w + after_row0)
+    if trim:
+        order = dls.order_trim(n, flags, order, depth)
+        o_order = orders.trim_tail(n, o_order, depth, diagonal=bool(flags & D), vsym=vs)
+        assert [tuple(map(int, c)) for c in order] == o_order
     base = np.array([orders.identity(n, vs)], np.uint8)
     pre, _ = dls.extend_prefixes(n, flags, order, base, depth)
     o_pre, _ = oracle.extend(n, flags, o_order, base, depth)

@@ -68,8 +68,8 @@ def test_oracle_sample_is_the_gpu_workload(dls):
             order, pre, par = autotune.build_problem(spec.n, spec.flags, order0, base[idx],
                                                      depth, suffix)
             o_order, o_pre, o_par = spec.oracle_sample(0, spec.units, idx, depth, suffix)
-            # (vertical symmetry: nothing is dropped)
-            assert [tuple(map(int, c)) for c in order] == list(o_order)
+            assert [tuple(map(int, c)) for c in order] == orders.trim_tail(
+                spec.n, o_order, depth, vsym=True)
             assert (pre == o_pre).all() and (par == o_par).all()
 
 

@@ -209,23 +209,25 @@ def test_order_trim_matches_oracle(dls):
     dropped = 0
     for trial in range(600):
         n = int(rng.integers(2, 11))
-        flags = D if rng.random() < 0.7 else 0
+        flags = int(rng.choice([D, 0, D | V, V]))
+        vs = bool(flags & V)
         if trial % 3 == 0:
-            order = orders.heuristic_complete(n, orders.row0(n), squares=bool(trial % 2))
+            order = orders.heuristic_complete(n, orders.row0(n, vs), vsym=vs,
+                                              squares=bool(trial % 2))
         else:
-            cells = [(i, j) for i in range(n) for j in range(n)]
+            cells = [(i, j) for i in range(n) for j in range(n // 2 if vs else n)]
             order = [cells[k] for k in rng.permutation(len(cells))]
         keep = int(rng.integers(0, len(order) + 1))
         window = int(rng.choice([0, 1, 4, 6, 9, 200]))
         got = [tuple(map(int, c)) for c in dls.order_trim(n, flags, order, keep, window)]
-        want = orders.trim_tail(n, order, keep, window, diagonal=bool(flags))
+        want = orders.trim_tail(n, order, keep, window, diagonal=bool(flags & D), vsym=vs)
         assert got == want, (n, flags, keep, window)
         dropped += len(order) - len(got)
     assert dropped > 600
     part = orders.md_ad_rows(7)[:40]
     assert [tuple(c) for c in dls.order_trim(7, D, part, 7)] == part
-    vs = orders.md_ad_rows(8, vsym=True)
-    assert [tuple(c) for c in dls.order_trim(8, D | V, vs, 4)] == vs
+    odd = orders.row_major(7, vsym=True)
+    assert [tuple(c) for c in dls.order_trim(7, D | V, odd, 3)] == odd
     from paper_1709_02599_gb300._lib import DlsError
     for keep, window in ((-1, 6), (65, 6), (8, -1)):
         with pytest.raises(DlsError) as e:

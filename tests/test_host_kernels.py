@@ -90,6 +90,24 @@ def test_kernels_against_oracle(dls, emulated, n, flags, after, kind, step):
     check_counts(emulated, wl, n, flags, shapes)
 
 
+@pytest.mark.parametrize("n,flags,after,kind,step", [
+    (6, D | V, 2, None, 1), (7, D, 14, None, 50), (6, D, 10, "heuristic", 1),
+    (6, V, 4, None, 4)])
+def test_kernels_on_trimmed_orders(dls, emulated, n, flags, after, kind, step):
+    """Every kernel on orders shortened by dls_order_trim, against the oracle
+    on its own trimmed order (counts and nodes) and on the whole order
+    (counts)."""
+    k = {None: None, "heuristic": dls.ORDER_HEURISTIC}[kind]
+    wl = every(gpu_cases.split(dls, n, flags, after, kind=k, trim=True), step)
+    full = every(gpu_cases.split(dls, n, flags, after, kind=k), step)
+    assert len(wl.order) < len(full.order)
+    shapes = [dict(), dict(kernel=1), dict(stack=1), dict(stack_cap=1)]
+    check_counts(emulated, wl, n, flags, shapes)
+    c_full, _ = oracle.count_many(n, flags, full.oracle_order, full.oracle_prefixes, threads=4)
+    rc, res = emulated.count("count", n, flags, wl.order, wl.prefixes)
+    assert rc == 0 and (res[0] == c_full).all()
+
+
 def test_lookahead_and_fused_step(dls, emulated):
     """Where no cell after the prefix lies on a diagonal and without vertical
     symmetry: the lookahead prunes (fewer nodes, same counts); the fused step

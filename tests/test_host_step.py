@@ -120,6 +120,23 @@ def test_step_against_oracle(dls, step_check, tmp_path, n, flags, after, kind):
     check_workload(step_check, tmp_path, wl, n, flags)
 
 
+@pytest.mark.parametrize("n,flags,after,kind", [
+    (6, D | V, 2, None), (6, V, 0, None), (8, D | V, 8, "heuristic"), (7, D, 14, "heuristic"),
+    (6, D, 10, "heuristic"), (6, 0, 3, "row_major"), (7, D, 4, None)])
+def test_step_on_trimmed_orders(dls, step_check, tmp_path, n, flags, after, kind):
+    """Orders shortened by dls_order_trim (the oracle runs its own trim_tail
+    of its order, so node counts compare too); the counts must also be those
+    of the whole order."""
+    k = {None: None, "heuristic": dls.ORDER_HEURISTIC, "row_major": dls.ORDER_ROW_MAJOR}[kind]
+    wl = gpu_cases.split(dls, n, flags, after, kind=k, trim=True)
+    full = gpu_cases.split(dls, n, flags, after, kind=k)
+    assert len(wl.order) < len(full.order) and (wl.prefixes == full.prefixes).all()
+    check_workload(step_check, tmp_path, wl, n, flags)
+    c_trim, _ = oracle.count_many(n, flags, wl.oracle_order, wl.oracle_prefixes, threads=4)
+    c_full, _ = oracle.count_many(n, flags, full.oracle_order, full.oracle_prefixes, threads=4)
+    assert (c_trim == c_full).all()
+
+
 @pytest.mark.parametrize("n,k,depth", [(6, 15, 8), (6, 20, 9), (7, 18, 9), (5, 12, 5)])
 def test_step_on_partial_orders(dls, step_check, tmp_path, n, k, depth):
     """Partial orders (the first k row-major cells, as for Section 5.3's

@@ -276,9 +276,58 @@ def test_trim_needs_one_line_and_no_diagonal():
     assert oracle.count(n, D, two[:-2], orders.identity(n))[0] != ref
 
 
-def test_trim_leaves_partial_and_symmetric_orders():
+def test_trim_leaves_partial_orders():
     n = 6
     part = orders.md_ad_rows(n)[:30]
     assert orders.trim_tail(n, part, n) == part
     vs = orders.md_ad_rows(n, vsym=True)
-    assert orders.trim_tail(n, vs, 3, diagonal=True, vsym=True) == vs
+    assert orders.trim_tail(n, vs[:14], 3, vsym=True) == vs[:14]
+    odd = orders.row_major(5, vsym=True)
+    assert orders.trim_tail(5, odd, 2, vsym=True) == odd
+
+
+def _vsym_orders_to_trim(n, seed, shuffled):
+    rng = np.random.default_rng(seed)
+    w = n // 2
+    out = [orders.md_ad_rows(n, vsym=True), orders.row_major(n, vsym=True),
+           orders.heuristic_complete(n, orders.row0(n, True), vsym=True),
+           orders.heuristic_complete(n, orders.row0(n, True), vsym=True, squares=True)]
+    rest = [(i, j) for i in range(1, n) for j in range(w)]
+    for _ in range(shuffled):
+        out.append(orders.row0(n, True) + [rest[k] for k in rng.permutation(len(rest))])
+    return out
+
+
+@pytest.mark.parametrize("n", [4, 6])
+def test_trimmed_symmetric_orders_by_brute_force(n):
+    # vertically symmetric squares with row 0 the identity, with and without
+    # the diagonal rule, listed by brute force; only row runs may drop
+    dropped = 0
+    for flags in (D | V, V):
+        sq = brute.squares(n, diagonal=bool(flags & D), vsym=True, row0=list(range(n)))
+        for order in _vsym_orders_to_trim(n, n, 6):
+            for window in (0, 3, 100):
+                t = orders.trim_tail(n, order, n // 2, window, diagonal=bool(flags & D),
+                                     vsym=True)
+                assert t[:n // 2] == order[:n // 2] and len(t) > n // 2
+                dropped += len(order) - len(t)
+                assert oracle.count(n, flags, t, orders.identity(n, True))[0] == len(sq)
+    assert dropped > 0
+
+
+def test_trimmed_symmetric_order8_and_a_column_run():
+    n, flags = 8, D | V
+    ref = _full_count(n, flags)
+    for order in _vsym_orders_to_trim(n, 8, 0)[::2] + _vsym_orders_to_trim(n, 8, 0)[3:]:
+        t = orders.trim_tail(n, order, 4, 6, vsym=True)
+        assert oracle.count(n, flags, t, orders.identity(n, True))[0] == ref
+    # a final run down a left column is not forced by its rows: dropping it
+    # changes the count; the rule drops only its last cell (a run of one
+    # cell is also a row's run)
+    n, flags = 6, V
+    ref = _full_count(n, flags)
+    col = [c for c in orders.row_major(n, vsym=True) if c not in [(3, 1), (4, 1)]]
+    col += [(3, 1), (4, 1)]
+    assert orders.trim_tail(n, col, 3, 0, diagonal=False, vsym=True) == col[:-1]
+    assert oracle.count(n, flags, col[:-1], orders.identity(n, True))[0] == ref
+    assert oracle.count(n, flags, col[:-2], orders.identity(n, True))[0] != ref
