@@ -286,8 +286,8 @@ typedef struct {
                              it -- the next iteration's move, so the counts,
                              nodes and stack entries are unchanged and the
                              iterations fewer; only where no cell after the
-                             prefix lies on a diagonal, without DLS_VSYM and
-                             without the lookahead.  1 = on (BAD_ARG where it
+                             prefix lies on a diagonal and without the
+                             lookahead.  1 = on (BAD_ARG where it
                              does not apply), -1 = off, 0 = on where it
                              applies (default)                              */
     int64_t budget;       /* stop early after this many search iterations per

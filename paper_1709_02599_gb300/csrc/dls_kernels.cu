@@ -1218,7 +1218,8 @@ static const void *pick_snapshot2(bool plain, bool nodes, bool dg) {
                : snapshot_ptr<VSYM, false, false, WIDE>(plain);
 }
 
-// the fused step or the lookahead (no diagonal words, no vertical symmetry)
+// the fused step (no diagonal words) or the lookahead (no diagonal words,
+// no vertical symmetry)
 template <bool WIDE>
 static const void *pick_snapshot_fl(bool plain, bool nodes, bool la) {
   if (!la && plain) return nodes ? (const void *)k_plain_snap<false, true, false, true, WIDE>
@@ -1229,12 +1230,20 @@ static const void *pick_snapshot_fl(bool plain, bool nodes, bool la) {
                : (const void *)k_snapshot<false, false, false, true, false, WIDE>;
 }
 
+static const void *pick_snapshot_vsym_fu(bool plain, bool nodes) {
+  if (plain) return nodes ? (const void *)k_plain_snap<true, true, false, true>
+                          : (const void *)k_plain_snap<true, false, false, true>;
+  return nodes ? (const void *)k_snapshot<true, true, false, false, true>
+               : (const void *)k_snapshot<true, false, false, false, true>;
+}
+
 // dg: some cell at or after the prefix depth lies on a diagonal (the
 // diagonal words change during the search); la: the persistent kernel with
-// the lookahead; fu: the fused step (both: no diagonal words, no vertical
-// symmetry only); wide: the wide-word search of order 9
+// the lookahead (no diagonal words, no vertical symmetry); fu: the fused
+// step (no diagonal words); wide: the wide-word search of order 9
 static const void *pick_snapshot(bool plain, bool vsym, bool wide, bool nodes, bool dg, bool la,
                                  bool fu) {
+  if (fu && vsym) return pick_snapshot_vsym_fu(plain, nodes);
   if (fu || la) return wide ? pick_snapshot_fl<true>(plain, nodes, la)
                             : pick_snapshot_fl<false>(plain, nodes, la);
   if (vsym) return pick_snapshot2<true, false>(plain, nodes, dg);
@@ -1424,9 +1433,9 @@ static int prepare_launch(int n, uint32_t flags, const uint8_t *order, int order
   const bool dgw = diagonal_cells_after(info, n, flags, depth);
   const bool la = snap && !plain && sh.lookahead && !dgw && !vsym;
   if (sh.lookahead && !la) return DLS_ERR_BAD_ARG;
-  // the fused step: snapshot search without diagonal words and without
-  // vertical symmetry; not with the lookahead
-  const bool fu_fits = snap && !dgw && !vsym && !la;
+  // the fused step: snapshot search without diagonal words; not with the
+  // lookahead
+  const bool fu_fits = snap && !dgw && !la;
   if (sh.fuse == 1 && !fu_fits) return DLS_ERR_BAD_ARG;
   const bool fu = fu_fits && (sh.fuse == 1 || (sh.fuse == 0 && kFuseByDefault));
   pr->fused = fu;

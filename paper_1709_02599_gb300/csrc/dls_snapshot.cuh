@@ -149,6 +149,71 @@ __device__ __forceinline__ void snap_place(Words<true> &w, uint32_t rs, uint32_t
   }
 }
 
+// Shared-memory accesses under a predicate.  On the GPU they are single
+// predicated instructions (a C++ `if` around them would become a branch,
+// and the lanes of a warp would split); a lane whose predicate is off makes
+// no access and its registers keep their values.
+#ifdef __CUDA_ARCH__
+// (the base's shared-window address is loop-invariant and computed once)
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void st_shared_if(bool c, uint4 *base, int k, uint4 v) {
+  asm volatile(
+      "{\n .reg .pred q;\n setp.ne.u32 q, %0, 0;\n"
+      " @q st.shared.v4.u32 [%1], {%2, %3, %4, %5};\n}\n" ::"r"((uint32_t)c),
+      "r"(smem_addr(base) + (uint32_t)k * 16u), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+      : "memory");
+}
+__device__ __forceinline__ void st_shared_if(bool c, uint32_t *base, int k, uint32_t v) {
+  asm volatile(
+      "{\n .reg .pred q;\n setp.ne.u32 q, %0, 0;\n"
+      " @q st.shared.u32 [%1], %2;\n}\n" ::"r"((uint32_t)c),
+      "r"(smem_addr(base) + (uint32_t)k * 4u), "r"(v)
+      : "memory");
+}
+__device__ __forceinline__ void ld_shared_if(bool c, const uint4 *base, int k, uint4 &v) {
+  asm volatile(
+      "{\n .reg .pred q;\n setp.ne.u32 q, %4, 0;\n"
+      " @q ld.shared.v4.u32 {%0, %1, %2, %3}, [%5];\n}\n"
+      : "+r"(v.x), "+r"(v.y), "+r"(v.z), "+r"(v.w)
+      : "r"((uint32_t)c), "r"(smem_addr(base) + (uint32_t)k * 16u)
+      : "memory");
+}
+__device__ __forceinline__ void ld_shared_if(bool c, const uint2 *base, int k, uint2 &v) {
+  asm volatile(
+      "{\n .reg .pred q;\n setp.ne.u32 q, %2, 0;\n"
+      " @q ld.shared.v2.u32 {%0, %1}, [%3];\n}\n"
+      : "+r"(v.x), "+r"(v.y)
+      : "r"((uint32_t)c), "r"(smem_addr(base) + (uint32_t)k * 8u)
+      : "memory");
+}
+__device__ __forceinline__ void ld_shared_if(bool c, const uint32_t *base, int k, uint32_t &v) {
+  asm volatile(
+      "{\n .reg .pred q;\n setp.ne.u32 q, %1, 0;\n"
+      " @q ld.shared.u32 %0, [%2];\n}\n"
+      : "+r"(v)
+      : "r"((uint32_t)c), "r"(smem_addr(base) + (uint32_t)k * 4u)
+      : "memory");
+}
+#else
+inline void st_shared_if(bool c, uint4 *base, int k, uint4 v) {
+  if (c) base[k] = v;
+}
+inline void st_shared_if(bool c, uint32_t *base, int k, uint32_t v) {
+  if (c) base[k] = v;
+}
+inline void ld_shared_if(bool c, const uint4 *base, int k, uint4 &v) {
+  if (c) v = base[k];
+}
+inline void ld_shared_if(bool c, const uint2 *base, int k, uint2 &v) {
+  if (c) v = base[k];
+}
+inline void ld_shared_if(bool c, const uint32_t *base, int k, uint32_t &v) {
+  if (c) v = base[k];
+}
+#endif
+
 // One search iteration.  Returns true when the lane's work is finished.
 //   nv = lowest untried candidate at p (Algorithm 4's L & -L), removed from L
 //   place nv; candidates of the next cell: at the last cell their popcount
@@ -156,18 +221,20 @@ __device__ __forceinline__ void snap_place(Words<true> &w, uint32_t rs, uint32_t
 //   no dead end: if candidates remain at p, the state before placing nv is
 //   pushed as an entry; descend
 //   dead end or leaf: resume at p itself if candidates remain there (that
-//   state is the entry just written, read back), else at the deepest entry.
+//   state is still in registers), else at the deepest entry.
 // ovf is set (and the stack index held at cap, so every access stays in the
 // lane's cap + 2 slots) if a lane ever needs more entries than cap -- which
-// the bound on cap excludes.
+// the bound on cap excludes, and which a capped stack turns into a deferred
+// prefix.
 // LA (lookahead, Section 2.4.2; only without diagonal words and without
 // vertical symmetry): the cell after the next one must still have a
 // candidate, or the placement is a dead end already -- placing the next cell
 // only removes candidates.  Its field shifts are in dm (the diagonal masks
 // are not needed there).
-// FU (fused forced placement; same restriction, dm as for LA): when the next
-// cell is left with exactly one candidate and is not the last cell, that
-// value is placed in the same iteration and the lane moves two cells on.
+// FU (fused forced placement; no diagonal words, dm as for LA; with or
+// without vertical symmetry): when the next cell is left with exactly one
+// candidate and is not the last cell, that value is placed in the same
+// iteration and the lane moves two cells on.
 // It is the move the next iteration would make -- a single candidate makes
 // no entry -- so the counts, the nodes and the entries are those of the
 // plain step; only the iterations are fewer.  On the order-8 split after
@@ -177,7 +244,7 @@ template <bool VSYM, bool NODES, bool DG, bool LA = false, bool FU = false>
 __device__ __forceinline__ bool snap_step(SnapLane &s, const Geo &g, const SnapStack &st,
                                           const SnapTable &tb, unsigned B, uint32_t &ovf) {
   static_assert(!LA || (!DG && !VSYM), "lookahead: no diagonal words, no symmetry");
-  static_assert(!FU || (!DG && !VSYM && !LA), "fused step: no diagonal words, no symmetry");
+  static_assert(!FU || (!DG && !LA), "fused step: no diagonal words, no lookahead");
   const uint32_t nv = s.L & (0u - s.L);
   const uint32_t Lr = s.L ^ nv;
   const bool keep = Lr != 0u;
@@ -192,8 +259,8 @@ __device__ __forceinline__ bool snap_step(SnapLane &s, const Geo &g, const SnapS
     // one candidate at q (q not the last cell): place it too (placing 0
     // changes nothing); L1 becomes the candidates of the cell after q
     const bool f = q != g.last && L1 != 0u && (L1 & (L1 - 1u)) == 0u;
-    snap_place<false, false>(s.w, s.sh.z, s.sh.w, 0u, f ? L1 : 0u, g);
-    const uint32_t L2 = snap_cands<false, false>(s.w, s.dm.x, s.dm.y, 0u, g);
+    snap_place<VSYM, false>(s.w, s.sh.z, s.sh.w, 0u, f ? L1 : 0u, g);
+    const uint32_t L2 = snap_cands<VSYM, false>(s.w, s.dm.x, s.dm.y, 0u, g);
     if (NODES) s.nodes += f ? 1u : 0u;
     L1 = f ? L2 : L1;
     q = f ? q + 1 : q;
@@ -204,37 +271,40 @@ __device__ __forceinline__ bool snap_step(SnapLane &s, const Geo &g, const SnapS
   if (NODES) s.nodes += leaves;
   bool dead = leaf || L1 == 0u;
   if (LA) dead = dead || snap_cands<false, false>(s.w, s.dm.x, s.dm.y, 0u, g) == 0u;
-  // entry e lives in slot e + 1 (slot 0 is never live, slot cap + 1 is
-  // spare): the state before placing nv is written to the first free slot
-  // every iteration; a push keeps it
-  st.sa[(s.sp + 1) * (int)B] = make_uint4((uint32_t)R0, (uint32_t)(R0 >> 32), (uint32_t)C0,
-                                          (uint32_t)(C0 >> 32));
-  st.sw[(s.sp + 1) * (int)B] = snap_pack<VSYM>(DG ? dg0 : 0u, s.p, Lr);
-  // a dead end resumes the entry just written if candidates remain at p,
-  // else the deepest live one (read back after the write; used only on a
-  // dead end).  A lane that finishes -- no candidate left, no live entry --
-  // reads the entry just written as well, so that every position read back
-  // is a valid one (it indexes the position table below).
-  const int rd = (keep || s.sp <= s.bot) ? s.sp + 1 : s.sp;
-  const uint4 ea = st.sa[rd * (int)B];
-  const uint32_t ew = st.sw[rd * (int)B];
+  // entry e lives in slot e + 1 (slot 0 is never live; a full stack pushes
+  // into the spare slot cap + 1, which the index clamp below never makes
+  // live).  Only a push writes its entry (the state before placing nv); only
+  // a move back to an older cell reads one, loaded over the registers that
+  // hold the state before the placement -- so a dead end with candidates
+  // left at p resumes from those registers, and a lane that finishes (no
+  // candidate left, no live entry) stays on p; only a move to another
+  // position reads a table row.  Every access is one predicated
+  // shared-memory instruction: the step has no branch.
+  uint4 e = make_uint4((uint32_t)R0, (uint32_t)(R0 >> 32), (uint32_t)C0, (uint32_t)(C0 >> 32));
+  uint32_t ew = snap_pack<VSYM>(DG ? dg0 : 0u, s.p, Lr);
   const bool push = keep && !dead;
   const bool pop = dead && !keep && has;
   ovf |= (push && s.sp >= st.cap) ? 1u : 0u;
+  st_shared_if(push, st.sa, (s.sp + 1) * (int)B, e);
+  st_shared_if(push, st.sw, (s.sp + 1) * (int)B, ew);
+  ld_shared_if(pop, st.sa, s.sp * (int)B, e);
+  ld_shared_if(pop, st.sw, s.sp * (int)B, ew);
   uint32_t edg, eL;
   int ep;
   snap_unpack<VSYM>(ew, g.n, edg, ep, eL);
-  const unsigned long long eR = ((unsigned long long)ea.y << 32) | ea.x;
-  const unsigned long long eC = ((unsigned long long)ea.w << 32) | ea.z;
+  const unsigned long long eR = ((unsigned long long)e.y << 32) | e.x;
+  const unsigned long long eC = ((unsigned long long)e.w << 32) | e.z;
   s.w.R = dead ? eR : s.w.R;
   s.w.C = dead ? eC : s.w.C;
   if (DG) s.w.dg = dead ? edg : s.w.dg;
   s.L = dead ? eL : L1;
-  s.p = dead ? ep : q;
+  const int np = dead ? ep : q;
+  const bool moved = np != s.p;
+  s.p = np;
   s.sp = min(s.sp + (push ? 1 : 0) - (pop ? 1 : 0), st.cap);
   // table row of the new position, for the next iteration
-  s.sh = tb.sh[s.p];
-  s.dm = tb.dm[s.p];
+  ld_shared_if(moved, tb.sh, s.p, s.sh);
+  ld_shared_if(moved, tb.dm, s.p, s.dm);
   return dead && !keep && !has;
 }
 
@@ -306,68 +376,14 @@ __device__ __forceinline__ uint32_t bcands(uint32_t R0, uint32_t R1, uint32_t C0
   return all & ~(__byte_perm(R0, R1, sr) | __byte_perm(C0, C1, sc));
 }
 
-// Shared-memory accesses under a predicate.  On the GPU they are single
-// predicated instructions (a C++ `if` around them would become a branch,
-// and the lanes of a warp would split); a lane whose predicate is off makes
-// no access and its registers keep their values.
-#ifdef __CUDA_ARCH__
-// (the base's shared-window address is loop-invariant and computed once)
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void st_shared_if(bool c, uint4 *base, int k, uint4 v) {
-  asm volatile(
-      "{\n .reg .pred q;\n setp.ne.u32 q, %0, 0;\n"
-      " @q st.shared.v4.u32 [%1], {%2, %3, %4, %5};\n}\n" ::"r"((uint32_t)c),
-      "r"(smem_addr(base) + (uint32_t)k * 16u), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
-      : "memory");
-}
-__device__ __forceinline__ void st_shared_if(bool c, uint32_t *base, int k, uint32_t v) {
-  asm volatile(
-      "{\n .reg .pred q;\n setp.ne.u32 q, %0, 0;\n"
-      " @q st.shared.u32 [%1], %2;\n}\n" ::"r"((uint32_t)c),
-      "r"(smem_addr(base) + (uint32_t)k * 4u), "r"(v)
-      : "memory");
-}
-__device__ __forceinline__ void ld_shared_if(bool c, const uint4 *base, int k, uint4 &v) {
-  asm volatile(
-      "{\n .reg .pred q;\n setp.ne.u32 q, %4, 0;\n"
-      " @q ld.shared.v4.u32 {%0, %1, %2, %3}, [%5];\n}\n"
-      : "+r"(v.x), "+r"(v.y), "+r"(v.z), "+r"(v.w)
-      : "r"((uint32_t)c), "r"(smem_addr(base) + (uint32_t)k * 16u)
-      : "memory");
-}
-__device__ __forceinline__ void ld_shared_if(bool c, const uint32_t *base, int k, uint32_t &v) {
-  asm volatile(
-      "{\n .reg .pred q;\n setp.ne.u32 q, %1, 0;\n"
-      " @q ld.shared.u32 %0, [%2];\n}\n"
-      : "+r"(v)
-      : "r"((uint32_t)c), "r"(smem_addr(base) + (uint32_t)k * 4u)
-      : "memory");
-}
-#else
-inline void st_shared_if(bool c, uint4 *base, int k, uint4 v) {
-  if (c) base[k] = v;
-}
-inline void st_shared_if(bool c, uint32_t *base, int k, uint32_t v) {
-  if (c) base[k] = v;
-}
-inline void ld_shared_if(bool c, const uint4 *base, int k, uint4 &v) {
-  if (c) v = base[k];
-}
-inline void ld_shared_if(bool c, const uint32_t *base, int k, uint32_t &v) {
-  if (c) v = base[k];
-}
-#endif
-
 // One search iteration of the byte-word search: the moves of snap_step (see
-// there), with the stack and table traffic cut to what each lane needs.
-// Only a push writes its entry (the state before placing nv); only a move
-// back to an older cell reads one, loaded over the registers that hold the
-// state before the placement -- so a dead end with candidates left at p
-// resumes from those registers, and one select per register picks the new
-// state; only a move to another position reads a table row.  Returns true
-// when the lane's work is finished (then it stays on p with no candidate).
+// there), with its stack and table traffic: only a push writes its entry
+// (the state before placing nv); only a move back to an older cell reads
+// one, loaded over the registers that hold the state before the placement --
+// so a dead end with candidates left at p resumes from those registers, and
+// one select per register picks the new state; only a move to another
+// position reads a table row.  Returns true when the lane's work is finished
+// (then it stays on p with no candidate).
 template <bool NODES, bool DG, bool LA = false, bool FU = false>
 __device__ __forceinline__ bool bsnap_step(BLane &s, const Geo &g, const SnapStack &st,
                                            const BRow *tb, unsigned B, uint32_t &ovf) {

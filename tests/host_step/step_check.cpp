@@ -346,7 +346,7 @@ int main(int argc, char **argv) {
     const int i = ob[2 * t], j = ob[2 * t + 1];
     if (diag && (i == j || i + j == n - 1)) dg = true;
   }
-  if ((mode == 1 || mode == 2) && (dg || vsym)) return 2;
+  if ((mode == 1 && (dg || vsym)) || (mode == 2 && dg)) return 2;
   if (pos) return run_pos(n, flags, mode, ob, pre, depth, sp);
   if (!vsym && n == 9) return run_wide(n, flags, mode, ob, pre, depth, cap);
 
@@ -440,7 +440,8 @@ int main(int argc, char **argv) {
         if (mode == 1)
           done = search<false, false, true, false>(s, g, st, tb, len, run);
         else if (mode == 2)
-          done = search<false, false, false, true>(s, g, st, tb, len, run);
+          done = vsym ? search<true, false, false, true>(s, g, st, tb, len, run)
+                      : search<false, false, false, true>(s, g, st, tb, len, run);
         else if (vsym)
           done = dg ? search<true, true, false, false>(s, g, st, tb, len, run)
                     : search<true, false, false, false>(s, g, st, tb, len, run);

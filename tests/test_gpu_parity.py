@@ -183,10 +183,11 @@ def test_fused_step_where_it_applies(dls):
     """The fused step (a following cell with one candidate is placed in the
     same iteration) makes the next iteration's move early: counts and node
     counts equal the oracle's, with the step on and off, in the persistent
-    and plain kernels; refused where diagonal words or vertical symmetry
-    are in play, and with the lookahead."""
+    and plain kernels, with and without vertical symmetry; refused where
+    diagonal words are in play, and with the lookahead."""
     for n, flags, after, kind in ((7, D, 14, dls.ORDER_HEURISTIC), (6, D, 10, dls.ORDER_HEURISTIC),
-                                  (6, 0, 3, None), (5, 0, 4, None), (6, 0, 8, None)):
+                                  (6, 0, 3, None), (5, 0, 4, None), (6, 0, 8, None),
+                                  (8, D | V, 8, None), (6, V, 0, None)):
         wl = gpu_cases.split(dls, n, flags, after, kind=kind)
         ref_c, ref_n = oracle.count_many(n, flags, wl.oracle_order, wl.oracle_prefixes,
                                          threads=THREADS)

@@ -109,15 +109,20 @@ def test_kernels_on_trimmed_orders(dls, emulated, n, flags, after, kind, step):
 
 
 def test_lookahead_and_fused_step(dls, emulated):
-    """Where no cell after the prefix lies on a diagonal and without vertical
-    symmetry: the lookahead prunes (fewer nodes, same counts); the fused step
-    keeps the counts and the nodes."""
+    """Where no cell after the prefix lies on a diagonal: the lookahead
+    (without vertical symmetry) prunes (fewer nodes, same counts); the fused
+    step (also with it) keeps the counts and the nodes."""
     for n, flags, after, kind, step in ((7, D, 14, dls.ORDER_HEURISTIC, 30),
-                                        (6, 0, 8, None, 1000), (5, 0, 4, None, 1)):
+                                        (6, 0, 8, None, 1000), (5, 0, 4, None, 1),
+                                        (8, D | V, 8, None, 4), (6, V, 0, None, 1)):
         wl = every(gpu_cases.split(dls, n, flags, after, kind=kind), step)
         check_counts(emulated, wl, n, flags,
                      [dict(fuse=1), dict(fuse=1, kernel=1), dict(fuse=1, block_threads=32,
                                                                  check_every=1)])
+        if flags & V:
+            rc, _ = emulated.count("count", n, flags, wl.order, wl.prefixes, lookahead=1)
+            assert rc == ERR_BAD_ARG
+            continue
         check_counts(emulated, wl, n, flags,
                      [dict(lookahead=1), dict(lookahead=1, block_threads=32, check_every=1)],
                      nodes_exact=False)

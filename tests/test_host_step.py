@@ -91,7 +91,7 @@ def check_workload(exe, tmp_path, wl, n, flags):
     cap = entry_bound(wl.order, n, flags, depth)
     diag_after = bool(flags & D) and any(int(i) == int(j) or int(i) + int(j) == n - 1
                                          for i, j in wl.order[depth:])
-    modes = [0] if (diag_after or flags & V) else [0, 1, 2]
+    modes = [0] if diag_after else ([0, 2] if flags & V else [0, 1, 2])
     iters = {}
     for mode in modes:
         c, nd, info = run_step(exe, tmp_path, n, flags, mode, wl.order, wl.prefixes, depth, cap)
