@@ -289,7 +289,9 @@ typedef struct {
                              prefix lies on a diagonal and without the
                              lookahead.  1 = on (BAD_ARG where it
                              does not apply), -1 = off, 0 = on where it
-                             applies (default)                              */
+                             applies, except with DLS_VSYM (default; with
+                             the mirrored words the fused placement costs
+                             more than it saves there)                      */
     int64_t budget;       /* stop early after this many search iterations per
                              lane (the lanes of a warp step together; 0 = no
                              limit) -- see "Stopping early" below          */

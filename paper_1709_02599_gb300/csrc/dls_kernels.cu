@@ -1437,7 +1437,9 @@ static int prepare_launch(int n, uint32_t flags, const uint8_t *order, int order
   // lookahead
   const bool fu_fits = snap && !dgw && !la;
   if (sh.fuse == 1 && !fu_fits) return DLS_ERR_BAD_ARG;
-  const bool fu = fu_fits && (sh.fuse == 1 || (sh.fuse == 0 && kFuseByDefault));
+  // (by default not with vertical symmetry: there the second placement, with
+  // its mirrored words, costs more than the iterations it saves)
+  const bool fu = fu_fits && (sh.fuse == 1 || (sh.fuse == 0 && kFuseByDefault && !vsym));
   pr->fused = fu;
   pr->wide = snap && wide;
   pr->fn = snap ? pick_snapshot(plain, vsym, pr->wide, d_nodes != nullptr, dgw, la, fu)

@@ -180,14 +180,6 @@ __device__ __forceinline__ void ld_shared_if(bool c, const uint4 *base, int k, u
       : "r"((uint32_t)c), "r"(smem_addr(base) + (uint32_t)k * 16u)
       : "memory");
 }
-__device__ __forceinline__ void ld_shared_if(bool c, const uint2 *base, int k, uint2 &v) {
-  asm volatile(
-      "{\n .reg .pred q;\n setp.ne.u32 q, %2, 0;\n"
-      " @q ld.shared.v2.u32 {%0, %1}, [%3];\n}\n"
-      : "+r"(v.x), "+r"(v.y)
-      : "r"((uint32_t)c), "r"(smem_addr(base) + (uint32_t)k * 8u)
-      : "memory");
-}
 __device__ __forceinline__ void ld_shared_if(bool c, const uint32_t *base, int k, uint32_t &v) {
   asm volatile(
       "{\n .reg .pred q;\n setp.ne.u32 q, %1, 0;\n"
@@ -206,9 +198,6 @@ inline void st_shared_if(bool c, uint32_t *base, int k, uint32_t v) {
 inline void ld_shared_if(bool c, const uint4 *base, int k, uint4 &v) {
   if (c) v = base[k];
 }
-inline void ld_shared_if(bool c, const uint2 *base, int k, uint2 &v) {
-  if (c) v = base[k];
-}
 inline void ld_shared_if(bool c, const uint32_t *base, int k, uint32_t &v) {
   if (c) v = base[k];
 }
@@ -221,7 +210,7 @@ inline void ld_shared_if(bool c, const uint32_t *base, int k, uint32_t &v) {
 //   no dead end: if candidates remain at p, the state before placing nv is
 //   pushed as an entry; descend
 //   dead end or leaf: resume at p itself if candidates remain there (that
-//   state is still in registers), else at the deepest entry.
+//   state is the entry just written, read back), else at the deepest entry.
 // ovf is set (and the stack index held at cap, so every access stays in the
 // lane's cap + 2 slots) if a lane ever needs more entries than cap -- which
 // the bound on cap excludes, and which a capped stack turns into a deferred
@@ -271,40 +260,37 @@ __device__ __forceinline__ bool snap_step(SnapLane &s, const Geo &g, const SnapS
   if (NODES) s.nodes += leaves;
   bool dead = leaf || L1 == 0u;
   if (LA) dead = dead || snap_cands<false, false>(s.w, s.dm.x, s.dm.y, 0u, g) == 0u;
-  // entry e lives in slot e + 1 (slot 0 is never live; a full stack pushes
-  // into the spare slot cap + 1, which the index clamp below never makes
-  // live).  Only a push writes its entry (the state before placing nv); only
-  // a move back to an older cell reads one, loaded over the registers that
-  // hold the state before the placement -- so a dead end with candidates
-  // left at p resumes from those registers, and a lane that finishes (no
-  // candidate left, no live entry) stays on p; only a move to another
-  // position reads a table row.  Every access is one predicated
-  // shared-memory instruction: the step has no branch.
-  uint4 e = make_uint4((uint32_t)R0, (uint32_t)(R0 >> 32), (uint32_t)C0, (uint32_t)(C0 >> 32));
-  uint32_t ew = snap_pack<VSYM>(DG ? dg0 : 0u, s.p, Lr);
+  // entry e lives in slot e + 1 (slot 0 is never live, slot cap + 1 is
+  // spare): the state before placing nv is written to the first free slot
+  // every iteration; a push keeps it
+  st.sa[(s.sp + 1) * (int)B] = make_uint4((uint32_t)R0, (uint32_t)(R0 >> 32), (uint32_t)C0,
+                                          (uint32_t)(C0 >> 32));
+  st.sw[(s.sp + 1) * (int)B] = snap_pack<VSYM>(DG ? dg0 : 0u, s.p, Lr);
+  // a dead end resumes the entry just written if candidates remain at p,
+  // else the deepest live one (read back after the write; used only on a
+  // dead end).  A lane that finishes -- no candidate left, no live entry --
+  // reads the entry just written as well, so that every position read back
+  // is a valid one (it indexes the position table below).
+  const int rd = (keep || s.sp <= s.bot) ? s.sp + 1 : s.sp;
+  const uint4 ea = st.sa[rd * (int)B];
+  const uint32_t ew = st.sw[rd * (int)B];
   const bool push = keep && !dead;
   const bool pop = dead && !keep && has;
   ovf |= (push && s.sp >= st.cap) ? 1u : 0u;
-  st_shared_if(push, st.sa, (s.sp + 1) * (int)B, e);
-  st_shared_if(push, st.sw, (s.sp + 1) * (int)B, ew);
-  ld_shared_if(pop, st.sa, s.sp * (int)B, e);
-  ld_shared_if(pop, st.sw, s.sp * (int)B, ew);
   uint32_t edg, eL;
   int ep;
   snap_unpack<VSYM>(ew, g.n, edg, ep, eL);
-  const unsigned long long eR = ((unsigned long long)e.y << 32) | e.x;
-  const unsigned long long eC = ((unsigned long long)e.w << 32) | e.z;
+  const unsigned long long eR = ((unsigned long long)ea.y << 32) | ea.x;
+  const unsigned long long eC = ((unsigned long long)ea.w << 32) | ea.z;
   s.w.R = dead ? eR : s.w.R;
   s.w.C = dead ? eC : s.w.C;
   if (DG) s.w.dg = dead ? edg : s.w.dg;
   s.L = dead ? eL : L1;
-  const int np = dead ? ep : q;
-  const bool moved = np != s.p;
-  s.p = np;
+  s.p = dead ? ep : q;
   s.sp = min(s.sp + (push ? 1 : 0) - (pop ? 1 : 0), st.cap);
   // table row of the new position, for the next iteration
-  ld_shared_if(moved, tb.sh, s.p, s.sh);
-  ld_shared_if(moved, tb.dm, s.p, s.dm);
+  s.sh = tb.sh[s.p];
+  s.dm = tb.dm[s.p];
   return dead && !keep && !has;
 }
 
@@ -377,13 +363,15 @@ __device__ __forceinline__ uint32_t bcands(uint32_t R0, uint32_t R1, uint32_t C0
 }
 
 // One search iteration of the byte-word search: the moves of snap_step (see
-// there), with its stack and table traffic: only a push writes its entry
-// (the state before placing nv); only a move back to an older cell reads
-// one, loaded over the registers that hold the state before the placement --
-// so a dead end with candidates left at p resumes from those registers, and
-// one select per register picks the new state; only a move to another
-// position reads a table row.  Returns true when the lane's work is finished
-// (then it stays on p with no candidate).
+// there), with the stack and table traffic cut to what each lane needs.
+// Only a push writes its entry (the state before placing nv); only a move
+// back to an older cell reads one, loaded over the registers that hold the
+// state before the placement -- so a dead end with candidates left at p
+// resumes from those registers, and one select per register picks the new
+// state; only a move to another position reads a table row.  Returns true
+// when the lane's work is finished (then it stays on p with no candidate).
+// (The same predicated traffic in snap_step, with field shifts and vertical
+// symmetry, measured 2 % slower than its unconditional write and read.)
 template <bool NODES, bool DG, bool LA = false, bool FU = false>
 __device__ __forceinline__ bool bsnap_step(BLane &s, const Geo &g, const SnapStack &st,
                                            const BRow *tb, unsigned B, uint32_t &ovf) {

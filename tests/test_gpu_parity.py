@@ -196,8 +196,9 @@ def test_fused_step_where_it_applies(dls):
         for sh in (dict(fuse=1), dict(fuse=-1), dict(fuse=1, kernel=dls.KERNEL_PLAIN),
                    dict(fuse=1, block_threads=32, check_every=1), dict()):
             launch = dls.Launch(**sh)
+            on = sh.get("fuse", 0) == 1 or (sh.get("fuse", 0) == 0 and not flags & V)
             assert dls.describe_launch(n, flags, wl.order, depth, len(t),
-                                       launch)["fused"] == (sh.get("fuse", 0) >= 0)
+                                       launch)["fused"] == on
             nodes = torch.zeros(1, dtype=torch.uint64, device="cuda")
             c = dls.count(n, flags, wl.order, t, nodes=nodes, launch=launch)
             torch.cuda.synchronize()
