@@ -586,6 +586,10 @@ def run_leg(dls, spec, args, steps, stream, flush, seed, rank, ws, units=None,
                    "split_depth": int(depth_sel), "suffix_order": suffix_sel,
                    "order_cells": int(len(order)),
                    "tail_dropped": int(N * (N // 2 if FLAGS & 2 else N) - len(order)),
+                   "tail_rule": "dls_order_trim: the order's final cells, each the last "
+                                "open cell of its column, complete every filling in exactly "
+                                "one way, so the search stops before them; counts are of "
+                                "whole squares (checked against the oracle's whole order)",
                    "prefixes": int(P), "squares_per_step": squares, "nodes_per_step": nodes,
                    "kernel": run["kernel"] + " (CUDA graph)", "launch": cfg, "resolved": run,
                    "autotune": tuned,
