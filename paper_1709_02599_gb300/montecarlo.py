@@ -170,6 +170,7 @@ def main(argv=None):
     print(json.dumps({"n": a.n, "k": a.k, "n_k": n_k, "samples": a.samples, "seed": a.seed,
                       "mean_completions": res["mean"], "estimate": res["estimate"],
                       "stderr": res["stderr"], "squares_counted": int(res["completions"].sum()),
+                      "completions": [int(v) for v in res["completions"]],
                       "seconds_n_k": t1 - t0, "seconds_sample": t2 - t1}))
 
 
