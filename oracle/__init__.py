@@ -7,7 +7,9 @@ shares no code with the CUDA path.
 * ``dls_oracle.c`` -- recursive counter with value-indexed boolean occupancy
   arrays (Algorithms 1 and 2 of the paper), prefix enumeration and the
   draw-driven prefix sampler.
-* ``orders.py`` -- fill orders written from their definitions.
+* ``orders.py`` -- fill orders written from their definitions, and
+  ``trim_tail``, the shortened order whose count equals the whole order's
+  (pinned in tests/test_oracle.py on known totals and brute force).
 * ``brute.py`` -- row-permutation brute force for tiny orders (independent of
   any cell-by-cell search).
 """
