@@ -69,6 +69,9 @@ L2_FLUSH_BYTES = 256 << 20
 # 251 741 184 B read and 35 493 376 B written.
 _BW = ("dls8_diag64", "k_snapshot", "snapshot, byte words", True)
 TRAFFIC_PER_PREFIX = {
+    # symmetric order 10, field-shift step, 100 of the 2 000 rows-1-2
+    # prefixes split at depth 23 (125 320 prefixes, 3 914 240 B read)
+    ("vsym10_rows2", "k_snapshot", "snapshot, field shifts", False, 23): 3914240 / 125320,
     _BW + (22,): 678656 / 4573,
     _BW + (25,): 4960768 / 149590,
     _BW + (28,): 9852416 / 273038,
