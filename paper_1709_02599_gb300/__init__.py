@@ -95,8 +95,8 @@ def order_trim(n, flags, order, keep, window=TAIL_WINDOW):
     move to the end, then the run of that line's off-diagonal cells at the
     end is dropped -- each of them is the last open cell of its column (row)
     and the values these force are exactly those the line lacks.  The first
-    ``keep`` cells stay in place.  Orders with vertical symmetry and partial
-    orders come back unchanged."""
+    ``keep`` cells stay in place.  With vertical symmetry only a row's run
+    drops; partial orders come back unchanged."""
     L = lib()
     o, op, ol = _order(order)
     buf = np.zeros((DLS_MAX_N * DLS_MAX_N, 2), np.uint8)

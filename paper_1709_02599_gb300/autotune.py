@@ -6,8 +6,9 @@ Every trial counts the same squares: the base prefixes are extended to the
 candidate split depth with the same leading cells, and only the cells after
 the split are reordered (counts do not depend on their order; Section 2.3
 shows the search size does), and every order is shortened by dls_order_trim
-(a final run of cells forced by their columns or rows is dropped).  A trial is timed as a CUDA-graph launch
-(dls_plan_*) with CUDA events; all trials must report the same total.
+(a final run of cells forced by their columns or rows is dropped).  A trial
+is timed as a CUDA-graph launch (dls_plan_*) with CUDA events; all trials
+must report the same total.
 
     best = tune(n, flags, order, base, depths=[...])
     best["order"], best["depth"], best["launch"]    # Launch fields dict
