@@ -382,6 +382,22 @@ def serving_leg(n_jobs, limit_s, seed=0, **cfg):
                   "fixed, Poisson 200/s, seed %d" % seed}
     if out["unfinished"]:
         out["note"] = "stopped after %.0f s with jobs unfinished" % limit_s
+    # the served counts of the jobs of order <= 8, recounted by the batch
+    # kernels (each job split 2^14 ways), after the replay
+    from paper_1709_02599_gb300.montecarlo import counts_split
+    small = [k for k in sorted(done) if jobs[k]["n"] <= 8]
+    try:
+        bad = 0
+        for k in small:
+            j = jobs[k]
+            ref = counts_split(j["n"], j["flags"], j["order"],
+                               np.asarray(j["prefix"], np.uint8)[None], min_items=1 << 14)
+            bad += int(int(ref[0]) != int(done[k][1]))
+        out["batch_check"] = {"jobs": len(small), "agree": bad == 0, "mismatches": bad,
+                              "rule": "every completed job of order <= 8 recounted by the "
+                                      "batch kernels"}
+    except Exception as e:  # the check must not lose the serving numbers
+        out["batch_check"] = {"jobs": len(small), "error": repr(e)[:200]}
     return out
 
 
