@@ -60,22 +60,14 @@ ISSUE_LANES_PER_SM = 4 * 32      # 4 schedulers x 32 lanes, one instruction/clk
 L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) per prefix of the batched kernel, per (workload,
 # kernel, step, fused, split depth), from an ncu capture of that build (the
-# summary under profiles/ gives the command); a kernel without a capture of
-# its current build reports traffic null.  Captures of 16 of the 64
-# diagonals (stack cap 17), scaled per prefix: depth 22, 4 573 prefixes,
-# 678 656 B read; depth 25, 149 590 prefixes, 4 960 768 B read (the order
-# shortened by dls_order_trim, as the benchmark runs it); depth 28,
-# 273 038 prefixes, 9 852 416 B read; depth 31, 6 460 099 prefixes,
-# 251 741 184 B read and 35 493 376 B written.
+# summaries under profiles/ give the commands); a kernel or depth without a
+# capture of its current build reports traffic null.  Order 8: 16 of the 64
+# diagonals at depth 25 (stack cap 17, blocks of 64, strided queue), 149 590
+# prefixes, 4 972 544 B read.  (The symmetric order-10 capture, 31.2 bytes
+# per prefix, predates the strided queue: that leg reports null.)
 _BW = ("dls8_diag64", "k_snapshot", "snapshot, byte words", True)
 TRAFFIC_PER_PREFIX = {
-    # symmetric order 10, field-shift step, 100 of the 2 000 rows-1-2
-    # prefixes split at depth 23 (125 320 prefixes, 3 914 240 B read)
-    ("vsym10_rows2", "k_snapshot", "snapshot, field shifts", False, 23): 3914240 / 125320,
-    _BW + (22,): 678656 / 4573,
-    _BW + (25,): 4960768 / 149590,
-    _BW + (28,): 9852416 / 273038,
-    _BW + (31,): (251741184 + 35493376) / 6460099,
+    _BW + (25,): 4972544 / 149590,
 }
 
 

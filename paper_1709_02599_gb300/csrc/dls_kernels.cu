@@ -35,6 +35,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <numeric>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -87,6 +88,11 @@ struct KParams {
   int defer;                  // a stack overflow defers the prefix to the recount pass
   int recount;                // the recount pass: only deferred prefixes are searched
   int diag_words;             // DLS_DIAGONAL (the wide load checks the diagonals)
+  // k_snapshot hands out queue place k as item k * qstride mod n_items (0:
+  // in order): a stride near n_items / 64, coprime with n_items, interleaves
+  // the runs of neighbouring prefixes, whose search sizes are alike, so the
+  // heavy ones of a run are not all taken at the end of the queue
+  unsigned long long qstride;
   int8_t rslot[DLS_MAX_N];    // wide words: byte slot of each row / column (-1: none)
   int8_t cslot[DLS_MAX_N];
   uint8_t ci[DLS_MAX_CELLS];
@@ -910,8 +916,12 @@ __global__ void __launch_bounds__(512)
       if (lane == 0) base = atomicAdd(p.queue, (unsigned long long)nidle);
       base = __shfl_sync(FULL, base, 0);
       if (!busy) {
-        const long long item = (long long)base + __popc(idle & ((1u << lane) - 1u));
-        if (item < p.n_items) {
+        const long long k = (long long)base + __popc(idle & ((1u << lane) - 1u));
+        if (k < p.n_items) {
+          const long long item =
+              p.qstride ? (long long)(((unsigned long long)k * p.qstride) %
+                                      (unsigned long long)p.n_items)
+                        : k;
           busy = !snap_load<VSYM, NODES>(s, p, item, tbl, tb);
           if (!busy) finish_snapshot_item(s.prefix, s.cnt, p, ovf, lane_total);
         }
@@ -1353,6 +1363,7 @@ static int prepare_launch(int n, uint32_t flags, const uint8_t *order, int order
   kp.n_prefixes = n_prefixes;
   kp.n_items = n_prefixes << sh.lanes_log2;
   kp.prefixes = d_prefixes;
+  kp.qstride = 0ull;
   kp.counts = reinterpret_cast<unsigned long long *>(d_counts);
   kp.total = reinterpret_cast<unsigned long long *>(d_total);
   kp.nodes = reinterpret_cast<unsigned long long *>(d_nodes);
@@ -1442,6 +1453,15 @@ static int prepare_launch(int n, uint32_t flags, const uint8_t *order, int order
   const bool fu = fu_fits && (sh.fuse == 1 || (sh.fuse == 0 && kFuseByDefault && !vsym));
   pr->fused = fu;
   pr->wide = snap && wide;
+  // the batched snapshot kernel takes its queue in a strided order (see
+  // KParams::qstride); not where a count may stop early, whose report of
+  // the prefixes handed out ("every prefix from here on") needs the order
+  if (snap && !plain && sh.budget == 0 && sh.abort_flag == nullptr &&
+      kp.n_items >= 4096 && kp.n_items < (1ll << 32)) {
+    unsigned long long a = (unsigned long long)(kp.n_items + 63) / 64ull;
+    while (std::gcd(a, (unsigned long long)kp.n_items) != 1ull) ++a;
+    kp.qstride = a;
+  }
   pr->fn = snap ? pick_snapshot(plain, vsym, pr->wide, d_nodes != nullptr, dgw, la, fu)
                 : pick_kernel(sh.kernel, reg, vsym, d_nodes != nullptr, sh.lanes_log2 > 0);
   auto smem_for = [&](int block) {

@@ -108,6 +108,20 @@ def test_kernels_on_trimmed_orders(dls, emulated, n, flags, after, kind, step):
     assert rc == 0 and (res[0] == c_full).all()
 
 
+def test_strided_queue_order(dls, emulated):
+    """With 4 096 prefixes or more the batched snapshot kernel takes its
+    queue in a strided order (place k is prefix k * stride mod P): every
+    prefix is still counted once, into its own slot, also through the
+    recount pass of a capped stack and with the node count."""
+    wl = gpu_cases.split(dls, 7, D, 16, kind=dls.ORDER_HEURISTIC)
+    assert len(wl.prefixes) >= 4096
+    check_counts(emulated, wl, 7, D, [dict(), dict(block_threads=32), dict(stack_cap=2)])
+    # the field-shift step (vertical symmetry) takes the same queue
+    wl = gpu_cases.split(dls, 6, V, 6)
+    assert len(wl.prefixes) >= 4096
+    check_counts(emulated, wl, 6, V, [dict(), dict(stack_cap=1)])
+
+
 def test_lookahead_and_fused_step(dls, emulated):
     """Where no cell after the prefix lies on a diagonal: the lookahead
     (without vertical symmetry) prunes (fewer nodes, same counts); the fused
