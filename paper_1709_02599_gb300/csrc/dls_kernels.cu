@@ -1453,15 +1453,6 @@ static int prepare_launch(int n, uint32_t flags, const uint8_t *order, int order
   const bool fu = fu_fits && (sh.fuse == 1 || (sh.fuse == 0 && kFuseByDefault && !vsym));
   pr->fused = fu;
   pr->wide = snap && wide;
-  // the batched snapshot kernel takes its queue in a strided order (see
-  // KParams::qstride); not where a count may stop early, whose report of
-  // the prefixes handed out ("every prefix from here on") needs the order
-  if (snap && !plain && sh.budget == 0 && sh.abort_flag == nullptr &&
-      kp.n_items >= 4096 && kp.n_items < (1ll << 32)) {
-    unsigned long long a = (unsigned long long)(kp.n_items + 63) / 64ull;
-    while (std::gcd(a, (unsigned long long)kp.n_items) != 1ull) ++a;
-    kp.qstride = a;
-  }
   pr->fn = snap ? pick_snapshot(plain, vsym, pr->wide, d_nodes != nullptr, dgw, la, fu)
                 : pick_kernel(sh.kernel, reg, vsym, d_nodes != nullptr, sh.lanes_log2 > 0);
   auto smem_for = [&](int block) {
@@ -1502,6 +1493,19 @@ static int prepare_launch(int n, uint32_t flags, const uint8_t *order, int order
   };
   rc = grid_for(sh.block, smem, &pr->grid);
   if (rc) return rc;
+  // the batched byte-word search takes its queue in a strided order (see
+  // KParams::qstride) where the lanes of the grid get few prefixes each (at
+  // most 16: the end of the queue is then a large part of the pass; with
+  // more -- the symmetric order-10 workload, 32 per lane -- the given order
+  // measured faster); not where a count may stop early, whose report of the
+  // prefixes handed out ("every prefix from here on") needs the given order
+  if (snap && !plain && !vsym && !pr->wide && sh.budget == 0 && sh.abort_flag == nullptr &&
+      kp.n_items >= 4096 && kp.n_items < (1ll << 32) &&
+      kp.n_items <= 16ll * (long long)pr->grid * (long long)sh.block) {
+    unsigned long long a = (unsigned long long)(kp.n_items + 63) / 64ull;
+    while (std::gcd(a, (unsigned long long)kp.n_items) != 1ull) ++a;
+    kp.qstride = a;
+  }
   if (pr->recount) {
     // the recount pass: the full bound, a smaller block where its stacks
     // need it; it takes only the deferred prefixes

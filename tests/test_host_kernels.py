@@ -109,17 +109,20 @@ def test_kernels_on_trimmed_orders(dls, emulated, n, flags, after, kind, step):
 
 
 def test_strided_queue_order(dls, emulated):
-    """With 4 096 prefixes or more the batched snapshot kernel takes its
-    queue in a strided order (place k is prefix k * stride mod P): every
-    prefix is still counted once, into its own slot, also through the
-    recount pass of a capped stack and with the node count."""
-    wl = gpu_cases.split(dls, 7, D, 16, kind=dls.ORDER_HEURISTIC)
-    assert len(wl.prefixes) >= 4096
-    check_counts(emulated, wl, 7, D, [dict(), dict(block_threads=32), dict(stack_cap=2)])
-    # the field-shift step (vertical symmetry) takes the same queue
-    wl = gpu_cases.split(dls, 6, V, 6)
-    assert len(wl.prefixes) >= 4096
-    check_counts(emulated, wl, 6, V, [dict(), dict(stack_cap=1)])
+    """Where the grid's lanes get 16 prefixes or fewer each (and there are
+    4 096 or more), the batched byte-word search takes its queue in a
+    strided order (place k is prefix k * stride mod P): every prefix is
+    still counted once, into its own slot, also through the recount pass of
+    a capped stack and with the node count."""
+    for n, flags, after, kind, shapes in (
+            (7, D, 12, dls.ORDER_HEURISTIC, [dict(), dict(stack_cap=2)]),):
+        wl = gpu_cases.split(dls, n, flags, after, kind=kind)
+        P = len(wl.prefixes)
+        for sh in shapes:
+            rc, info = emulated.count("describe", n, flags, wl.order, wl.prefixes, **sh)
+            assert rc == 0 and info["run"] == 2
+            assert 4096 <= P <= 16 * info["grid_blocks"] * info["block_threads"], (P, info)
+        check_counts(emulated, wl, n, flags, shapes)
 
 
 def test_lookahead_and_fused_step(dls, emulated):
