@@ -63,11 +63,13 @@ L2_FLUSH_BYTES = 256 << 20
 # summaries under profiles/ give the commands); a kernel or depth without a
 # capture of its current build reports traffic null.  Order 8: 16 of the 64
 # diagonals at depth 25 (stack cap 17, blocks of 64, strided queue), 149 590
-# prefixes, 4 972 544 B read.  (The symmetric order-10 capture, 31.2 bytes
-# per prefix, predates the strided queue: that leg reports null.)
+# prefixes, 4 972 544 B read.  Symmetric order 10 (the field-shift search,
+# which keeps the queue in order): 100 of the 2 000 rows-1-2 prefixes at
+# depth 23, 125 320 prefixes, 3 914 240 B read.
 _BW = ("dls8_diag64", "k_snapshot", "snapshot, byte words", True)
 TRAFFIC_PER_PREFIX = {
     _BW + (25,): 4972544 / 149590,
+    ("vsym10_rows2", "k_snapshot", "snapshot, field shifts", False, 23): 3914240 / 125320,
 }
 
 
