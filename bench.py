@@ -51,11 +51,11 @@ import dls_inputs  # noqa: E402
 METRIC = "diagonal Latin squares enumerated/sec on 1 GB300 (exact count) vs plain launch; p99 latency"
 UNIT = "squares/s"
 DIAGS, AFTER_ROW0 = 64, 20
-# integer operations per search node in the bitmask form (see the design
-# notes): isolate + clear the lowest candidate bit (4), mark and unmark the
-# row and column words (4), next cell's forbidden mask and complement (2),
-# loop test (1)
-OPS_PER_NODE = 11
+# the fewest integer operations a search node takes in the bitmask form:
+# isolate + clear the lowest candidate bit (4), mark and unmark the row and
+# column words (4), next cell's forbidden mask and complement (2), the depth
+# step (1), the loop test (1)
+OPS_PER_NODE = 12
 ISSUE_LANES_PER_SM = 4 * 32      # 4 schedulers x 32 lanes, one instruction/clk
 L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) per prefix of the batched kernel, per (workload,
