@@ -24,6 +24,7 @@ import pytest
 
 import gpu_cases
 import oracle
+from oracle import orders
 
 D, V = 1, 2
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -170,6 +171,16 @@ def test_wide_step_on_order9(dls, step_check, tmp_path, flags):
         wl2 = gpu_cases.Workload(9, D, wl.order, pre, wl.oracle_order, o_pre, depth=depth)
         iters = check_workload(step_check, tmp_path, wl2, 9, D)
         assert set(iters) == {0, 1, 2}
+        # the same on orders shortened by dls_order_trim (the oracle runs its
+        # own trim_tail of its order; counts also equal the whole order's)
+        t = dls.order_trim(9, D, wl.order, depth)
+        o_t = orders.trim_tail(9, wl.oracle_order, depth)
+        assert [tuple(map(int, c)) for c in t] == o_t and len(t) < len(wl.order)
+        wl3 = gpu_cases.Workload(9, D, t, pre, o_t, o_pre, depth=depth)
+        check_workload(step_check, tmp_path, wl3, 9, D)
+        c_t, _ = oracle.count_many(9, D, o_t, o_pre, threads=4)
+        c_f, _ = oracle.count_many(9, D, wl.oracle_order, o_pre, threads=4)
+        assert (c_t == c_f).all()
 
 
 def test_step_on_one_diagonal_of_the_order8_workload(dls, step_check, tmp_path):
